@@ -1,0 +1,310 @@
+"""Benchmark of the adaptive Hessian-sketch ridge solver on one GB300.
+
+Workload (one "step" = one full adaptive solve from x = 0 to the stopping rule,
+i.e. every step of the hot path: sketches, factorisations, gradient passes,
+applies and the controller): A = U diag(j^-1) V^T of size 131072 x 2048 (FP32,
+1 GiB, larger than L2), Haar U and V, nu set so sum s^2/(s^2+nu^2) = 100,
+b = A x0 + 0.01 noise; SRHT sketch, gradient-only adaptive IHS from m = 1,
+tolerance 1e-5 on the relative prediction norm.  Synthetic stand-in for the
+paper's MNIST/CIFAR workloads (absent here).
+
+Reported: ms per solve (device time, CUDA events), verified against the CPU
+FP64 direct solution; the roofline of the gradient pass (the dominant kernel)
+from CUDA events recorded around every gradient pass inside the timed solves;
+an end-to-end time through host buffers; the CPU oracle on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ROWS, D_COLS, DE_TARGET, NOISE, SEED = 131072, 2048, 100.0, 0.01, 0
+TOL = 1e-5
+WORKLOAD = "spectral_131072x2048_poly1_de100_srht_gd"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problem(device):
+    from paper_2006_05874_gb300 import problems
+
+    return problems.spectral(n=N_ROWS, d=D_COLS, de_target=DE_TARGET, noise=NOISE, seed=SEED, device=device)
+
+
+def oracle_reference_solution(p):
+    from oracle import linalg
+
+    return linalg.direct_solve(p.A, p.b, p.nu)
+
+
+def cpu_oracle_sample(p, budget_s=20.0):
+    """The CPU oracle's adaptive IHS (FP64, as it stands) on the first n_s rows
+    of the workload; time scaled by N_ROWS / n_s (work per pass is linear in n)."""
+    from oracle import ihs as oracle_ihs
+
+    n_s = 4096
+    while True:
+        t0 = time.perf_counter()
+        res = oracle_ihs.adaptive_ihs(p.A[:n_s], p.b[:n_s], p.nu, kind="srht", variant="gd", tol=TOL)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 3 or n_s * 2 > N_ROWS:
+            break
+        n_s *= 2
+    return {
+        "value": dt * 1e3 * (N_ROWS / n_s),
+        "unit": "ms",
+        "cores": os.cpu_count(),
+        "kind": "oracle",
+        "sample": "adaptive IHS (SRHT, gradient-only, FP64 numpy) on the first %d of %d rows, %d gradient passes, "
+                  "levels %s; wall time %.2f s scaled by %d/%d" % (n_s, N_ROWS, res.grad_passes, res.levels, dt,
+                                                                  N_ROWS, n_s),
+    }
+
+
+def run_reference(args):
+    """--impl reference: the CPU FP64 oracle on the host cores, same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2006_05874_gb300 import problems
+
+    # generate on CPU (no GPU work in this arm): the same construction, numpy
+    p = problems.spectral(n=N_ROWS, d=D_COLS, de_target=DE_TARGET, noise=NOISE, seed=SEED, device=None) \
+        if os.environ.get("IHS_REF_FULL") else None
+    if p is None:
+        p = make_problem("cuda" if _has_cuda() else None)
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    base = None
+    for _ in range(args.steps):
+        base = cpu_oracle_sample(p, budget_s=6.0)
+        vals.append(base["value"])
+    v = statistics.median(vals)
+    base["value"] = v
+    line = {"metric": "ms to 1e-5 rel. error vs FP64 oracle", "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {"workload": WORKLOAD},
+            "cpu_baseline": base,
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def _has_cuda():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2006_05874_gb300 import ihs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    p = make_problem("cuda")
+    x_star = oracle_reference_solution(p)
+    A = torch.from_numpy(p.A).cuda()
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros(p.d, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = ihs.Context(kind="srht", variant="gd", tol=TOL, stream=stream)
+
+    def one_solve():
+        x.zero_()
+        return ctx.solve(A, b, p.nu, x)
+
+    for _ in range(max(3, args.warmup)):
+        one_solve()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = ihs.kernel_launches()
+    reps = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            reps.append(one_solve())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = ihs.kernel_launches() - launches0
+    ms_total = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    ms_per = ms_total / args.steps
+
+    from oracle import linalg
+
+    err = linalg.relative_error(p.A, p.nu, x.cpu().numpy(), x_star)
+    grad_passes = sum(r.grad_passes for r in reps)
+    ms_grad = sum(r.ms_grad for r in reps) / grad_passes
+    bytes_per_pass = 4.0 * p.n * p.d + 4.0 * p.n + 8.0 * p.d
+    peaks, peak_kind = measured_peaks()
+    achieved = bytes_per_pass / (ms_grad * 1e-3) / 1e9
+
+    # end to end through host buffers: pinned A, b -> device, solve, x -> host
+    A_h = torch.from_numpy(p.A).pin_memory()
+    b_h = torch.from_numpy(p.b).pin_memory()
+    x_h = torch.empty(p.d).pin_memory()
+    A_d = torch.empty_like(A)
+    b_d = torch.empty_like(b)
+    x_d = torch.zeros(p.d, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        A_d.copy_(A_h, non_blocking=True)
+        b_d.copy_(b_h, non_blocking=True)
+        x_d.zero_()
+        ctx.solve(A_d, b_d, p.nu, x_d)
+        x_h.copy_(x_d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    err_e2e = linalg.relative_error(p.A, p.nu, x_h.numpy(), x_star)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(p)
+    r0 = reps[-1]
+    line = {
+        "metric": "ms to 1e-5 rel. error vs FP64 oracle; grad-pass & sketch HBM GB/s",
+        "value": ms_per,
+        "unit": "ms",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": ms_per,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": p.n, "d": p.d, "nu": p.nu, "tol": TOL, "sketch": "srht",
+                   "variant": "gd", "l2": "inputs larger than L2 (A is 1 GiB)",
+                   "rel_error": err, "rel_error_e2e": err_e2e, "levels": r0.levels(), "iterations": r0.iterations,
+                   "grad_passes_per_solve": r0.grad_passes, "ms_sketch_factor": r0.ms_sketch,
+                   "ms_iterate": r0.ms_iterate},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
+                     "kernel": "gradient pass (k_grad_fast + k_grad_reduce)", "ms_per_launch": ms_grad,
+                     "algorithmic_bytes": bytes_per_pass},
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * p.n * p.d + 4 * p.n,
+                "d2h_bytes_per_step": 4 * p.d},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.destroy()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

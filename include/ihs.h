@@ -1,0 +1,180 @@
+/*
+ * ihs.h - C ABI of the GB300 adaptive Hessian-sketch ridge solver.
+ *
+ * Method: Lacotte & Pilanci, "Effective Dimension Adaptive Sketching Methods for
+ * Faster Regularized Least-Squares Optimization" (NeurIPS 2020).  The library
+ * solves the ridge problem of Eq. 1,
+ *
+ *     x* = argmin_x  1/2 ||A x - b||^2 + nu^2/2 ||x||^2 ,   A in R^{n x d}, n >= d,
+ *
+ * with the adaptive Polyak-IHS of Algorithm 1 or its gradient-only variant
+ * (Sec. 5), preconditioning with the sketched Hessian H_S = (SA)^T SA + nu^2 I
+ * of Eq. 3 applied through the Woodbury identity of App. B.4.
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are row-major with leading dimension equal to their column count
+ *    (A: n x d, SA: m x d).  Vectors are contiguous.
+ *  - Pointers without a `_h` suffix are DEVICE pointers (cudaMalloc'd or torch
+ *    CUDA tensors) on the current device; `_h` pointers are host pointers.
+ *    float buffers must be 4-byte aligned; the fast kernels also want 16-byte
+ *    alignment and d % 4 == 0, and fall back to slower kernels otherwise.
+ *  - The caller owns every input and output buffer.  The library owns only the
+ *    opaque handles (ihs_ctx, ihs_factor_t) and the scratch memory they hold;
+ *    the matching *_destroy call frees them.
+ *  - All device work is ordered on the stream given to ihs_ctx_create.  A call
+ *    that returns a host scalar (`*_h` outputs) synchronises that stream before
+ *    returning; others return as soon as the work is enqueued.
+ *  - Every call returns an int status: IHS_OK (0) or a negative IHS_E* code.  A
+ *    failing call leaves its outputs unspecified.  Device faults and launch
+ *    failures surface as IHS_ECUDA.
+ *  - A context is not thread-safe; use one per host thread / stream.
+ */
+#ifndef IHS_H
+#define IHS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define IHS_OK          0
+#define IHS_EINVAL     (-1)  /* bad argument (sizes, nu <= 0, n < d, m < 1, ...) */
+#define IHS_ENOMEM     (-2)  /* device or pinned-host allocation failed          */
+#define IHS_ENOTPD     (-3)  /* Cholesky met a non-positive pivot (FP64)          */
+#define IHS_ENONFINITE (-4)  /* NaN/Inf in an input or in the decrement r_t       */
+#define IHS_EMCAP      (-5)  /* sketch size reached its cap (report flag only)    */
+#define IHS_EMAXITER   (-6)  /* iteration limit reached; x holds the last iterate */
+#define IHS_ETIMEOUT   (-7)  /* a bounded device wait gave up                     */
+#define IHS_ECUDA      (-8)  /* CUDA runtime error                                */
+
+/* ---- enumerations -------------------------------------------------------- */
+#define IHS_SKETCH_SRHT   0  /* subsampled randomized Hadamard transform (App. C.2) */
+#define IHS_SKETCH_GAUSS  1  /* i.i.d. N(0, 1/m) entries (Sec. 1, App. C.1)        */
+
+#define IHS_VARIANT_GD     0 /* gradient-IHS candidates only (Sec. 5 variant)   */
+#define IHS_VARIANT_POLYAK 1 /* Algorithm 1: Polyak candidate, then gradient-IHS */
+
+#define IHS_PREC_FP32  0     /* Gaussian sketch arithmetic: FP32 products       */
+#define IHS_PREC_BF16  1     /* BF16 operands, FP32 accumulation (tensor cores)  */
+#define IHS_PREC_FP8   2     /* FP8 e4m3 operands + per-column scales, FP32 acc. */
+
+#define IHS_REPORT_MAX_LEVELS 40
+
+/* Solver parameters (Algorithm 1's inputs plus the build's choices). */
+typedef struct ihs_params {
+    int32_t  kind;       /* IHS_SKETCH_*                                         */
+    int32_t  variant;    /* IHS_VARIANT_*                                        */
+    int32_t  precision;  /* IHS_PREC_* (Gaussian sketch only)                    */
+    int32_t  max_iter;   /* limit on accepted iterations t                       */
+    int64_t  m_init;     /* initial sketch size, a power of two >= 1             */
+    double   rho;        /* aspect-ratio target of Def 3.1 / 3.2 (default 0.1)   */
+    double   eta;        /* Gaussian concentration slack of Def 3.1 (0.01)       */
+    double   tol;        /* stop when sqrt(2 Lambda r_t) <= tol ||Abar x_t||      */
+    double   floor;      /* noise-floor guard: a rejected step with
+                            r_t <= floor^2 r_1 stops instead of doubling (0: off) */
+    uint64_t seed;       /* Philox key of every random draw                      */
+} ihs_params;
+
+/* What ihs_solve did. */
+typedef struct ihs_report {
+    int32_t status;          /* IHS_OK, IHS_EMAXITER, ...                        */
+    int32_t iterations;      /* final t                                          */
+    int32_t grad_passes;     /* gradient evaluations (passes over A)             */
+    int32_t n_levels;        /* number of sketches drawn                         */
+    int32_t accepted_polyak;
+    int32_t accepted_gd;
+    int32_t rejected;        /* doublings of m                                   */
+    int32_t flags;           /* bit 0: m reached its cap; bit 1: floor guard hit */
+    int64_t m_final;
+    int64_t m_levels[IHS_REPORT_MAX_LEVELS]; /* sketch size of each level drawn   */
+    double  r1;              /* sketched Newton decrement at x_1 (Lemma 4.1)     */
+    double  r_final;         /* decrement at the returned iterate                */
+    double  axnorm_final;    /* ||Abar x_T||                                     */
+    double  ms_sketch;       /* device time in sketch + factor (CUDA events)     */
+    double  ms_iterate;      /* device time in gradient passes + applies         */
+    double  ms_grad;         /* device time in the gradient passes alone          */
+} ihs_report;
+
+typedef struct ihs_ctx ihs_ctx;
+typedef struct ihs_factor ihs_factor_t;
+
+/* Library version string (static storage). */
+const char* ihs_version(void);
+
+/* Text of the last CUDA runtime error seen by this host thread (static
+ * storage; empty if none). */
+const char* ihs_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts); a diagnostic for counting device work. */
+int64_t ihs_kernel_launches(void);
+
+/* Fill *p with the defaults: SRHT, gradient-only, FP32, rho = 0.1, eta = 0.01,
+ * m_init = 1, tol = 1e-5, floor = 0, max_iter = 500, seed = 0. */
+int ihs_params_default(ihs_params* p_h);
+
+/* Create a context bound to `stream` (a cudaStream_t; NULL = legacy default
+ * stream) on the current device.  *p_h may be NULL (defaults).  The context
+ * owns its scratch memory and a pinned host buffer. */
+int ihs_ctx_create(ihs_ctx** ctx_h, void* stream, const ihs_params* p_h);
+int ihs_ctx_destroy(ihs_ctx* ctx);
+/* Replace the parameters of an existing context. */
+int ihs_ctx_set_params(ihs_ctx* ctx, const ihs_params* p_h);
+
+/* ---- random draws (App. C.2) --------------------------------------------- */
+/* Rademacher signs eps_i in {-1,+1}, i < n_pad (int8, device).  Philox4x32-10
+ * with key (seed_lo, seed_hi), counter (i_lo, i_hi, level, 0); eps_i = +1 iff
+ * bit 0 of the first output word is 0. */
+int ihs_srht_signs(ihs_ctx* ctx, int64_t n_pad, uint64_t seed, int32_t level, int8_t* eps);
+
+/* The m row indices of [0, n_pad) with the smallest 64-bit keys
+ * key_i = (w1 << 32) | w0 of Philox counter (i_lo, i_hi, level, 1), ties broken
+ * by index, written in ascending index order (int32, device): a uniformly
+ * random m-subset drawn without replacement (App. C.2).  1 <= m <= n_pad <= 2^31. */
+int ihs_srht_rows(ihs_ctx* ctx, int64_t n_pad, int64_t m, uint64_t seed, int32_t level, int32_t* rows);
+
+/* ---- the three hot kernels ----------------------------------------------- */
+/* SA = S A for the embedding S of `kind` drawn at (seed, level) (Sec. 1, Eq. 3):
+ *  SRHT : S = sqrt(n_pad/m) R H_norm diag(eps) on A zero-padded to
+ *         n_pad = 2^ceil(log2 n) rows, i.e. SA_j = m^-1/2 sum_i
+ *         (-1)^popcount(r_j & i) eps_i a_i, rows r_j from ihs_srht_rows.
+ *  GAUSS: S_ji = z_ji / sqrt(m), z from Philox counter (i, j/4, level, 2) by
+ *         Box-Muller; arithmetic per the context's precision.
+ * A: n x d (device), SA: m x d FP32 (device, overwritten).  1 <= m; for SRHT
+ * m <= n_pad.  Uses context scratch. */
+int ihs_sketch(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m,
+               int32_t kind, uint64_t seed, int32_t level, float* SA);
+
+/* Factor H_S = (SA)^T SA + nu^2 I (Eq. 3) for repeated applies: m < d caches
+ * the FP64 Cholesky factor of nu^2 I_m + SA SA^T (Woodbury, App. B.4); m >= d
+ * the FP64 Cholesky factor of H_S itself.  SA (m x d, device) must stay valid
+ * and unchanged while *F_h is in use.  nu > 0.  IHS_ENOTPD on breakdown. */
+int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** F_h);
+int ihs_factor_destroy(ihs_factor_t* F);
+
+/* gt = H_S^{-1} g (d-vectors, device FP32) and, if r_h != NULL, the sketched
+ * Newton decrement r = 1/2 g^T gt (Lemma 4.1) in FP64 (host; synchronises). */
+int ihs_apply_hinv(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt, double* r_h);
+
+/* One fused pass over A: g = A^T (A x - b) + nu^2 x (gradient of Eq. 1, App.
+ * B.1 stacked form) with compensated FP32 accumulation and a fixed-order
+ * reduction (bitwise reproducible).  If axnorm2_h != NULL also returns
+ * ||A x||^2 (FP64, host; synchronises).  A n x d, b n, x d, g d: device FP32. */
+int ihs_grad(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
+             double nu, const float* x, float* g, double* axnorm2_h);
+
+/* ---- the solver ---------------------------------------------------------- */
+/* Adaptive IHS (Algorithm 1 or its gradient-only variant, per the context's
+ * parameters; `tol` overrides params.tol when > 0).  x (device, d): on entry
+ * x_1 (also x_0), on exit the last iterate.  rep_h may be NULL.  Returns IHS_OK
+ * on convergence, IHS_EMAXITER if the limit was hit. */
+int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
+              double nu, double tol, float* x, ihs_report* rep_h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IHS_H */

@@ -92,6 +92,22 @@ def gaussian_z_cols(m, i0, i1, seed, level):
     return z[:m]
 
 
+def gaussian_z_rows(rows, n, seed, level):
+    """Selected rows j of the standard normal draws, all n columns
+    (len(rows) x n); for sampled checks at large n."""
+    k0, k1 = seed_key(seed)
+    out = np.empty((len(rows), n), dtype=np.float64)
+    i = np.arange(n, dtype=np.uint64)
+    for k, j in enumerate(rows):
+        w = philox4x32_10(i, np.uint64(j // 4), np.uint64(level), np.uint64(GAUSS), k0, k1)
+        lane = j % 4
+        wa, wb = (w[0], w[1]) if lane < 2 else (w[2], w[3])
+        radius = np.sqrt(-2.0 * np.log(_uniform_open0(wa)))
+        angle = 2.0 * np.pi * _uniform_closed0(wb)
+        out[k] = radius * (np.cos(angle) if lane % 2 == 0 else np.sin(angle))
+    return out
+
+
 def gaussian_z(m, n, seed, level):
     """All n columns of the standard normal draws (m x n)."""
     return gaussian_z_cols(m, 0, n, seed, level)

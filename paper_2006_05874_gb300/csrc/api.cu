@@ -1,0 +1,145 @@
+// Context, scratch arena, parameters and status plumbing of the C ABI.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+#include <atomic>
+
+namespace {
+thread_local char g_last_error[512];
+std::atomic<int64_t> g_launches{0};
+}
+
+void ihs_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" int64_t ihs_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void ihs_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s (%d) at %s:%d: %s", cudaGetErrorString(e), (int)e, file,
+             line, what);
+}
+
+extern "C" const char* ihs_last_error(void) { return g_last_error; }
+
+extern "C" const char* ihs_version(void) { return "ihs-gb300 0.1 (sm_103a)"; }
+
+extern "C" int ihs_params_default(ihs_params* p) {
+    if (!p) return IHS_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->kind = IHS_SKETCH_SRHT;
+    p->variant = IHS_VARIANT_GD;
+    p->precision = IHS_PREC_FP32;
+    p->max_iter = 500;
+    p->m_init = 1;
+    p->rho = 0.1;
+    p->eta = 0.01;
+    p->tol = 1e-5;
+    p->floor = 0.0;
+    p->seed = 0;
+    return IHS_OK;
+}
+
+static int validate_params(const ihs_params* p) {
+    if (p->kind != IHS_SKETCH_SRHT && p->kind != IHS_SKETCH_GAUSS) return IHS_EINVAL;
+    if (p->variant != IHS_VARIANT_GD && p->variant != IHS_VARIANT_POLYAK) return IHS_EINVAL;
+    if (p->precision < IHS_PREC_FP32 || p->precision > IHS_PREC_FP8) return IHS_EINVAL;
+    if (p->m_init < 1 || (p->m_init & (p->m_init - 1))) return IHS_EINVAL;
+    if (!(p->rho > 0.0 && p->rho < 1.0)) return IHS_EINVAL;
+    if (p->kind == IHS_SKETCH_GAUSS && !(p->rho <= 0.18 && p->eta > 0.0 && p->eta <= 0.01)) return IHS_EINVAL;
+    if (!(p->tol >= 0.0) || !(p->floor >= 0.0) || p->max_iter < 1) return IHS_EINVAL;
+    return IHS_OK;
+}
+
+extern "C" int ihs_ctx_create(ihs_ctx** out, void* stream, const ihs_params* p) {
+    if (!out) return IHS_EINVAL;
+    *out = nullptr;
+    ihs_params prm;
+    if (p) {
+        prm = *p;
+    } else {
+        ihs_params_default(&prm);
+    }
+    IHS_TRY(validate_params(&prm));
+    ihs_ctx* c = new (std::nothrow) ihs_ctx;
+    if (!c) return IHS_ENOMEM;
+    memset(c, 0, sizeof(*c));
+    c->p = prm;
+    c->stream = static_cast<cudaStream_t>(stream);
+    int st = IHS_OK;
+    do {
+        if (cudaGetDevice(&c->device) != cudaSuccess) { st = IHS_ECUDA; break; }
+        if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+            st = IHS_ECUDA;
+            break;
+        }
+        if (cudaMallocHost(&c->pinned, 64 * sizeof(double)) != cudaSuccess) { st = IHS_ENOMEM; break; }
+        if (cudaMalloc(&c->d_status, 256) != cudaSuccess) { st = IHS_ENOMEM; break; }
+        if (cudaMemsetAsync(c->d_status, 0, 256, c->stream) != cudaSuccess) { st = IHS_ECUDA; break; }
+        for (int i = 0; i < 4; ++i)
+            if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { st = IHS_ECUDA; break; }
+    } while (0);
+    if (st != IHS_OK) {
+        ihs_ctx_destroy(c);
+        return st;
+    }
+    *out = c;
+    return IHS_OK;
+}
+
+extern "C" int ihs_ctx_destroy(ihs_ctx* c) {
+    if (!c) return IHS_OK;
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < SLOT_COUNT; ++i)
+        if (c->buf[i]) cudaFree(c->buf[i]);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->d_status) cudaFree(c->d_status);
+    for (int i = 0; i < 4; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    delete c;
+    return IHS_OK;
+}
+
+extern "C" int ihs_ctx_set_params(ihs_ctx* c, const ihs_params* p) {
+    if (!c || !p) return IHS_EINVAL;
+    IHS_TRY(validate_params(p));
+    c->p = *p;
+    return IHS_OK;
+}
+
+int ihs_scratch(ihs_ctx* c, int slot, size_t bytes, void** out) {
+    if (slot < 0 || slot >= SLOT_COUNT) return IHS_EINVAL;
+    if (bytes == 0) bytes = 16;
+    if (c->buf_bytes[slot] < bytes) {
+        if (c->buf[slot]) {
+            // in-flight kernels may still use the old buffer
+            IHS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+            cudaFree(c->buf[slot]);
+            c->buf[slot] = nullptr;
+            c->buf_bytes[slot] = 0;
+        }
+        const size_t grow = bytes + bytes / 4 + 4096;
+        if (cudaMalloc(&c->buf[slot], grow) != cudaSuccess) {
+            cudaGetLastError();
+            return IHS_ENOMEM;
+        }
+        c->buf_bytes[slot] = grow;
+    }
+    *out = c->buf[slot];
+    return IHS_OK;
+}
+
+int ihs_check_status(ihs_ctx* c) {
+    unsigned h = 0;
+    IHS_CUDA_TRY(cudaMemcpyAsync(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    IHS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (h) {
+        IHS_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
+        if (h & IHS_DEV_TIMEOUT) return IHS_ETIMEOUT;
+        if (h & IHS_DEV_NOTPD) return IHS_ENOTPD;
+    }
+    IHS_CUDA_TRY(cudaGetLastError());
+    return IHS_OK;
+}

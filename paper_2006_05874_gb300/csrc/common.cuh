@@ -1,0 +1,253 @@
+// Internal definitions shared by the CUDA translation units of the library.
+// Nothing here is part of the public C ABI (include/ihs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/ihs.h"
+
+#define IHS_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) {                            \
+            ihs_set_last_cuda_error(_e, #expr, __FILE__, __LINE__); \
+            return IHS_ECUDA;                               \
+        }                                                   \
+    } while (0)
+
+#define IHS_TRY(expr)                   \
+    do {                                \
+        int _s = (expr);                \
+        if (_s != IHS_OK) return _s;    \
+    } while (0)
+
+void ihs_count_launch();
+#define IHS_LAUNCH_CHECK()                    \
+    do {                                      \
+        ihs_count_launch();                   \
+        IHS_CUDA_TRY(cudaGetLastError());     \
+    } while (0)
+
+void ihs_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// ---------------------------------------------------------------------------
+// Scratch arena: grow-only device buffers keyed by slot.
+enum ScratchSlot {
+    SLOT_GRAD_PART = 0,   // per-CTA gradient partials (float2 x G x d) + G doubles
+    SLOT_GRAD_R,          // residual vector of the generic gradient path (n floats)
+    SLOT_SELECT,          // radix-select histograms and compaction counters
+    SLOT_SKETCH_PART,     // split partial sums of the sketch
+    SLOT_SKETCH_ROWS,     // selected SRHT rows
+    SLOT_SOLVE,           // solver state vectors
+    SLOT_SOLVE_SA,        // solver-owned SA (m x d)
+    SLOT_MISC,            // small device scalars (status word, reductions)
+    SLOT_COUNT
+};
+
+// Device-side status word bits (set by kernels that give up a bounded wait).
+#define IHS_DEV_TIMEOUT 1u
+#define IHS_DEV_NOTPD   2u
+
+struct ihs_ctx {
+    int device;
+    int sm_count;
+    cudaStream_t stream;
+    ihs_params p;
+    void* buf[SLOT_COUNT];
+    size_t buf_bytes[SLOT_COUNT];
+    double* pinned;          // host pinned scratch (64 doubles)
+    unsigned* d_status;      // device status word (IHS_DEV_*)
+    cudaEvent_t ev[4];
+};
+
+struct ihs_factor {
+    ihs_ctx* ctx;
+    const float* SA;
+    int64_t m, d, k;      // k = m (Woodbury) or d (direct)
+    double nu;
+    int woodbury;
+    double* L;            // k x k lower Cholesky factor (row-major, FP64)
+    double* Linv;         // k x k inverse of L (lower, FP64)
+    double* work;         // 3 k doubles + d doubles of apply scratch + reduction slots
+};
+
+int ihs_scratch(ihs_ctx* ctx, int slot, size_t bytes, void** out);
+int ihs_check_status(ihs_ctx* ctx);   // reads and clears the device status word
+
+// Internal launch helpers (enqueue only, no synchronisation).
+int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
+                     double nu, const float* x, float* g, double* d_axnorm2);
+int ihs_sketch_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m,
+                       int32_t kind, uint64_t seed, int32_t level, float* SA);
+int ihs_rows_enqueue(ihs_ctx* ctx, int64_t n_pad, int64_t m, uint64_t seed, int32_t level,
+                     int32_t* rows);
+int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F);       // enqueue + check pivots (syncs)
+int ihs_apply_enqueue(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt,
+                      double* d_r);
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+
+// Philox4x32-10 (Salmon et al., SC'11): two 32x32->64 multiplies per round,
+// Weyl-sequence key schedule, ten rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+enum { STREAM_SIGNS = 0, STREAM_ROWS = 1, STREAM_GAUSS = 2, STREAM_PROBE = 3 };
+
+__device__ __forceinline__ int srht_sign_bit(uint64_t i, uint32_t level, uint32_t k0, uint32_t k1) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), level, STREAM_SIGNS), k0, k1);
+    return (int)(w.x & 1u);   // 1 -> eps = -1
+}
+
+__device__ __forceinline__ uint64_t srht_row_key(uint64_t i, uint32_t level, uint32_t k0, uint32_t k1) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), level, STREAM_ROWS), k0, k1);
+    return ((uint64_t)w.y << 32) | (uint64_t)w.x;
+}
+
+// Box-Muller pair from two Philox words: u1 = (w/2^8 + 1) 2^-24 in (0, 1],
+// u2 = (w'/2^8) 2^-24 in [0, 1); both exact in binary32.
+__device__ __forceinline__ float2 box_muller(uint32_t wa, uint32_t wb) {
+    const float u1 = (float)((wa >> 8) + 1u) * 5.9604644775390625e-8f;
+    const float u2 = (float)(wb >> 8) * 5.9604644775390625e-8f;
+    const float radius = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    return make_float2(radius * c, radius * s);
+}
+
+// Four standard normals z[4q .. 4q+3] of column i at `level`.
+__device__ __forceinline__ float4 gauss4(uint32_t i, uint32_t q, uint32_t level, uint32_t k0, uint32_t k1) {
+    const uint4 w = philox4x32_10(make_uint4(i, q, level, STREAM_GAUSS), k0, k1);
+    const float2 a = box_muller(w.x, w.y);
+    const float2 b = box_muller(w.z, w.w);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Error-free transformations (Knuth TwoSum; TwoProduct through FMA).  The
+// _rn intrinsics keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Compensated accumulator (hi + lo) of float terms.
+struct Acc2 {
+    float hi, lo;
+    __device__ __forceinline__ void add(float v) {
+        float s, e;
+        two_sum(hi, v, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {   // Dot2 step
+        float p, ep, s, es;
+        two_prod(a, b, p, ep);
+        two_sum(hi, p, s, es);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(ep, es));
+    }
+    __device__ __forceinline__ void add_pair(float h2, float l2) {
+        float s, e;
+        two_sum(hi, h2, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(e, l2));
+    }
+};
+
+__device__ __forceinline__ Acc2 acc2_shfl_xor(Acc2 a, int mask) {
+    Acc2 o;
+    o.hi = __shfl_xor_sync(0xffffffffu, a.hi, mask);
+    o.lo = __shfl_xor_sync(0xffffffffu, a.lo, mask);
+    return o;
+}
+
+// ---- shared-memory barriers and bulk copies (sm_90+ PTX) -------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar` for at most ~limit_ns; on expiry set the
+// timeout bit of the device status word and return false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* status,
+                                                  uint64_t limit_ns = 1000000000ull) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) {
+            atomicOr(status, IHS_DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// 1-D bulk copy global -> shared, completing on `bar` (bytes % 16 == 0, both
+// addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__host__ __device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__host__ __device__ __forceinline__ int64_t next_pow2_64(int64_t n) {
+    int64_t p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}

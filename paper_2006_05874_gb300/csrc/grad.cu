@@ -1,0 +1,451 @@
+// Fused gradient pass g = A^T (A x - b) + nu^2 x (gradient of Eq. 1; the
+// per-iteration O(nd) cost of App. B.4), one read of A.
+//
+// Fast path (d % 4 == 0, 16-byte aligned A): a persistent grid, one CTA per
+// SM, streams contiguous row tiles of A through a ring of shared-memory
+// stages filled by 1-D bulk copies (cp.async.bulk, completion on mbarriers).
+// Each thread owns CPT float4 column chunks of a row; per row it forms a
+// compensated (Dot2) partial of a_i . x, the partials of a row are combined by
+// warp shuffles and, across warps, in shared memory in a fixed order; then
+// r_i = a_i . x - b_i is broadcast and every thread accumulates r_i a_i into
+// compensated per-column accumulators held in registers.  Each CTA writes its
+// d partial sums (hi, lo); a second kernel adds the partials in a fixed order
+// in FP64, adds nu^2 x and rounds to FP32.  The result is bitwise reproducible
+// for a given GPU.
+//
+// Generic path (any d, any alignment): r = A x - b (one warp per row), then
+// A^T r with one thread per column, then the same reduction.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// Dynamic shared-memory layout of k_grad_fast: [stages][R*d floats] | mbarriers
+// | per-warp row partials | row residuals | FP64 block-reduction slots.
+struct FastLayout {
+    size_t full, red, rbuf, dred, total;
+    __host__ __device__ FastLayout(int stages, int R, int W, int d) {
+        full = (size_t)stages * R * d * sizeof(float);
+        red = align16(full + 8 * (size_t)stages);
+        rbuf = align16(red + sizeof(Acc2) * (size_t)R * W);
+        dred = align16(rbuf + sizeof(float) * (size_t)R);
+        total = dred + sizeof(double) * kThreads;
+    }
+};
+
+template <int TPR, int CPT, int RT>
+__global__ void __launch_bounds__(kThreads, 1)
+k_grad_fast(const float* __restrict__ A, const float* __restrict__ b, const float* __restrict__ x,
+            int64_t n, int d, int64_t ntiles, int stages, float2* __restrict__ part,
+            double* __restrict__ part_ax2, unsigned* status) {
+    constexpr int RP = kThreads / TPR;  // rows handled in parallel
+    constexpr int R = RT * RP;          // rows per stage
+    constexpr int W = TPR / 32;         // warps per row
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int stage_floats = R * d;
+    const FastLayout lay(stages, R, W, d);
+    float* stage_base = reinterpret_cast<float*>(smem);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.full);
+    Acc2* red = reinterpret_cast<Acc2*>(smem + lay.red);      // R * W
+    float* rbuf = reinterpret_cast<float*>(smem + lay.rbuf);  // R
+    double* dred = reinterpret_cast<double*>(smem + lay.dred);
+
+    const int tid = threadIdx.x;
+    const int grp = tid / TPR;
+    const int t = tid % TPR;
+    const int wir = t / 32;   // warp index within the row's warps
+    const int lane = tid & 31;
+    const int chunks = d >> 2;
+
+    const int64_t t0 = (int64_t)blockIdx.x * ntiles / gridDim.x;
+    const int64_t t1 = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
+    const int64_t my_tiles = t1 - t0;
+
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    float4 xr[CPT];
+    bool cvalid[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        const int c = t + TPR * k;
+        cvalid[k] = c < chunks;
+        xr[k] = cvalid[k] ? reinterpret_cast<const float4*>(x)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    Acc2 gacc[CPT][4];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gacc[k][q] = Acc2{0.f, 0.f};
+    double ax2 = 0.0;
+
+    auto issue = [&](int64_t local) {
+        const int s = (int)(local % stages);
+        const int64_t row0 = (t0 + local) * R;
+        const int64_t rows = min((int64_t)R, n - row0);
+        const uint32_t bytes = (uint32_t)(rows * d * sizeof(float));
+        mbar_arrive_expect_tx(&full[s], bytes);
+        bulk_g2s(stage_base + (size_t)s * stage_floats, A + row0 * d, bytes, &full[s]);
+    };
+
+    int64_t issued = 0;
+    if (tid == 0) {
+        for (; issued < min((int64_t)(stages - 1), my_tiles); ++issued) issue(issued);
+    }
+    int64_t consumed = 0;
+    for (int64_t l = 0; l < my_tiles; ++l) {
+        const int s = (int)(l % stages);
+        if (tid == 0 && l + stages - 1 < my_tiles) {
+            issue(l + stages - 1);
+            issued = l + stages;
+        }
+        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((l / stages) & 1), status);
+        if (__syncthreads_or(!ok)) break;
+        consumed = l + 1;
+
+        const float* st = stage_base + (size_t)s * stage_floats;
+        const int64_t row0 = (t0 + l) * R;
+        const int rows = (int)min((int64_t)R, n - row0);
+
+        float4 a[RT][CPT];
+        Acc2 dot[RT];
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+            const int rr = grp + j * RP;
+            dot[j] = Acc2{0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+                const int c = t + TPR * k;
+                a[j][k] = (cvalid[k] && rr < rows) ? reinterpret_cast<const float4*>(st + (size_t)rr * d)[c]
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                dot[j].add_prod(a[j][k].x, xr[k].x);
+                dot[j].add_prod(a[j][k].y, xr[k].y);
+                dot[j].add_prod(a[j][k].z, xr[k].z);
+                dot[j].add_prod(a[j][k].w, xr[k].w);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                const Acc2 o = acc2_shfl_xor(dot[j], off);
+                dot[j].add_pair(o.hi, o.lo);
+            }
+        }
+        float rv[RT];
+        if (W == 1) {
+            __syncthreads();   // every thread is done with stage s
+#pragma unroll
+            for (int j = 0; j < RT; ++j) {
+                const int rr = grp + j * RP;
+                float r = 0.f;
+                if (rr < rows) {
+                    r = __fadd_rn(__fsub_rn(dot[j].hi, b[row0 + rr]), dot[j].lo);
+                    if (t == 0) {
+                        const double v = (double)dot[j].hi + (double)dot[j].lo;
+                        ax2 += v * v;
+                    }
+                }
+                rv[j] = r;
+            }
+        } else {
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < RT; ++j) red[(grp + j * RP) * W + wir] = dot[j];
+            }
+            __syncthreads();   // stage s consumed, per-warp partials visible
+            if (tid < R) {
+                const int rr = tid;
+                Acc2 s2 = red[rr * W];
+#pragma unroll
+                for (int w = 1; w < W; ++w) s2.add_pair(red[rr * W + w].hi, red[rr * W + w].lo);
+                float r = 0.f;
+                if (rr < rows) {
+                    r = __fadd_rn(__fsub_rn(s2.hi, b[row0 + rr]), s2.lo);
+                    const double v = (double)s2.hi + (double)s2.lo;
+                    ax2 += v * v;
+                }
+                rbuf[rr] = r;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < RT; ++j) rv[j] = rbuf[grp + j * RP];
+        }
+        // g += sum_rows r_i a_i : an FMA chain over the RT rows, then one
+        // compensated add per column.
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+            for (int j = 0; j < RT; ++j) {
+                s0 = __fmaf_rn(rv[j], a[j][k].x, s0);
+                s1 = __fmaf_rn(rv[j], a[j][k].y, s1);
+                s2 = __fmaf_rn(rv[j], a[j][k].z, s2);
+                s3 = __fmaf_rn(rv[j], a[j][k].w, s3);
+            }
+            gacc[k][0].add(s0);
+            gacc[k][1].add(s1);
+            gacc[k][2].add(s2);
+            gacc[k][3].add(s3);
+        }
+    }
+    if (consumed < my_tiles) {
+        // A wait gave up: let the copies already issued land before exiting.
+        if (tid == 0) {
+            for (int64_t l = consumed; l < issued; ++l)
+                mbar_wait_bounded(&full[l % stages], (uint32_t)((l / stages) & 1), status);
+        }
+        __syncthreads();
+        return;
+    }
+    __syncthreads();
+    // Combine the RP row groups (same columns) in a fixed order.
+    Acc2* comb = reinterpret_cast<Acc2*>(smem);   // RP x d, stages are idle now
+    if (RP > 1) {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            const int c = t + TPR * k;
+            if (cvalid[k]) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) comb[(size_t)grp * d + 4 * c + q] = gacc[k][q];
+            }
+        }
+        __syncthreads();
+        if (grp == 0) {
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+                const int c = t + TPR * k;
+                if (cvalid[k]) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        for (int g2 = 1; g2 < RP; ++g2) {
+                            const Acc2 o = comb[(size_t)g2 * d + 4 * c + q];
+                            gacc[k][q].add_pair(o.hi, o.lo);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (grp == 0) {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            const int c = t + TPR * k;
+            if (cvalid[k]) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    part[(size_t)blockIdx.x * d + 4 * c + q] = make_float2(gacc[k][q].hi, gacc[k][q].lo);
+            }
+        }
+    }
+    // ||A x||^2 partial of this CTA, fixed-order block reduction.
+    __syncthreads();
+    dred[tid] = ax2;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kThreads; ++i) s += dred[i];
+        part_ax2[blockIdx.x] = s;
+    }
+}
+
+// g[c] = fl32( sum_g (hi + lo)  + nu^2 x[c] ) over G partials in fixed order.
+__global__ void k_grad_reduce(const float2* __restrict__ part, const double* __restrict__ part_ax2, int G,
+                              int d, double nu2, const float* __restrict__ x, float* __restrict__ g,
+                              double* __restrict__ axnorm2) {
+    __shared__ double sm[8][33];
+    const int cx = threadIdx.x & 31, sy = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + cx;
+    double s = 0.0;
+    if (col < d) {
+        for (int gi = sy; gi < G; gi += 8) {
+            const float2 v = part[(size_t)gi * d + col];
+            s += (double)v.x + (double)v.y;
+        }
+    }
+    sm[sy][cx] = s;
+    __syncthreads();
+    if (sy == 0 && col < d) {
+        double t = sm[0][cx];
+        for (int k = 1; k < 8; ++k) t += sm[k][cx];
+        g[col] = (float)(t + nu2 * (double)x[col]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && axnorm2 != nullptr) {
+        double t = 0.0;
+        for (int gi = 0; gi < G; ++gi) t += part_ax2[gi];
+        *axnorm2 = t;
+    }
+}
+
+// Generic path, step 1: r_i = a_i . x - b_i (Dot2), one warp per row; per-block
+// FP64 partial of ||A x||^2.
+__global__ void k_resid_generic(const float* __restrict__ A, const float* __restrict__ b,
+                                const float* __restrict__ x, int64_t n, int d, float* __restrict__ r,
+                                double* __restrict__ part_ax2) {
+    __shared__ double sm[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t rows_per_block = 8 * 16;
+    const int64_t row_begin = (int64_t)blockIdx.x * rows_per_block;
+    double ax2 = 0.0;
+    for (int64_t i = row_begin + warp; i < min(n, row_begin + rows_per_block); i += 8) {
+        Acc2 acc{0.f, 0.f};
+        const float* ai = A + i * d;
+        for (int c = lane; c < d; c += 32) acc.add_prod(ai[c], x[c]);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const Acc2 o = acc2_shfl_xor(acc, off);
+            acc.add_pair(o.hi, o.lo);
+        }
+        if (lane == 0) {
+            r[i] = __fadd_rn(__fsub_rn(acc.hi, b[i]), acc.lo);
+            const double v = (double)acc.hi + (double)acc.lo;
+            ax2 += v * v;
+        }
+    }
+    if (lane == 0) sm[warp] = ax2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += sm[w];
+        part_ax2[blockIdx.x] = s;
+    }
+}
+
+// Generic path, step 2: per row-group partials of A^T r, one thread per column.
+__global__ void k_atr_generic(const float* __restrict__ A, const float* __restrict__ r, int64_t n, int d,
+                              int64_t rows_per_group, float2* __restrict__ part) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.y * rows_per_group;
+    const int64_t i1 = min(n, i0 + rows_per_group);
+    if (col >= d) return;
+    Acc2 acc{0.f, 0.f};
+    for (int64_t i = i0; i < i1; ++i) acc.add(__fmul_rn(r[i], A[i * d + col]));
+    part[(size_t)blockIdx.y * d + col] = make_float2(acc.hi, acc.lo);
+}
+
+// Sum src[0..count) in order into dst[0] and zero dst[1..G).
+__global__ void k_fold_doubles(const double* src, int64_t count, double* dst, int G) {
+    double s = 0.0;
+    for (int64_t i = 0; i < count; ++i) s += src[i];
+    for (int i = 1; i < G; ++i) dst[i] = 0.0;
+    dst[0] = s;
+}
+
+struct FastCfg {
+    int tpr, cpt, rt;
+};
+
+FastCfg pick_fast(int d) {
+    const int chunks = d / 4;
+    if (chunks <= 32) return {32, 1, 8};
+    if (chunks <= 64) return {64, 1, 8};
+    if (chunks <= 128) return {128, 1, 8};
+    if (chunks <= 256) return {256, 1, 8};
+    if (chunks <= 512) return {256, 2, 4};
+    if (chunks <= 1024) return {256, 4, 2};
+    return {256, 8, 1};
+}
+
+template <int TPR, int CPT, int RT>
+int launch_fast(ihs_ctx* ctx, const float* A, const float* b, const float* x, int64_t n, int d, float2* part,
+                double* part_ax2, int* G_out) {
+    constexpr int RP = kThreads / TPR;
+    constexpr int R = RT * RP;
+    constexpr int W = TPR / 32;
+    const size_t stage_bytes = (size_t)R * d * sizeof(float);
+    const size_t budget = 200 * 1024;
+    int stages = 8;
+    while (stages > 2 && FastLayout(stages, R, W, d).total > budget) --stages;
+    size_t smem = FastLayout(stages, R, W, d).total;
+    if (smem > budget || stage_bytes * stages > budget) return IHS_EINVAL;
+    const size_t comb = (size_t)RP * d * sizeof(Acc2);
+    if (smem < comb) smem = comb;
+    const int64_t ntiles = ceil_div64(n, R);
+    int64_t G = ctx->sm_count;
+    if (G > ntiles) G = ntiles;
+    auto kern = k_grad_fast<TPR, CPT, RT>;
+    IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)G, kThreads, smem, ctx->stream>>>(A, b, x, n, d, ntiles, stages, part, part_ax2,
+                                                      ctx->d_status);
+    IHS_LAUNCH_CHECK();
+    *G_out = (int)G;
+    return IHS_OK;
+}
+
+}  // namespace
+
+int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
+                     const float* x, float* g, double* d_axnorm2) {
+    if (n < 1 || d < 1 || d > (1 << 20)) return IHS_EINVAL;
+    const bool aligned = ((uintptr_t)A % 16 == 0) && ((uintptr_t)x % 16 == 0) && (d % 4 == 0) && d <= 8192;
+    const int64_t Gmax = 4 * (int64_t)ctx->sm_count + 1024;
+    void* ws = nullptr;
+    const size_t part_bytes = (size_t)Gmax * d * sizeof(float2);
+    IHS_TRY(ihs_scratch(ctx, SLOT_GRAD_PART, part_bytes + Gmax * sizeof(double) + 256, &ws));
+    float2* part = static_cast<float2*>(ws);
+    double* part_ax2 = reinterpret_cast<double*>(static_cast<char*>(ws) + part_bytes);
+    int G = 0;
+    if (aligned && n >= 1) {
+        const FastCfg c = pick_fast((int)d);
+        int st;
+        if (c.tpr == 32) st = launch_fast<32, 1, 8>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (c.tpr == 64) st = launch_fast<64, 1, 8>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (c.tpr == 128) st = launch_fast<128, 1, 8>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (c.cpt == 1) st = launch_fast<256, 1, 8>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (c.cpt == 2) st = launch_fast<256, 2, 4>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (c.cpt == 4) st = launch_fast<256, 4, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else st = launch_fast<256, 8, 1>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        IHS_TRY(st);
+    } else {
+        const int64_t rblocks = ceil_div64(n, 128);
+        void* rws = nullptr;
+        const size_t rbytes = ((size_t)n * sizeof(float) + 15) & ~(size_t)15;
+        IHS_TRY(ihs_scratch(ctx, SLOT_GRAD_R, rbytes + (size_t)rblocks * sizeof(double), &rws));
+        float* r = static_cast<float*>(rws);
+        double* rpart = reinterpret_cast<double*>(static_cast<char*>(rws) + rbytes);
+        const int64_t groups =
+            std::min<int64_t>(Gmax, std::max<int64_t>(1, 2 * (int64_t)ctx->sm_count / ceil_div64(d, 256)));
+        const int64_t rows_per_group = ceil_div64(n, groups);
+        const int64_t ngroups = ceil_div64(n, rows_per_group);
+        k_resid_generic<<<(unsigned)rblocks, 256, 0, ctx->stream>>>(A, b, x, n, (int)d, r, rpart);
+        IHS_LAUNCH_CHECK();
+        dim3 grid((unsigned)ceil_div64(d, 256), (unsigned)ngroups);
+        k_atr_generic<<<grid, 256, 0, ctx->stream>>>(A, r, n, (int)d, rows_per_group, part);
+        IHS_LAUNCH_CHECK();
+        G = (int)ngroups;
+        k_fold_doubles<<<1, 1, 0, ctx->stream>>>(rpart, rblocks, part_ax2, G);
+        IHS_LAUNCH_CHECK();
+    }
+    k_grad_reduce<<<(unsigned)ceil_div64(d, 32), 256, 0, ctx->stream>>>(part, part_ax2, G, (int)d, nu * nu, x, g,
+                                                                        d_axnorm2);
+    IHS_LAUNCH_CHECK();
+    return IHS_OK;
+}
+
+
+extern "C" int ihs_grad(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
+                        const float* x, float* g, double* axnorm2_h) {
+    if (!ctx || !A || !b || !x || !g) return IHS_EINVAL;
+    if (!(nu >= 0.0) || n < 1 || d < 1) return IHS_EINVAL;
+    double* d_ax = nullptr;
+    if (axnorm2_h) {
+        void* ws = nullptr;
+        IHS_TRY(ihs_scratch(ctx, SLOT_MISC, 4096, &ws));
+        d_ax = static_cast<double*>(ws) + 256;
+    }
+    IHS_TRY(ihs_grad_enqueue(ctx, A, b, n, d, nu, x, g, d_ax));
+    if (axnorm2_h) {
+        IHS_CUDA_TRY(cudaMemcpyAsync(ctx->pinned, d_ax, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        *axnorm2_h = ctx->pinned[0];
+    }
+    return ihs_check_status(ctx);
+}

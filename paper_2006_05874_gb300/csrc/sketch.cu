@@ -1,0 +1,268 @@
+// Sketch SA = S A (Sec. 1, Eq. 3) for the two embeddings of the paper.
+//
+// SRHT (App. C.2): S = sqrt(n_pad/m) R H_norm diag(eps) on A zero-padded to
+// n_pad rows.  With n_pad = P Q and i = p Q + q, the Hadamard entry factors as
+// (-1)^popcount(r & i) = (-1)^popcount(r_hi & p) (-1)^popcount(r_lo & q), so
+//   SA_j = m^-1/2 sum_p (-1)^popcount(r_hi_j & p) Y_p[r_lo_j],
+//   Y_p  = H_Q diag(eps_p) A_p   (length-Q FWHT of the sign-flipped block p).
+// A CTA owns a tile of C columns and a range of blocks p: it transforms each
+// Q x C block in shared memory and accumulates the m selected rows; block
+// ranges are combined by a fixed-order reduction.  A is read once.
+//
+// Gaussian (Sec. 1, App. C.1): S_ji = z_ji / sqrt(m), z drawn in-kernel from
+// Philox (never stored); split over n with a fixed-order reduction.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kSrhtQmax = 1024;
+constexpr int kSrhtC = 16;
+constexpr int kSrhtThreads = 512;
+
+__global__ void __launch_bounds__(kSrhtThreads)
+k_srht_fwht(const float* __restrict__ A, int64_t n, int d, int64_t m, int Q, int logQ, int64_t P, int PG,
+            const int32_t* __restrict__ rows, uint32_t level, uint32_t k0, uint32_t k1, int acc_in_smem,
+            float* __restrict__ out /* PG x m x d partials */) {
+    extern __shared__ __align__(16) float sm[];
+    const int CP = kSrhtC + 1;   // padded row stride
+    float* X = sm;               // Q x CP
+    float* sg = X + (size_t)Q * CP;          // Q signs (+-1)
+    float* acc = sg + Q;                     // m x C (when in shared memory)
+    const int tid = threadIdx.x;
+    const int col0 = blockIdx.x * kSrhtC;
+    const int ncol = min(kSrhtC, d - col0);
+    const int pg = blockIdx.y;
+    const int64_t p0 = (int64_t)pg * P / PG, p1 = (int64_t)(pg + 1) * P / PG;
+    float* outp = out + (size_t)pg * m * d;
+
+    if (acc_in_smem) {
+        for (int64_t e = tid; e < m * kSrhtC; e += kSrhtThreads) acc[e] = 0.f;
+    } else {
+        for (int64_t e = tid; e < m * kSrhtC; e += kSrhtThreads) {
+            const int64_t j = e / kSrhtC;
+            const int c = (int)(e % kSrhtC);
+            if (c < ncol) outp[j * d + col0 + c] = 0.f;
+        }
+    }
+    for (int64_t p = p0; p < p1; ++p) {
+        __syncthreads();
+        for (int q = tid; q < Q; q += kSrhtThreads) {
+            const uint64_t i = (uint64_t)(p * Q + q);
+            sg[q] = srht_sign_bit(i, level, k0, k1) ? -1.f : 1.f;
+        }
+        __syncthreads();
+        for (int e = tid; e < Q * kSrhtC; e += kSrhtThreads) {
+            const int q = e / kSrhtC, c = e % kSrhtC;
+            const int64_t i = p * Q + q;
+            float v = 0.f;
+            if (i < n && c < ncol) v = A[i * d + col0 + c];
+            X[q * CP + c] = sg[q] * v;
+        }
+        __syncthreads();
+        // radix-2 butterflies along q
+        for (int h = 1; h < Q; h <<= 1) {
+            for (int e = tid; e < (Q / 2) * kSrhtC; e += kSrhtThreads) {
+                const int bfly = e / kSrhtC, c = e % kSrhtC;
+                const int q0 = (bfly / h) * 2 * h + (bfly % h);
+                const float a = X[q0 * CP + c], b = X[(q0 + h) * CP + c];
+                X[q0 * CP + c] = a + b;
+                X[(q0 + h) * CP + c] = a - b;
+            }
+            __syncthreads();
+        }
+        // accumulate the selected rows of this block
+        for (int64_t e = tid; e < m * kSrhtC; e += kSrhtThreads) {
+            const int64_t j = e / kSrhtC;
+            const int c = (int)(e % kSrhtC);
+            const uint32_t r = (uint32_t)rows[j];
+            const uint32_t lo = r & (uint32_t)(Q - 1);
+            const uint64_t hi = (uint64_t)(r >> logQ);
+            const float v = X[lo * CP + c];
+            const float sv = (__popcll(hi & (uint64_t)p) & 1) ? -v : v;
+            if (acc_in_smem) {
+                acc[e] += sv;
+            } else if (c < ncol) {
+                outp[j * d + col0 + c] += sv;
+            }
+        }
+    }
+    if (acc_in_smem) {
+        __syncthreads();
+        for (int64_t e = tid; e < m * kSrhtC; e += kSrhtThreads) {
+            const int64_t j = e / kSrhtC;
+            const int c = (int)(e % kSrhtC);
+            if (c < ncol) outp[j * d + col0 + c] = acc[e];
+        }
+    }
+}
+
+// out[e] = scale * sum_k part[k][e] in a fixed order (FP64).
+__global__ void k_reduce_parts(const float* __restrict__ part, int K, int64_t count, double scale,
+                               float* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += (double)part[(size_t)k * count + e];
+        out[e] = (float)(s * scale);
+    }
+}
+
+__global__ void k_reduce_parts2(const float2* __restrict__ part, int K, int64_t count, double scale,
+                                float* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const float2 v = part[(size_t)k * count + e];
+            s += (double)v.x + (double)v.y;
+        }
+        out[e] = (float)(s * scale);
+    }
+}
+
+// Gaussian sketch, FP32 SIMT: tile BM x BN of SA over a K range of rows of A;
+// z tile generated in shared memory from Philox, compensated accumulation per
+// BK-chunk.
+constexpr int kGBM = 64, kGBN = 64, kGBK = 32, kGThreads = 256;
+
+__global__ void __launch_bounds__(kGThreads)
+k_gauss_simt(const float* __restrict__ A, int64_t n, int d, int64_t m, int64_t rows_per_split, uint32_t level,
+             uint32_t k0, uint32_t k1, float2* __restrict__ part /* KS x m x d */) {
+    __shared__ float zs[kGBK][kGBM + 4];
+    __shared__ float as[kGBK][kGBN + 4];
+    const int tid = threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.x * kGBM;
+    const int c0 = blockIdx.y * kGBN;
+    const int64_t i_begin = (int64_t)blockIdx.z * rows_per_split;
+    const int64_t i_end = min(n, i_begin + rows_per_split);
+    const int ty = tid / 16, tx = tid % 16;   // 16 x 16 threads, 4 x 4 outputs each
+    Acc2 acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = Acc2{0.f, 0.f};
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += kGBK) {
+        __syncthreads();
+        // z tile: kGBK columns i x kGBM rows j; one Philox call gives 4 rows.
+        for (int e = tid; e < kGBK * (kGBM / 4); e += kGThreads) {
+            const int ii = e / (kGBM / 4), qq = e % (kGBM / 4);
+            const int64_t i = i0 + ii;
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < i_end) z = gauss4((uint32_t)i, (uint32_t)((j0 >> 2) + qq), level, k0, k1);
+            zs[ii][qq * 4 + 0] = z.x;
+            zs[ii][qq * 4 + 1] = z.y;
+            zs[ii][qq * 4 + 2] = z.z;
+            zs[ii][qq * 4 + 3] = z.w;
+        }
+        for (int e = tid; e < kGBK * kGBN; e += kGThreads) {
+            const int ii = e / kGBN, cc = e % kGBN;
+            const int64_t i = i0 + ii;
+            as[ii][cc] = (i < i_end && c0 + cc < d) ? A[i * d + c0 + cc] : 0.f;
+        }
+        __syncthreads();
+        float cacc[4][4] = {};
+#pragma unroll 8
+        for (int kk = 0; kk < kGBK; ++kk) {
+            float zr[4], ar[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) zr[a] = zs[kk][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) ar[b] = as[kk][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) cacc[a][b] = __fmaf_rn(zr[a], ar[b], cacc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b].add(cacc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t j = j0 + ty * 4 + a;
+        if (j >= m) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int c = c0 + tx * 4 + b;
+            if (c < d) part[((size_t)blockIdx.z * m + j) * d + c] = make_float2(acc[a][b].hi, acc[a][b].lo);
+        }
+    }
+}
+
+int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed, int32_t level,
+                 float* SA) {
+    const int64_t n_pad = next_pow2_64(n);
+    if (m > n_pad) return IHS_EINVAL;
+    const int Q = (int)std::min<int64_t>(n_pad, kSrhtQmax);
+    int logQ = 0;
+    while ((1 << logQ) < Q) ++logQ;
+    const int64_t P = n_pad / Q;
+    const int64_t CT = ceil_div64(d, kSrhtC);
+    int64_t PG = std::max<int64_t>(1, ceil_div64(2 * (int64_t)ctx->sm_count, CT));
+    PG = std::min<int64_t>(PG, P);
+    // rows + partial buffer
+    void* rws = nullptr;
+    IHS_TRY(ihs_scratch(ctx, SLOT_SKETCH_ROWS, (size_t)m * sizeof(int32_t), &rws));
+    int32_t* rows = static_cast<int32_t*>(rws);
+    IHS_TRY(ihs_rows_enqueue(ctx, n_pad, m, seed, level, rows));
+    void* pws = nullptr;
+    IHS_TRY(ihs_scratch(ctx, SLOT_SKETCH_PART, (size_t)PG * m * d * sizeof(float), &pws));
+    float* part = static_cast<float*>(pws);
+    const size_t base = ((size_t)Q * (kSrhtC + 1) + Q) * sizeof(float);
+    const size_t acc_bytes = (size_t)m * kSrhtC * sizeof(float);
+    const int acc_in_smem = (base + acc_bytes <= 200 * 1024) ? 1 : 0;
+    const size_t smem = base + (acc_in_smem ? acc_bytes : 0);
+    IHS_CUDA_TRY(cudaFuncSetAttribute(k_srht_fwht, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)CT, (unsigned)PG);
+    k_srht_fwht<<<grid, kSrhtThreads, smem, ctx->stream>>>(A, n, (int)d, m, Q, logQ, P, (int)PG, rows,
+                                                          (uint32_t)level, (uint32_t)seed,
+                                                          (uint32_t)(seed >> 32), acc_in_smem, part);
+    IHS_LAUNCH_CHECK();
+    const int64_t count = m * d;
+    const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
+    k_reduce_parts<<<rgrid, 256, 0, ctx->stream>>>(part, (int)PG, count, 1.0 / sqrt((double)m), SA);
+    IHS_LAUNCH_CHECK();
+    return IHS_OK;
+}
+
+int gauss_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed, int32_t level,
+                  float* SA) {
+    const int64_t MT = ceil_div64(m, kGBM), NT = ceil_div64(d, kGBN);
+    int64_t KS = std::max<int64_t>(1, ceil_div64(4 * (int64_t)ctx->sm_count, MT * NT));
+    KS = std::min<int64_t>(KS, ceil_div64(n, 4 * kGBK));
+    KS = std::min<int64_t>(KS, 256);
+    const int64_t rows_per_split = ceil_div64(ceil_div64(n, KS), kGBK) * kGBK;
+    KS = ceil_div64(n, rows_per_split);
+    void* pws = nullptr;
+    IHS_TRY(ihs_scratch(ctx, SLOT_SKETCH_PART, (size_t)KS * m * d * sizeof(float2), &pws));
+    float2* part = static_cast<float2*>(pws);
+    dim3 grid((unsigned)MT, (unsigned)NT, (unsigned)KS);
+    k_gauss_simt<<<grid, kGThreads, 0, ctx->stream>>>(A, n, (int)d, m, rows_per_split, (uint32_t)level,
+                                                     (uint32_t)seed, (uint32_t)(seed >> 32), part);
+    IHS_LAUNCH_CHECK();
+    const int64_t count = m * d;
+    const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
+    k_reduce_parts2<<<rgrid, 256, 0, ctx->stream>>>(part, (int)KS, count, 1.0 / sqrt((double)m), SA);
+    IHS_LAUNCH_CHECK();
+    return IHS_OK;
+}
+
+}  // namespace
+
+int ihs_sketch_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, int32_t kind,
+                       uint64_t seed, int32_t level, float* SA) {
+    if (n < 1 || d < 1 || m < 1 || level < 0 || m > ((int64_t)1 << 31)) return IHS_EINVAL;
+    if (kind == IHS_SKETCH_SRHT) return srht_enqueue(ctx, A, n, d, m, seed, level, SA);
+    if (kind == IHS_SKETCH_GAUSS) return gauss_enqueue(ctx, A, n, d, m, seed, level, SA);
+    return IHS_EINVAL;
+}
+
+extern "C" int ihs_sketch(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, int32_t kind,
+                          uint64_t seed, int32_t level, float* SA) {
+    if (!ctx || !A || !SA) return IHS_EINVAL;
+    IHS_TRY(ihs_sketch_enqueue(ctx, A, n, d, m, kind, seed, level, SA));
+    return IHS_OK;
+}

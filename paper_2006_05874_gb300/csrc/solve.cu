@@ -1,0 +1,320 @@
+// Adaptive IHS controller: Algorithm 1 (Polyak candidate first, then the
+// gradient-IHS candidate, else m <- 2m and a new sketch) and its gradient-only
+// variant (Sec. 5).  Every step of the path runs in the library's kernels; the
+// host reads back three FP64 scalars per candidate (the sketched Newton
+// decrement r of Lemma 4.1, ||A x||^2 and ||x||^2) to take the accept /
+// double / stop decisions in FP64.
+//
+// Readings of points the paper leaves open (they match the CPU reference):
+//  * sketches are keyed by (seed, level), level = log2 m;
+//  * after a doubling both gt_t and r_t are recomputed; r_1 keeps its value;
+//  * m is capped at n_pad (SRHT) or n (Gaussian); at the cap a rejected
+//    gradient step is accepted and report flag bit 0 is set;
+//  * stop before an iteration once sqrt(2 Lambda r_t) <= tol ||Abar x_t||
+//    (delta_t <= gamma_1 r_t <= Lambda r_t, proofs of Thm 4.1 / 4.2);
+//  * optional floor guard: a rejected step with r_t <= floor^2 r_1 stops.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+struct Params {
+    double lam, Lam, mu_gd, c_gd, mu_p, beta_p, c_p;
+};
+
+// Thm 2.1 / 2.2 step sizes and rates at the bounds of Def 3.1 / Def 3.2.
+Params make_params(int kind, double rho, double eta) {
+    double lo, hi;
+    if (kind == IHS_SKETCH_GAUSS) {
+        const double c_eta = (1.0 + 3.0 * sqrt(eta)) * (1.0 + 3.0 * sqrt(eta));
+        const double s = sqrt(c_eta * rho);
+        lo = (1.0 - s) * (1.0 - s);
+        hi = (1.0 + s) * (1.0 + s);
+    } else {
+        lo = 1.0 - sqrt(rho);
+        hi = 1.0 + sqrt(rho);
+    }
+    Params p;
+    p.lam = lo;
+    p.Lam = hi;
+    p.mu_gd = 2.0 / (1.0 / lo + 1.0 / hi);
+    p.c_gd = ((hi - lo) / (hi + lo)) * ((hi - lo) / (hi + lo));
+    const double a = 1.0 / sqrt(lo) + 1.0 / sqrt(hi);
+    p.mu_p = 4.0 / (a * a);
+    const double q = (sqrt(hi) - sqrt(lo)) / (sqrt(hi) + sqrt(lo));
+    p.beta_p = q * q;
+    p.c_p = p.beta_p;
+    return p;
+}
+
+// xc = x - mu gt + beta (x - xp); block partials of ||xc||^2 (FP64).
+__global__ void k_candidate(const float* __restrict__ x, const float* __restrict__ gt,
+                            const float* __restrict__ xp, int64_t d, float mu, float beta, float* __restrict__ xc,
+                            double* __restrict__ part) {
+    __shared__ double sm[256];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (i < d) {
+        float v = __fmaf_rn(-mu, gt[i], x[i]);
+        if (beta != 0.f) v = __fmaf_rn(beta, __fsub_rn(x[i], xp[i]), v);
+        xc[i] = v;
+        sq = (double)v * (double)v;
+    }
+    sm[threadIdx.x] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 256; ++k) s += sm[k];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_sumsq(const float* __restrict__ x, int64_t d, double* __restrict__ part) {
+    __shared__ double sm[256];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const double v = i < d ? (double)x[i] : 0.0;
+    sm[threadIdx.x] = v * v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 256; ++k) s += sm[k];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_fold(const double* __restrict__ part, int count, double* __restrict__ out) {
+    double s = 0.0;
+    for (int k = 0; k < count; ++k) s += part[k];
+    *out = s;
+}
+
+struct Solver {
+    ihs_ctx* ctx;
+    const float* A;
+    const float* b;
+    int64_t n, d;
+    double nu;
+    float* vec[7];        // x, x_prev, g, gt, xc, gc, gtc
+    double* dsc;          // device scalars: [0] r, [1] ax2, [2] xx, [8..] partials
+    ihs_factor_t* F;
+    float* SA;
+    int64_t m;
+    int level;
+    float ms_sketch, ms_iter, ms_grad;
+};
+
+int sketch_level(Solver& S, int64_t m, int level) {
+    ihs_ctx* ctx = S.ctx;
+    if (S.F) {
+        ihs_factor_destroy(S.F);
+        S.F = nullptr;
+    }
+    void* ws = nullptr;
+    IHS_TRY(ihs_scratch(ctx, SLOT_SOLVE_SA, (size_t)m * S.d * sizeof(float), &ws));
+    S.SA = static_cast<float*>(ws);
+    IHS_CUDA_TRY(cudaEventRecord(ctx->ev[0], ctx->stream));
+    IHS_TRY(ihs_sketch_enqueue(ctx, S.A, S.n, S.d, m, ctx->p.kind, ctx->p.seed, level, S.SA));
+    IHS_TRY(ihs_factor(ctx, S.SA, m, S.d, S.nu, &S.F));   // synchronises (pivot check)
+    IHS_CUDA_TRY(cudaEventRecord(ctx->ev[1], ctx->stream));
+    IHS_CUDA_TRY(cudaEventSynchronize(ctx->ev[1]));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    S.ms_sketch += ms;
+    S.m = m;
+    S.level = level;
+    return IHS_OK;
+}
+
+// g, gt, r, ax2, xx at point `x` (vector indices into S.vec); reads back scalars.
+int evaluate(Solver& S, int ix, int ig, int igt, double* r, double* ax2, double* xx, bool need_xx) {
+    ihs_ctx* ctx = S.ctx;
+    IHS_CUDA_TRY(cudaEventRecord(ctx->ev[2], ctx->stream));
+    IHS_TRY(ihs_grad_enqueue(ctx, S.A, S.b, S.n, S.d, S.nu, S.vec[ix], S.vec[ig], S.dsc + 1));
+    IHS_CUDA_TRY(cudaEventRecord(ctx->ev[0], ctx->stream));
+    IHS_TRY(ihs_apply_enqueue(ctx, S.F, S.vec[ig], S.vec[igt], S.dsc + 0));
+    if (need_xx) {
+        const unsigned blocks = (unsigned)ceil_div64(S.d, 256);
+        k_sumsq<<<blocks, 256, 0, ctx->stream>>>(S.vec[ix], S.d, S.dsc + 8);
+        IHS_LAUNCH_CHECK();
+        k_fold<<<1, 1, 0, ctx->stream>>>(S.dsc + 8, (int)blocks, S.dsc + 2);
+        IHS_LAUNCH_CHECK();
+    }
+    IHS_CUDA_TRY(cudaEventRecord(ctx->ev[3], ctx->stream));
+    IHS_CUDA_TRY(cudaMemcpyAsync(ctx->pinned, S.dsc, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f, msg = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+    cudaEventElapsedTime(&msg, ctx->ev[2], ctx->ev[0]);
+    S.ms_iter += ms;
+    S.ms_grad += msg;
+    *r = ctx->pinned[0];
+    *ax2 = ctx->pinned[1];
+    if (need_xx) *xx = ctx->pinned[2];
+    return IHS_OK;
+}
+
+// Re-apply the (new) factor to the current gradient: gt_t and r_t.
+int reapply(Solver& S, int ig, int igt, double* r) {
+    ihs_ctx* ctx = S.ctx;
+    IHS_TRY(ihs_apply_enqueue(ctx, S.F, S.vec[ig], S.vec[igt], S.dsc + 0));
+    IHS_CUDA_TRY(cudaMemcpyAsync(ctx->pinned, S.dsc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    *r = ctx->pinned[0];
+    return IHS_OK;
+}
+
+int make_candidate(Solver& S, int ix, int igt, int ixp, double mu, double beta, int ixc, double* xx) {
+    ihs_ctx* ctx = S.ctx;
+    const unsigned blocks = (unsigned)ceil_div64(S.d, 256);
+    k_candidate<<<blocks, 256, 0, ctx->stream>>>(S.vec[ix], S.vec[igt], S.vec[ixp], S.d, (float)mu, (float)beta,
+                                                S.vec[ixc], S.dsc + 8);
+    IHS_LAUNCH_CHECK();
+    k_fold<<<1, 1, 0, ctx->stream>>>(S.dsc + 8, (int)blocks, S.dsc + 2);
+    IHS_LAUNCH_CHECK();
+    (void)xx;
+    return IHS_OK;
+}
+
+int solve_impl(Solver& S, double tol, ihs_report* rep) {
+    ihs_ctx* ctx = S.ctx;
+    const ihs_params& p = ctx->p;
+    const Params prm = make_params(p.kind, p.rho, p.eta);
+    const int64_t m_cap = p.kind == IHS_SKETCH_SRHT ? next_pow2_64(S.n) : S.n;
+    int64_t m = std::min<int64_t>(p.m_init, m_cap);
+    int level = 0;
+    while (((int64_t)1 << level) < m) ++level;
+    enum { X = 0, XP = 1, G = 2, GT = 3, XC = 4, GC = 5, GTC = 6 };
+    int ix = X, ixp = XP, ig = G, igt = GT, ixc = XC, igc = GC, igtc = GTC;
+    const size_t vbytes = (size_t)S.d * sizeof(float);
+    IHS_CUDA_TRY(cudaMemcpyAsync(S.vec[XP], S.vec[X], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+
+    IHS_TRY(sketch_level(S, m, level));
+    rep->m_levels[0] = m;
+    rep->n_levels = 1;
+    double r, ax2, xx;
+    IHS_TRY(evaluate(S, ix, ig, igt, &r, &ax2, &xx, true));
+    rep->grad_passes = 1;
+    const double r1 = r;
+    rep->r1 = r1;
+    int t = 1;
+    int status = IHS_EMAXITER;
+    while (true) {
+        if (!isfinite(r) || !isfinite(ax2)) {
+            status = IHS_ENONFINITE;
+            break;
+        }
+        if (r <= 0.0 || sqrt(2.0 * prm.Lam * r) <= tol * sqrt(ax2 + S.nu * S.nu * xx)) {
+            status = IHS_OK;
+            break;
+        }
+        if (t >= p.max_iter) break;
+        bool accepted = false;
+        if (p.variant == IHS_VARIANT_POLYAK) {
+            double rc, ax2c, xxc;
+            IHS_TRY(make_candidate(S, ix, igt, ixp, prm.mu_p, prm.beta_p, ixc, nullptr));
+            IHS_TRY(evaluate(S, ixc, igc, igtc, &rc, &ax2c, &xxc, false));
+            xxc = ctx->pinned[2];
+            rep->grad_passes++;
+            const double ratio = rc > 0.0 ? pow(rc / r1, 1.0 / t) : 0.0;
+            if (isfinite(rc) && ratio <= prm.c_p) {
+                std::swap(ixp, ix);
+                std::swap(ix, ixc);   // x_prev <- x, x <- xc, xc <- old x_prev
+                std::swap(ig, igc);
+                std::swap(igt, igtc);
+                r = rc;
+                ax2 = ax2c;
+                xx = xxc;
+                rep->accepted_polyak++;
+                accepted = true;
+            }
+        }
+        if (!accepted) {
+            double rc, ax2c, xxc;
+            IHS_TRY(make_candidate(S, ix, igt, ixp, prm.mu_gd, 0.0, ixc, nullptr));
+            IHS_TRY(evaluate(S, ixc, igc, igtc, &rc, &ax2c, &xxc, false));
+            xxc = ctx->pinned[2];
+            rep->grad_passes++;
+            if (!isfinite(rc)) {
+                status = IHS_ENONFINITE;
+                break;
+            }
+            const double ratio = rc / r;
+            if (ratio <= prm.c_gd || S.m >= m_cap) {
+                if (!(ratio <= prm.c_gd)) rep->flags |= 1;
+                std::swap(ixp, ix);
+                std::swap(ix, ixc);
+                std::swap(ig, igc);
+                std::swap(igt, igtc);
+                r = rc;
+                ax2 = ax2c;
+                xx = xxc;
+                rep->accepted_gd++;
+                accepted = true;
+            } else if (p.floor > 0.0 && r <= p.floor * p.floor * r1) {
+                rep->flags |= 2;
+                status = IHS_OK;
+                break;
+            } else {
+                rep->rejected++;
+                const int64_t m_new = std::min<int64_t>(2 * S.m, m_cap);
+                IHS_TRY(sketch_level(S, m_new, S.level + 1));
+                if (rep->n_levels < IHS_REPORT_MAX_LEVELS) rep->m_levels[rep->n_levels] = m_new;
+                rep->n_levels++;
+                IHS_TRY(reapply(S, ig, igt, &r));
+                continue;
+            }
+        }
+        ++t;
+    }
+    if (ix != X) {
+        IHS_CUDA_TRY(cudaMemcpyAsync(S.vec[X], S.vec[ix], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    rep->status = status;
+    rep->iterations = t;
+    rep->m_final = S.m;
+    rep->r_final = r;
+    rep->axnorm_final = sqrt(ax2 + S.nu * S.nu * xx);
+    rep->ms_sketch = S.ms_sketch;
+    rep->ms_iterate = S.ms_iter;
+    rep->ms_grad = S.ms_grad;
+    return status;
+}
+
+}  // namespace
+
+extern "C" int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu, double tol,
+                         float* x, ihs_report* rep_h) {
+    if (!ctx || !A || !b || !x) return IHS_EINVAL;
+    if (n < 1 || d < 1 || n < d || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
+    if (!(tol > 0.0)) tol = ctx->p.tol;
+    ihs_report rep;
+    memset(&rep, 0, sizeof(rep));
+    Solver S;
+    memset(&S, 0, sizeof(S));
+    S.ctx = ctx;
+    S.A = A;
+    S.b = b;
+    S.n = n;
+    S.d = d;
+    S.nu = nu;
+    void* ws = nullptr;
+    const size_t vb = ((size_t)d * sizeof(float) + 255) & ~(size_t)255;
+    IHS_TRY(ihs_scratch(ctx, SLOT_SOLVE, 7 * vb + 8192 * sizeof(double), &ws));
+    char* base = static_cast<char*>(ws);
+    S.vec[0] = x;
+    for (int i = 1; i < 7; ++i) S.vec[i] = reinterpret_cast<float*>(base + i * vb);
+    S.dsc = reinterpret_cast<double*>(base + 7 * vb);
+    const int st = solve_impl(S, tol, &rep);
+    if (S.F) ihs_factor_destroy(S.F);
+    if (rep_h) *rep_h = rep;
+    if (st == IHS_OK || st == IHS_EMAXITER) {
+        const int s2 = ihs_check_status(ctx);
+        if (s2 != IHS_OK) return s2;
+    }
+    return st;
+}

@@ -1,0 +1,223 @@
+"""Thin Python binding of the C ABI in include/ihs.h (argument marshalling only).
+
+Every computation happens in libihs.so (hand-written CUDA for sm_103a).  There is
+no fallback: if the library is missing, `load()` raises.  Tensors are torch CUDA
+tensors; their device pointers are passed through unchanged.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libihs.so")
+
+IHS_OK, IHS_EINVAL, IHS_ENOMEM, IHS_ENOTPD = 0, -1, -2, -3
+IHS_ENONFINITE, IHS_EMCAP, IHS_EMAXITER, IHS_ETIMEOUT, IHS_ECUDA = -4, -5, -6, -7, -8
+SKETCH_SRHT, SKETCH_GAUSS = 0, 1
+VARIANT_GD, VARIANT_POLYAK = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+REPORT_MAX_LEVELS = 40
+
+STATUS_NAMES = {0: "IHS_OK", -1: "IHS_EINVAL", -2: "IHS_ENOMEM", -3: "IHS_ENOTPD", -4: "IHS_ENONFINITE",
+                -5: "IHS_EMCAP", -6: "IHS_EMAXITER", -7: "IHS_ETIMEOUT", -8: "IHS_ECUDA"}
+KINDS = {"srht": SKETCH_SRHT, "gauss": SKETCH_GAUSS}
+VARIANTS = {"gd": VARIANT_GD, "polyak": VARIANT_POLYAK}
+PRECISIONS = {"fp32": PREC_FP32, "bf16": PREC_BF16, "fp8": PREC_FP8}
+
+
+class IHSError(RuntimeError):
+    def __init__(self, func, status, detail=""):
+        self.status = status
+        super().__init__("%s returned %s%s" % (func, STATUS_NAMES.get(status, status),
+                                              (": " + detail) if detail else ""))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("variant", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("m_init", ctypes.c_int64), ("rho", ctypes.c_double),
+                ("eta", ctypes.c_double), ("tol", ctypes.c_double), ("floor", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("grad_passes", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("accepted_polyak", ctypes.c_int32),
+                ("accepted_gd", ctypes.c_int32), ("rejected", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("m_final", ctypes.c_int64), ("m_levels", ctypes.c_int64 * REPORT_MAX_LEVELS),
+                ("r1", ctypes.c_double), ("r_final", ctypes.c_double), ("axnorm_final", ctypes.c_double),
+                ("ms_sketch", ctypes.c_double), ("ms_iterate", ctypes.c_double), ("ms_grad", ctypes.c_double)]
+
+    def levels(self):
+        return [int(self.m_levels[i]) for i in range(min(self.n_levels, REPORT_MAX_LEVELS))]
+
+
+_vp, _i64, _i32, _u64, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+_SIGNATURES = {
+    "ihs_version": ([], ctypes.c_char_p),
+    "ihs_last_error": ([], ctypes.c_char_p),
+    "ihs_kernel_launches": ([], ctypes.c_int64),
+    "ihs_params_default": ([ctypes.POINTER(Params)], ctypes.c_int),
+    "ihs_ctx_create": ([ctypes.POINTER(_vp), _vp, ctypes.POINTER(Params)], ctypes.c_int),
+    "ihs_ctx_destroy": ([_vp], ctypes.c_int),
+    "ihs_ctx_set_params": ([_vp, ctypes.POINTER(Params)], ctypes.c_int),
+    "ihs_srht_signs": ([_vp, _i64, _u64, _i32, _vp], ctypes.c_int),
+    "ihs_srht_rows": ([_vp, _i64, _i64, _u64, _i32, _vp], ctypes.c_int),
+    "ihs_sketch": ([_vp, _vp, _i64, _i64, _i64, _i32, _u64, _i32, _vp], ctypes.c_int),
+    "ihs_factor": ([_vp, _vp, _i64, _i64, _dbl, ctypes.POINTER(_vp)], ctypes.c_int),
+    "ihs_factor_destroy": ([_vp], ctypes.c_int),
+    "ihs_apply_hinv": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
+    "ihs_grad": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
+    "ihs_solve": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libihs.so (built by paper_2006_05874_gb300.build.build()); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libihs.so not built (%s); run paper_2006_05874_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(func, status):
+    if status != IHS_OK:
+        detail = ""
+        if status == IHS_ECUDA:
+            detail = _lib.ihs_last_error().decode()
+        raise IHSError(func, status, detail)
+    return status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def version():
+    return load().ihs_version().decode()
+
+
+def kernel_launches():
+    """Kernels launched by the library so far in this process."""
+    return int(load().ihs_kernel_launches())
+
+
+def default_params(**kw):
+    p = Params()
+    load().ihs_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "kind":
+            v = KINDS.get(v, v)
+        elif k == "variant":
+            v = VARIANTS.get(v, v)
+        elif k == "precision":
+            v = PRECISIONS.get(v, v)
+        setattr(p, k, v)
+    return p
+
+
+class Factor:
+    def __init__(self, ctx, handle, SA):
+        self.ctx, self.handle, self.SA = ctx, handle, SA
+
+    def apply_hinv(self, g, gt, want_r=True):
+        r = ctypes.c_double(0.0)
+        _check("ihs_apply_hinv", _lib.ihs_apply_hinv(self.ctx.handle, self.handle, _ptr(g), _ptr(gt),
+                                                     ctypes.byref(r) if want_r else None))
+        return r.value if want_r else None
+
+    def destroy(self):
+        if self.handle:
+            _lib.ihs_factor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Context:
+    """An ihs_ctx bound to a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, params=None, stream=None, **kw):
+        import torch
+
+        lib = load()
+        self.params = params if params is not None else default_params(**kw)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check("ihs_ctx_create", lib.ihs_ctx_create(ctypes.byref(h), ctypes.c_void_p(stream.cuda_stream),
+                                                    ctypes.byref(self.params)))
+        self.handle = h
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            if k == "kind":
+                v = KINDS.get(v, v)
+            elif k == "variant":
+                v = VARIANTS.get(v, v)
+            elif k == "precision":
+                v = PRECISIONS.get(v, v)
+            setattr(self.params, k, v)
+        _check("ihs_ctx_set_params", _lib.ihs_ctx_set_params(self.handle, ctypes.byref(self.params)))
+
+    def srht_signs(self, n_pad, seed, level, eps):
+        _check("ihs_srht_signs", _lib.ihs_srht_signs(self.handle, n_pad, seed, level, _ptr(eps)))
+
+    def srht_rows(self, n_pad, m, seed, level, rows):
+        _check("ihs_srht_rows", _lib.ihs_srht_rows(self.handle, n_pad, m, seed, level, _ptr(rows)))
+
+    def sketch(self, A, m, kind, seed, level, SA):
+        n, d = A.shape
+        _check("ihs_sketch", _lib.ihs_sketch(self.handle, _ptr(A), n, d, m, KINDS.get(kind, kind), seed, level,
+                                             _ptr(SA)))
+
+    def factor(self, SA, nu):
+        m, d = SA.shape
+        h = ctypes.c_void_p()
+        _check("ihs_factor", _lib.ihs_factor(self.handle, _ptr(SA), m, d, float(nu), ctypes.byref(h)))
+        return Factor(self, h, SA)
+
+    def grad(self, A, b, nu, x, g, want_axnorm2=True):
+        n, d = A.shape
+        ax2 = ctypes.c_double(0.0)
+        _check("ihs_grad", _lib.ihs_grad(self.handle, _ptr(A), _ptr(b), n, d, float(nu), _ptr(x), _ptr(g),
+                                         ctypes.byref(ax2) if want_axnorm2 else None))
+        return ax2.value if want_axnorm2 else None
+
+    def solve(self, A, b, nu, x, tol=0.0, raise_on_maxiter=False):
+        n, d = A.shape
+        rep = Report()
+        st = _lib.ihs_solve(self.handle, _ptr(A), _ptr(b), n, d, float(nu), float(tol), _ptr(x), ctypes.byref(rep))
+        if st != IHS_OK and (st != IHS_EMAXITER or raise_on_maxiter):
+            _check("ihs_solve", st)
+        return rep
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            _lib.ihs_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -19,3 +19,21 @@ def lib():
     from paper_2006_05874_gb300 import ihs
 
     return ihs.load()
+
+
+@pytest.fixture(scope="session")
+def torch_cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test selected but no CUDA device is visible")
+    return torch
+
+
+@pytest.fixture()
+def ctx(lib, torch_cuda):
+    from paper_2006_05874_gb300 import ihs
+
+    c = ihs.Context()
+    yield c
+    c.destroy()

@@ -111,3 +111,9 @@ def test_gaussian_uniforms_in_range():
     u2 = rng._uniform_closed0(w)
     assert u1.min() > 0 and u1.max() == 1.0
     assert u2.min() == 0.0 and u2.max() < 1.0
+
+
+def test_gaussian_rows_match_full():
+    full = rng.gaussian_z(11, 200, seed=8, level=2)
+    rows = [0, 3, 5, 10]
+    assert np.array_equal(rng.gaussian_z_rows(rows, 200, seed=8, level=2), full[rows])
