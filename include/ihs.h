@@ -165,6 +165,33 @@ int ihs_apply_hinv(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* g
 int ihs_grad(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
              double nu, const float* x, float* g, double* axnorm2_h);
 
+/* Allocation-free variant of ihs_grad, for callers that cannot let a library
+ * call cudaMalloc/cudaFree: code whose device memory belongs to another
+ * allocator (a framework's caching pool, a fixed arena sized up front) and
+ * latency-critical loops that must not block in cudaMalloc/cudaFree, which
+ * synchronise the device.  The paper has no counterpart; this is a library
+ * facility around its gradient of Eq. 1.
+ *
+ * Same result as ihs_grad (same kernels, same fixed-order reduction), but it
+ * takes no context and allocates nothing: its scratch is a file-scope device
+ * array of about 10 MiB (partials of at most 160 CTAs x 8192 columns) that
+ * every GPU which loads the library holds until the process exits.
+ *  - stream: a cudaStream_t (NULL = legacy default stream) on the current
+ *    device.  Asynchronous: returns once the work is enqueued.
+ *  - A (n x d), b (n), x (d), g (d): device FP32; axnorm2: device double
+ *    receiving ||A x||^2, or NULL.
+ *  - Limits: 4 <= d <= 8192, d % 4 == 0, n >= 1, A and x 16-byte aligned,
+ *    nu >= 0 and finite; anything else returns IHS_EINVAL before any work.
+ *  - The first call on a device looks up the device address of the scratch
+ *    array (cudaGetSymbolAddress, once per device, with that device current);
+ *    make that first call before any stream capture.
+ *  - Every call on a device shares the one scratch array (each call rewrites
+ *    it fully and clears its status word first): calls that overlap on the
+ *    GPU, e.g. from two streams at once, race and must be serialised.
+ *  - If the kernel's bounded wait ever gives up, g and *axnorm2 are NaN. */
+int ihs_grad_noalloc(void* stream, const float* A, const float* b, int64_t n, int64_t d,
+                     double nu, const float* x, float* g, double* axnorm2);
+
 /* ---- the solver ---------------------------------------------------------- */
 /* Adaptive IHS (Algorithm 1 or its gradient-only variant, per the context's
  * parameters; `tol` overrides params.tol when > 0).  x (device, d): on entry

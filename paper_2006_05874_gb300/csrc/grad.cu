@@ -449,3 +449,144 @@ extern "C" int ihs_grad(ihs_ctx* ctx, const float* A, const float* b, int64_t n,
     }
     return ihs_check_status(ctx);
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free gradient pass (ihs_grad_noalloc).
+//
+// Some callers cannot let a library call cudaMalloc or cudaFree: code whose
+// device memory is owned by another allocator (a framework's caching pool or
+// a fixed arena sized up front, where a hidden allocation breaks the memory
+// budget), and latency-critical loops that must not block in cudaMalloc /
+// cudaFree, which synchronise the device.  This variant of the gradient pass
+// needs no context and allocates nothing: its scratch (the per-CTA partial
+// sums and a status word) lives in a file-scope __device__ array of fixed
+// size, which every GPU that loads the library holds until the process exits.
+#include <mutex>
+
+#define IHS_NOALLOC_MAX_CTAS 160
+#define IHS_NOALLOC_MAX_D 8192
+
+namespace {
+
+constexpr size_t kNoallocPartBytes = (size_t)IHS_NOALLOC_MAX_CTAS * IHS_NOALLOC_MAX_D * sizeof(float2);
+constexpr size_t kNoallocAx2Bytes = (size_t)IHS_NOALLOC_MAX_CTAS * sizeof(double);
+constexpr size_t kNoallocBytes = kNoallocPartBytes + kNoallocAx2Bytes + 256;   // + status word
+
+// ~10 MiB: 160 x 8192 float2 partials, 160 double partials, a status word.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+struct NoallocDevice {
+    unsigned char* scratch;   // device address of g_noalloc_scratch on this device
+    int sm_count;
+    bool ready;
+};
+NoallocDevice g_noalloc_dev[128];
+std::mutex g_noalloc_mu;
+
+// Once per device, with that device current: the device address of the
+// scratch array (the host-side symbol is only a stand-in) and the SM count.
+int noalloc_setup(NoallocDevice** out) {
+    int dev = 0;
+    IHS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return IHS_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocDevice& nd = g_noalloc_dev[dev];
+    if (!nd.ready) {
+        void* ptr = nullptr;
+        IHS_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        int sms = 0;
+        IHS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        nd.scratch = static_cast<unsigned char*>(ptr);
+        nd.sm_count = sms;
+        nd.ready = true;
+    }
+    *out = &nd;
+    return IHS_OK;
+}
+
+// Fixed-order FP64 reduction of the partials, as k_grad_reduce, except that a
+// gradient pass whose bounded wait gave up (status word non-zero) yields NaN.
+__global__ void k_grad_reduce_noalloc(const float2* __restrict__ part, const double* __restrict__ part_ax2, int G,
+                                      int d, double nu2, const float* __restrict__ x, float* __restrict__ g,
+                                      double* __restrict__ axnorm2, const unsigned* __restrict__ status) {
+    __shared__ double sm[8][33];
+    const bool failed = *status != 0u;
+    const int cx = threadIdx.x & 31, sy = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + cx;
+    double s = 0.0;
+    if (col < d) {
+        for (int gi = sy; gi < G; gi += 8) {
+            const float2 v = part[(size_t)gi * d + col];
+            s += (double)v.x + (double)v.y;
+        }
+    }
+    sm[sy][cx] = s;
+    __syncthreads();
+    if (sy == 0 && col < d) {
+        double t = sm[0][cx];
+        for (int k = 1; k < 8; ++k) t += sm[k][cx];
+        g[col] = failed ? __int_as_float(0x7fc00000) : (float)(t + nu2 * (double)x[col]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && axnorm2 != nullptr) {
+        double t = 0.0;
+        for (int gi = 0; gi < G; ++gi) t += part_ax2[gi];
+        *axnorm2 = failed ? __longlong_as_double(0x7ff8000000000000ll) : t;
+    }
+}
+
+template <int TPR, int CPT, int RT>
+int launch_fast_noalloc(cudaStream_t stream, int sm_count, const float* A, const float* b, const float* x,
+                        int64_t n, int d, float2* part, double* part_ax2, unsigned* status, int* G_out) {
+    constexpr int RP = kThreads / TPR;
+    constexpr int R = RT * RP;
+    constexpr int W = TPR / 32;
+    const size_t stage_bytes = (size_t)R * d * sizeof(float);
+    const size_t budget = 200 * 1024;
+    int stages = 8;
+    while (stages > 2 && FastLayout(stages, R, W, d).total > budget) --stages;
+    size_t smem = FastLayout(stages, R, W, d).total;
+    if (smem > budget || stage_bytes * stages > budget) return IHS_EINVAL;
+    const size_t comb = (size_t)RP * d * sizeof(Acc2);
+    if (smem < comb) smem = comb;
+    const int64_t ntiles = ceil_div64(n, R);
+    int64_t G = std::min<int64_t>(std::min<int64_t>(sm_count, IHS_NOALLOC_MAX_CTAS), ntiles);
+    auto kern = k_grad_fast<TPR, CPT, RT>;
+    IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)G, kThreads, smem, stream>>>(A, b, x, n, d, ntiles, stages, part, part_ax2, status);
+    IHS_LAUNCH_CHECK();
+    *G_out = (int)G;
+    return IHS_OK;
+}
+
+}  // namespace
+
+extern "C" int ihs_grad_noalloc(void* stream_v, const float* A, const float* b, int64_t n, int64_t d, double nu,
+                                const float* x, float* g, double* axnorm2) {
+    if (!A || !b || !x || !g) return IHS_EINVAL;
+    if (n < 1 || d < 4 || d > IHS_NOALLOC_MAX_D || d % 4 != 0) return IHS_EINVAL;
+    if (!(nu >= 0.0) || !isfinite(nu)) return IHS_EINVAL;
+    if ((uintptr_t)A % 16 != 0 || (uintptr_t)x % 16 != 0) return IHS_EINVAL;
+    NoallocDevice* nd = nullptr;
+    IHS_TRY(noalloc_setup(&nd));
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    float2* part = reinterpret_cast<float2*>(nd->scratch);
+    double* part_ax2 = reinterpret_cast<double*>(nd->scratch + kNoallocPartBytes);
+    unsigned* status = reinterpret_cast<unsigned*>(nd->scratch + kNoallocPartBytes + kNoallocAx2Bytes);
+    // The status word must start at zero; the partials are fully rewritten.
+    IHS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned), stream));
+    const FastCfg c = pick_fast((int)d);
+    int G = 0;
+    int st;
+    if (c.tpr == 32) st = launch_fast_noalloc<32, 1, 8>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
+    else if (c.tpr == 64) st = launch_fast_noalloc<64, 1, 8>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
+    else if (c.tpr == 128) st = launch_fast_noalloc<128, 1, 8>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
+    else if (c.cpt == 1) st = launch_fast_noalloc<256, 1, 8>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
+    else if (c.cpt == 2) st = launch_fast_noalloc<256, 2, 4>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
+    else if (c.cpt == 4) st = launch_fast_noalloc<256, 4, 2>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
+    else st = launch_fast_noalloc<256, 8, 1>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
+    IHS_TRY(st);
+    k_grad_reduce_noalloc<<<(unsigned)ceil_div64(d, 32), 256, 0, stream>>>(part, part_ax2, G, (int)d, nu * nu, x, g,
+                                                                          axnorm2, status);
+    IHS_LAUNCH_CHECK();
+    return IHS_OK;
+}

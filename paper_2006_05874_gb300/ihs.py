@@ -67,6 +67,7 @@ _SIGNATURES = {
     "ihs_apply_hinv": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
     "ihs_grad": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
     "ihs_solve": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
+    "ihs_grad_noalloc": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, _vp], ctypes.c_int),
 }
 
 _lib = None
@@ -114,6 +115,17 @@ def version():
 def kernel_launches():
     """Kernels launched by the library so far in this process."""
     return int(load().ihs_kernel_launches())
+
+
+def grad_noalloc(A, b, nu, x, g, axnorm2=None, stream=None):
+    """ihs_grad_noalloc: the gradient pass without a context and without any
+    allocation (scratch in a fixed device array; see include/ihs.h)."""
+    import torch
+
+    stream = torch.cuda.current_stream() if stream is None else stream
+    n, d = A.shape
+    _check("ihs_grad_noalloc", load().ihs_grad_noalloc(ctypes.c_void_p(stream.cuda_stream), _ptr(A), _ptr(b), n, d,
+                                                       float(nu), _ptr(x), _ptr(g), _ptr(axnorm2)))
 
 
 def default_params(**kw):
