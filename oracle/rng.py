@@ -11,7 +11,9 @@ source:
 
 Counter layout (Philox4x32-10, key = (seed_lo, seed_hi)):
 
-    stream SIGNS = 0 : counter (i_lo, i_hi, level, 0)     -> eps_i = +1 if bit0(w0)==0 else -1
+    stream SIGNS = 0 : counter (k_lo, k_hi, level, 0), k = i // 128 -> the 128 output
+                       bits (w0 bit 0 .. w3 bit 31) give eps_{128k} .. eps_{128k+127};
+                       eps_i = +1 if bit (i mod 128) is 0 else -1
     stream ROWS  = 1 : counter (i_lo, i_hi, level, 1)     -> key_i = (w1 << 32) | w0
     stream GAUSS = 2 : counter (i, q, level, 2), q = j//4 -> z[4q .. 4q+3, i] by Box-Muller
 
@@ -40,11 +42,16 @@ def _split_index(i):
 
 
 def signs(n_pad, seed, level):
-    """Rademacher vector eps in {-1, +1}^n_pad (int8)."""
+    """Rademacher vector eps in {-1, +1}^n_pad (int8): bit (i mod 128) of the
+    128-bit Philox output for counter i // 128."""
     k0, k1 = seed_key(seed)
-    lo, hi = _split_index(np.arange(n_pad, dtype=np.uint64))
-    w0, _, _, _ = philox4x32_10(lo, hi, np.uint64(level), np.uint64(SIGNS), k0, k1)
-    return (1 - 2 * (w0 & np.uint64(1)).astype(np.int64)).astype(np.int8)
+    blocks = (n_pad + 127) // 128
+    lo, hi = _split_index(np.arange(blocks, dtype=np.uint64))
+    words = philox4x32_10(lo, hi, np.uint64(level), np.uint64(SIGNS), k0, k1)
+    i = np.arange(n_pad, dtype=np.int64)
+    word = np.stack(words, axis=1)[i // 128, (i % 128) // 32]
+    bit = (word >> (i % 32).astype(np.uint64)) & np.uint64(1)
+    return (1 - 2 * bit.astype(np.int64)).astype(np.int8)
 
 
 def row_keys(n_pad, seed, level):

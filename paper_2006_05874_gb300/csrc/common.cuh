@@ -68,9 +68,11 @@ struct ihs_factor {
     int64_t m, d, k;      // k = m (Woodbury) or d (direct)
     double nu;
     int woodbury;
-    double* L;            // k x k lower Cholesky factor (row-major, FP64)
-    double* Linv;         // k x k inverse of L (lower, FP64)
-    double* work;         // 3 k doubles + d doubles of apply scratch + reduction slots
+    double* L;            // k x k: K, then its lower Cholesky factor (row-major, FP64)
+    double* W;            // inverses of the 64 x 64 diagonal blocks of L (FP64)
+    float* X;             // k x k lower inverse L^{-1} (FP32)
+    float* XT;            // its transpose (upper)
+    double* work;         // apply scratch vectors and reduction slots
 };
 
 int ihs_scratch(ihs_ctx* ctx, int slot, size_t bytes, void** out);
@@ -110,9 +112,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 enum { STREAM_SIGNS = 0, STREAM_ROWS = 1, STREAM_GAUSS = 2, STREAM_PROBE = 3 };
 
+// Sign bits of rows 128k .. 128k+127: one Philox call, bit (i mod 128) of
+// (w0, w1, w2, w3) is the sign bit of row i (1 -> eps = -1).
+__device__ __forceinline__ uint4 srht_sign_block(uint64_t k, uint32_t level, uint32_t k0, uint32_t k1) {
+    return philox4x32_10(make_uint4((uint32_t)k, (uint32_t)(k >> 32), level, STREAM_SIGNS), k0, k1);
+}
+
 __device__ __forceinline__ int srht_sign_bit(uint64_t i, uint32_t level, uint32_t k0, uint32_t k1) {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), level, STREAM_SIGNS), k0, k1);
-    return (int)(w.x & 1u);   // 1 -> eps = -1
+    const uint4 w = srht_sign_block(i >> 7, level, k0, k1);
+    const uint32_t sel = (uint32_t)(i >> 5) & 3u;
+    const uint32_t word = sel == 0 ? w.x : (sel == 1 ? w.y : (sel == 2 ? w.z : w.w));
+    return (int)((word >> (i & 31u)) & 1u);
 }
 
 __device__ __forceinline__ uint64_t srht_row_key(uint64_t i, uint32_t level, uint32_t k0, uint32_t k1) {

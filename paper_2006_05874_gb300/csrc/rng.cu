@@ -18,6 +18,7 @@ __global__ void k_signs(int64_t n_pad, uint32_t level, uint32_t k0, uint32_t k1,
 }
 
 // sel[0] = prefix of K* found so far, sel[1] = rank still needed (1-based).
+// hist[0..65536) per-digit counts, hist[65536..65600) per-1024-digit sums.
 __global__ void k_hist16(int64_t n_pad, uint32_t level, uint32_t k0, uint32_t k1, int pass,
                          const unsigned long long* __restrict__ sel, unsigned* __restrict__ hist) {
     const int shift = 48 - 16 * pass;
@@ -26,48 +27,58 @@ __global__ void k_hist16(int64_t n_pad, uint32_t level, uint32_t k0, uint32_t k1
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = srht_row_key((uint64_t)i, level, k0, k1);
         const bool match = (pass == 0) || ((key >> (shift + 16)) == (prefix >> (shift + 16)));
-        if (match) atomicAdd(&hist[(key >> shift) & 0xFFFFu], 1u);
+        if (match) {
+            const unsigned digit = (unsigned)((key >> shift) & 0xFFFFu);
+            atomicAdd(&hist[digit], 1u);
+            atomicAdd(&hist[65536 + (digit >> 10)], 1u);
+        }
     }
 }
 
-// One CTA of 1024 threads: choose the digit holding the needed rank, extend the
-// prefix, reduce the rank, clear the histogram for the next pass.
+// One CTA of 1024 threads: choose the digit holding the needed rank (first the
+// 1024-digit bucket from the 64 coarse sums, then the digit inside it), extend
+// the prefix, reduce the rank, clear the histogram for the next pass.
 __global__ void __launch_bounds__(1024) k_pick16(int pass, unsigned long long* __restrict__ sel,
                                                  unsigned* __restrict__ hist) {
-    __shared__ unsigned long long part[1024];
-    __shared__ int found;
+    __shared__ unsigned long long fine[1024];
+    __shared__ int bucket;
+    __shared__ unsigned long long before_bucket;
     const int tid = threadIdx.x;
     const int shift = 48 - 16 * pass;
-    unsigned long long s = 0;
-    for (int k = 0; k < 64; ++k) s += hist[tid * 64 + k];
-    part[tid] = s;
-    if (tid == 0) found = -1;
-    __syncthreads();
-    // inclusive scan (Hillis-Steele, fixed order)
-    for (int off = 1; off < 1024; off <<= 1) {
-        const unsigned long long v = tid >= off ? part[tid - off] : 0ull;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
-    }
     const unsigned long long need = sel[1];
-    const unsigned long long before = tid ? part[tid - 1] : 0ull;
-    if (before < need && need <= part[tid]) found = tid;
-    __syncthreads();
-    if (tid == found) {
-        unsigned long long acc = before;
-        for (int k = 0; k < 64; ++k) {
-            const unsigned h = hist[tid * 64 + k];
+    if (tid == 0) {
+        unsigned long long acc = 0;
+        int b = 63;
+        for (int i = 0; i < 64; ++i) {
+            const unsigned long long h = hist[65536 + i];
             if (acc + h >= need) {
-                sel[0] |= (unsigned long long)(tid * 64 + k) << shift;
-                sel[1] = need - acc;
+                b = i;
                 break;
             }
             acc += h;
         }
+        bucket = b;
+        before_bucket = acc;
     }
     __syncthreads();
-    for (int k = 0; k < 64; ++k) hist[tid * 64 + k] = 0u;
+    const int b = bucket;
+    fine[tid] = hist[b * 1024 + tid];
+    __syncthreads();
+    // inclusive scan of the bucket's 1024 digits (Hillis-Steele, fixed order)
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned long long v = tid >= off ? fine[tid - off] : 0ull;
+        __syncthreads();
+        fine[tid] += v;
+        __syncthreads();
+    }
+    const unsigned long long incl = before_bucket + fine[tid];
+    const unsigned long long excl = before_bucket + (tid ? fine[tid - 1] : 0ull);
+    __syncthreads();
+    if (excl < need && need <= incl) {
+        sel[0] |= (unsigned long long)(b * 1024 + tid) << shift;
+        sel[1] = need - excl;
+    }
+    for (int k = tid; k < 65536 + 64; k += 1024) hist[k] = 0u;
 }
 
 constexpr int kCompactBlock = 1024;
@@ -179,7 +190,7 @@ int ihs_rows_enqueue(ihs_ctx* ctx, int64_t n_pad, int64_t m, uint64_t seed, int3
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const int64_t nblocks = ceil_div64(n_pad, kCompactBlock);
     void* ws = nullptr;
-    const size_t hist_bytes = 65536 * sizeof(unsigned);
+    const size_t hist_bytes = (65536 + 64) * sizeof(unsigned);
     const size_t cnt_bytes = (size_t)nblocks * sizeof(uint2);
     IHS_TRY(ihs_scratch(ctx, SLOT_SELECT, hist_bytes + 2 * cnt_bytes + 64, &ws));
     unsigned* hist = static_cast<unsigned*>(ws);

@@ -98,6 +98,116 @@ k_srht_fwht(const float* __restrict__ A, int64_t n, int d, int64_t m, int Q, int
     }
 }
 
+// Radix-32 register FWHT for blocks of Q = 1024 rows (n_pad >= 1024).
+// CTA = 512 threads = 16 columns x 32 "lanes" ql; thread (c, ql) holds rows
+// 32k + ql (k = 0..31) of its column in registers: a 32-point WHT over k, a
+// padded shared-memory transpose, a 32-point WHT over ql (H_1024 = H_32 (x)
+// H_32), then the selected rows are accumulated with the sign of their high
+// index bits against the block index p.
+constexpr int kR32C = 16, kR32T = 512, kR32Stride = 528;   // 528 = 33 x 16: conflict-free transposes
+
+__device__ __forceinline__ void wht32(float (&v)[32]) {
+#pragma unroll
+    for (int h = 1; h < 32; h <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if ((i & h) == 0) {
+                const float a = v[i], b = v[i + h];
+                v[i] = __fadd_rn(a, b);
+                v[i + h] = __fsub_rn(a, b);
+            }
+        }
+    }
+}
+
+__host__ __device__ inline size_t r32_smem_bytes(int64_t m, int acc_smem) {
+    // the row list and the accumulators live in shared memory only in smem mode
+    return (size_t)32 * kR32Stride * sizeof(float) + 32 * sizeof(uint32_t) +
+           (acc_smem ? (size_t)((m + 3) & ~3ll) * sizeof(int32_t) + (size_t)m * kR32C * sizeof(float) : 0);
+}
+
+__global__ void __launch_bounds__(kR32T)
+k_srht_r32(const float* __restrict__ A, int64_t n, int d, int64_t m, int64_t P, int PG,
+           const int32_t* __restrict__ rows, uint32_t level, uint32_t k0, uint32_t k1, int acc_smem,
+           float* __restrict__ out /* PG x m x d partials */) {
+    extern __shared__ __align__(16) float sm[];
+    float* T = sm;                                                    // 32 x 528
+    uint32_t* sbits = reinterpret_cast<uint32_t*>(T + 32 * kR32Stride);   // 32 words = 1024 sign bits
+    int32_t* srows = reinterpret_cast<int32_t*>(sbits + 32);             // m selected rows (smem mode)
+    float* acc = reinterpret_cast<float*>(srows + ((m + 3) & ~3ll));     // m x 16 (smem mode)
+    const int32_t* rinfo = acc_smem ? srows : rows;
+    const int tid = threadIdx.x;
+    const int c = tid & 15, ql = tid >> 4;
+    const int col0 = blockIdx.x * kR32C;
+    const int col = col0 + c;
+    const bool colok = col < d;
+    const int pg = blockIdx.y;
+    const int64_t p0 = (int64_t)pg * P / PG, p1 = (int64_t)(pg + 1) * P / PG;
+    float* outp = out + (size_t)pg * m * d;
+
+    if (acc_smem) {
+        for (int64_t j = tid; j < m; j += kR32T) srows[j] = rows[j];
+        for (int64_t e = tid; e < m * kR32C; e += kR32T) acc[e] = 0.f;
+    } else {
+        for (int64_t e = tid; e < m * kR32C; e += kR32T) {
+            const int cc = (int)(e & 15);
+            if (col0 + cc < d) outp[(e >> 4) * d + col0 + cc] = 0.f;
+        }
+    }
+    for (int64_t p = p0; p < p1; ++p) {
+        if (tid < 8) {
+            const uint4 w = srht_sign_block((uint64_t)p * 8 + tid, level, k0, k1);
+            sbits[4 * tid + 0] = w.x;
+            sbits[4 * tid + 1] = w.y;
+            sbits[4 * tid + 2] = w.z;
+            sbits[4 * tid + 3] = w.w;
+        }
+        float v[32];
+        const int64_t base = p * 1024 + ql;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const int64_t row = base + 32 * k;
+            v[k] = (colok && row < n) ? __ldg(A + row * d + col) : 0.f;
+        }
+        __syncthreads();   // signs ready; previous block's gather done with T
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            // row 32k + ql of the block: word k, bit ql
+            if ((sbits[k] >> ql) & 1u) v[k] = -v[k];
+        }
+        wht32(v);   // over k (high five index bits)
+#pragma unroll
+        for (int k = 0; k < 32; ++k) T[k * kR32Stride + ql * 16 + c] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < 32; ++l) v[l] = T[ql * kR32Stride + l * 16 + c];
+        wht32(v);   // over the low five index bits; thread now holds Y[32 ql + l]
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < 32; ++l) T[ql * kR32Stride + l * 16 + c] = v[l];
+        __syncthreads();
+        for (int64_t e = tid; e < m * kR32C; e += kR32T) {
+            const int cc = (int)(e & 15);
+            const uint32_t r = (uint32_t)rinfo[e >> 4];
+            const uint32_t lo = r & 1023u;
+            const float val = T[(lo >> 5) * kR32Stride + (lo & 31u) * 16 + cc];
+            const float sv = (__popcll((uint64_t)(r >> 10) & (uint64_t)p) & 1) ? -val : val;
+            if (acc_smem) {
+                acc[e] += sv;
+            } else if (col0 + cc < d) {
+                outp[(e >> 4) * d + col0 + cc] += sv;
+            }
+        }
+    }
+    if (acc_smem) {
+        __syncthreads();
+        for (int64_t e = tid; e < m * kR32C; e += kR32T) {
+            const int cc = (int)(e & 15);
+            if (col0 + cc < d) outp[(e >> 4) * d + col0 + cc] = acc[e];
+        }
+    }
+}
+
 // out[e] = scale * sum_k part[k][e] in a fixed order (FP64).
 __global__ void k_reduce_parts(const float* __restrict__ part, int K, int64_t count, double scale,
                                float* __restrict__ out) {
@@ -211,16 +321,35 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
     void* pws = nullptr;
     IHS_TRY(ihs_scratch(ctx, SLOT_SKETCH_PART, (size_t)PG * m * d * sizeof(float), &pws));
     float* part = static_cast<float*>(pws);
-    const size_t base = ((size_t)Q * (kSrhtC + 1) + Q) * sizeof(float);
-    const size_t acc_bytes = (size_t)m * kSrhtC * sizeof(float);
-    const int acc_in_smem = (base + acc_bytes <= 200 * 1024) ? 1 : 0;
-    const size_t smem = base + (acc_in_smem ? acc_bytes : 0);
-    IHS_CUDA_TRY(cudaFuncSetAttribute(k_srht_fwht, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)CT, (unsigned)PG);
-    k_srht_fwht<<<grid, kSrhtThreads, smem, ctx->stream>>>(A, n, (int)d, m, Q, logQ, P, (int)PG, rows,
-                                                          (uint32_t)level, (uint32_t)seed,
-                                                          (uint32_t)(seed >> 32), acc_in_smem, part);
-    IHS_LAUNCH_CHECK();
+    if (Q == 1024) {
+        const int acc_smem = m <= 2048 ? 1 : 0;
+        const size_t smem = r32_smem_bytes(m, acc_smem);
+        const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+        const int64_t CT32 = ceil_div64(d, kR32C);
+        int64_t PG32 = std::max<int64_t>(1, ceil_div64((int64_t)per_sm * ctx->sm_count, CT32));
+        PG32 = std::min<int64_t>(PG32, P);
+        if (PG32 > PG) {
+            IHS_TRY(ihs_scratch(ctx, SLOT_SKETCH_PART, (size_t)PG32 * m * d * sizeof(float), &pws));
+            part = static_cast<float*>(pws);
+        }
+        PG = PG32;
+        IHS_CUDA_TRY(cudaFuncSetAttribute(k_srht_r32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid((unsigned)CT32, (unsigned)PG);
+        k_srht_r32<<<grid, kR32T, smem, ctx->stream>>>(A, n, (int)d, m, P, (int)PG, rows, (uint32_t)level,
+                                                      (uint32_t)seed, (uint32_t)(seed >> 32), acc_smem, part);
+        IHS_LAUNCH_CHECK();
+    } else {
+        const size_t base = ((size_t)Q * (kSrhtC + 1) + Q) * sizeof(float);
+        const size_t acc_bytes = (size_t)m * kSrhtC * sizeof(float);
+        const int acc_in_smem = (base + acc_bytes <= 200 * 1024) ? 1 : 0;
+        const size_t smem = base + (acc_in_smem ? acc_bytes : 0);
+        IHS_CUDA_TRY(cudaFuncSetAttribute(k_srht_fwht, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid((unsigned)CT, (unsigned)PG);
+        k_srht_fwht<<<grid, kSrhtThreads, smem, ctx->stream>>>(A, n, (int)d, m, Q, logQ, P, (int)PG, rows,
+                                                              (uint32_t)level, (uint32_t)seed,
+                                                              (uint32_t)(seed >> 32), acc_in_smem, part);
+        IHS_LAUNCH_CHECK();
+    }
     const int64_t count = m * d;
     const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
     k_reduce_parts<<<rgrid, 256, 0, ctx->stream>>>(part, (int)PG, count, 1.0 / sqrt((double)m), SA);
