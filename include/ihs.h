@@ -125,9 +125,10 @@ int ihs_ctx_set_params(ihs_ctx* ctx, const ihs_params* p_h);
 
 /* ---- random draws (App. C.2) --------------------------------------------- */
 /* Rademacher signs eps_i in {-1,+1}, i < n_pad (int8, device).  Philox4x32-10
- * with key (seed_lo, seed_hi) and counter (k_lo, k_hi, level, 0), k = i / 128,
- * yields 128 bits (w0 bit 0 first, w3 bit 31 last); eps_i = +1 iff bit
- * (i mod 128) is 0. */
+ * with key (seed_lo, seed_hi) and counter (c_lo, c_hi, level, 0): rows form
+ * blocks of 1024; block b owns the 32 words of counters 8b .. 8b+7 (word
+ * 4t + k is output word k of counter 8b + t); row i = 1024 b + q takes bit
+ * (q >> 5) of word (q & 31), and eps_i = +1 iff that bit is 0. */
 int ihs_srht_signs(ihs_ctx* ctx, int64_t n_pad, uint64_t seed, int32_t level, int8_t* eps);
 
 /* The m row indices of [0, n_pad) with the smallest 64-bit keys

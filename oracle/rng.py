@@ -11,9 +11,11 @@ source:
 
 Counter layout (Philox4x32-10, key = (seed_lo, seed_hi)):
 
-    stream SIGNS = 0 : counter (k_lo, k_hi, level, 0), k = i // 128 -> the 128 output
-                       bits (w0 bit 0 .. w3 bit 31) give eps_{128k} .. eps_{128k+127};
-                       eps_i = +1 if bit (i mod 128) is 0 else -1
+    stream SIGNS = 0 : rows are grouped in blocks of 1024; block b owns the 32
+                       words of Philox counters 8b .. 8b+7 (counter (c_lo, c_hi,
+                       level, 0); word 4t + k is output word k of counter 8b + t).
+                       Row i = 1024 b + q takes bit (q >> 5) of word (q & 31):
+                       eps_i = +1 if that bit is 0 else -1
     stream ROWS  = 1 : counter (i_lo, i_hi, level, 1)     -> key_i = (w1 << 32) | w0
     stream GAUSS = 2 : counter (i, q, level, 2), q = j//4 -> z[4q .. 4q+3, i] by Box-Muller
 
@@ -42,15 +44,18 @@ def _split_index(i):
 
 
 def signs(n_pad, seed, level):
-    """Rademacher vector eps in {-1, +1}^n_pad (int8): bit (i mod 128) of the
-    128-bit Philox output for counter i // 128."""
+    """Rademacher vector eps in {-1, +1}^n_pad (int8): row i = 1024 b + q takes
+    bit (q >> 5) of word (q & 31) of block b's 32 Philox words."""
     k0, k1 = seed_key(seed)
-    blocks = (n_pad + 127) // 128
-    lo, hi = _split_index(np.arange(blocks, dtype=np.uint64))
-    words = philox4x32_10(lo, hi, np.uint64(level), np.uint64(SIGNS), k0, k1)
+    blocks = (n_pad + 1023) // 1024
+    ctr = np.arange(8 * blocks, dtype=np.uint64)
+    lo, hi = _split_index(ctr)
+    w = philox4x32_10(lo, hi, np.uint64(level), np.uint64(SIGNS), k0, k1)
+    words = np.stack(w, axis=1).reshape(blocks, 32)   # word 4t + k of block b
     i = np.arange(n_pad, dtype=np.int64)
-    word = np.stack(words, axis=1)[i // 128, (i % 128) // 32]
-    bit = (word >> (i % 32).astype(np.uint64)) & np.uint64(1)
+    q = i % 1024
+    word = words[i // 1024, q % 32]
+    bit = (word >> (q // 32).astype(np.uint64)) & np.uint64(1)
     return (1 - 2 * bit.astype(np.int64)).astype(np.int8)
 
 

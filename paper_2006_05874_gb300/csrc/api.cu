@@ -2,6 +2,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cudaTypedefs.h>
+
 #include <new>
 
 #include "common.cuh"
@@ -80,6 +82,10 @@ extern "C" int ihs_ctx_create(ihs_ctx** out, void* stream, const ihs_params* p) 
         if (cudaMemsetAsync(c->d_status, 0, 256, c->stream) != cudaSuccess) { st = IHS_ECUDA; break; }
         for (int i = 0; i < 4; ++i)
             if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { st = IHS_ECUDA; break; }
+        if (st != IHS_OK) break;
+        if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess) { st = IHS_ECUDA; break; }
+        for (int i = 0; i < 8; ++i)
+            if (cudaEventCreateWithFlags(&c->fev[i], cudaEventDisableTiming) != cudaSuccess) { st = IHS_ECUDA; break; }
     } while (0);
     if (st != IHS_OK) {
         ihs_ctx_destroy(c);
@@ -98,6 +104,12 @@ extern "C" int ihs_ctx_destroy(ihs_ctx* c) {
     if (c->d_status) cudaFree(c->d_status);
     for (int i = 0; i < 4; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    for (int i = 0; i < 8; ++i)
+        if (c->fev[i]) cudaEventDestroy(c->fev[i]);
+    if (c->aux) {
+        cudaStreamSynchronize(c->aux);
+        cudaStreamDestroy(c->aux);
+    }
     delete c;
     return IHS_OK;
 }
@@ -129,6 +141,29 @@ int ihs_scratch(ihs_ctx* c, int slot, size_t bytes, void** out) {
     }
     *out = c->buf[slot];
     return IHS_OK;
+}
+
+int ihs_tensor_map_f32(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                       int box_rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return IHS_ECUDA;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    if (((uintptr_t)base & 15) || ((ld * 4) & 15) || rows < 1 || cols < 1) return IHS_EINVAL;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? IHS_OK : IHS_EINVAL;
 }
 
 int ihs_check_status(ihs_ctx* c) {

@@ -2,6 +2,7 @@
 // Nothing here is part of the public C ABI (include/ihs.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -43,6 +44,7 @@ enum ScratchSlot {
     SLOT_SOLVE,           // solver state vectors
     SLOT_SOLVE_SA,        // solver-owned SA (m x d)
     SLOT_MISC,            // small device scalars (status word, reductions)
+    SLOT_FACTOR,          // the solver's factor (K/L, block inverses, X, X^T, apply scratch)
     SLOT_COUNT
 };
 
@@ -60,6 +62,8 @@ struct ihs_ctx {
     double* pinned;          // host pinned scratch (64 doubles)
     unsigned* d_status;      // device status word (IHS_DEV_*)
     cudaEvent_t ev[4];
+    cudaStream_t aux;        // private stream for the look-ahead Cholesky (joined back before return)
+    cudaEvent_t fev[8];      // fork/join events of the look-ahead Cholesky
 };
 
 struct ihs_factor {
@@ -73,6 +77,7 @@ struct ihs_factor {
     float* X;             // k x k lower inverse L^{-1} (FP32)
     float* XT;            // its transpose (upper)
     double* work;         // apply scratch vectors and reduction slots
+    int owned;            // 1: the buffers above are this handle's own allocations
 };
 
 int ihs_scratch(ihs_ctx* ctx, int slot, size_t bytes, void** out);
@@ -86,6 +91,9 @@ int ihs_sketch_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64
 int ihs_rows_enqueue(ihs_ctx* ctx, int64_t n_pad, int64_t m, uint64_t seed, int32_t level,
                      int32_t* rows);
 int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F);       // enqueue + check pivots (syncs)
+// Factor into the context's scratch (no allocation once the slot is large
+// enough); F is caller storage, valid until the next call with the same ctx.
+int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t* F);
 int ihs_apply_enqueue(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt,
                       double* d_r);
 
@@ -112,17 +120,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 enum { STREAM_SIGNS = 0, STREAM_ROWS = 1, STREAM_GAUSS = 2, STREAM_PROBE = 3 };
 
-// Sign bits of rows 128k .. 128k+127: one Philox call, bit (i mod 128) of
-// (w0, w1, w2, w3) is the sign bit of row i (1 -> eps = -1).
-__device__ __forceinline__ uint4 srht_sign_block(uint64_t k, uint32_t level, uint32_t k0, uint32_t k1) {
-    return philox4x32_10(make_uint4((uint32_t)k, (uint32_t)(k >> 32), level, STREAM_SIGNS), k0, k1);
+// SRHT signs: rows form blocks of 1024; block b owns the 32 words of Philox
+// counters 8b .. 8b+7 (word 4t + k = output word k of counter 8b + t), and row
+// i = 1024 b + q takes bit (q >> 5) of word (q & 31) (1 -> eps = -1).
+__device__ __forceinline__ uint4 srht_sign_words(uint64_t ctr, uint32_t level, uint32_t k0, uint32_t k1) {
+    return philox4x32_10(make_uint4((uint32_t)ctr, (uint32_t)(ctr >> 32), level, STREAM_SIGNS), k0, k1);
 }
 
 __device__ __forceinline__ int srht_sign_bit(uint64_t i, uint32_t level, uint32_t k0, uint32_t k1) {
-    const uint4 w = srht_sign_block(i >> 7, level, k0, k1);
-    const uint32_t sel = (uint32_t)(i >> 5) & 3u;
+    const uint32_t q = (uint32_t)(i & 1023u);
+    const uint32_t wi = q & 31u;
+    const uint4 w = srht_sign_words((i >> 10) * 8 + (wi >> 2), level, k0, k1);
+    const uint32_t sel = wi & 3u;
     const uint32_t word = sel == 0 ? w.x : (sel == 1 ? w.y : (sel == 2 ? w.z : w.w));
-    return (int)((word >> (i & 31u)) & 1u);
+    return (int)((word >> (q >> 5)) & 1u);
 }
 
 __device__ __forceinline__ uint64_t srht_row_key(uint64_t i, uint32_t level, uint32_t k0, uint32_t k1) {
@@ -253,6 +264,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+
+// 2-D tiled bulk tensor load (TMA) into shared memory, completing on `bar`.
+// x is the innermost coordinate (elements), y the row.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Host: encode a row-major FP32 matrix (rows x cols, leading dimension ld
+// elements) as a 2-D tensor map with box (box_cols, box_rows); out-of-range
+// elements read as zero.  Returns IHS_EINVAL if the layout is not TMA-able.
+int ihs_tensor_map_f32(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                       int box_rows);
 
 __host__ __device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

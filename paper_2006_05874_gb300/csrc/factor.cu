@@ -4,13 +4,14 @@
 //         H_S^{-1} g = nu^-2 (g - (SA)^T K^{-1} SA g),  K = nu^2 I_m + SA (SA)^T,
 // m >= d: K = H_S itself (d x d) and H_S^{-1} g = K^{-1} g.
 // K is formed from the FP32 sketch with compensated FP32 accumulation and
-// stored in FP64; K = L L^T by a blocked FP64 Cholesky (64-wide blocks; the
-// diagonal block also yields its inverse, the panel is a GEMM with it, the
-// trailing update is an FP64 SYRK on 64 x 64 tiles; non-positive or non-finite
-// pivots set IHS_DEV_NOTPD).  X = L^{-1} is formed once in FP32 by recursive
-// doubling ([L11 0; L21 L22]^{-1} has lower-left block -X22 L21 X11), so every
-// apply is a chain of parallel matrix-vector products, followed by one step of
-// iterative refinement against the exact operator in FP64 accumulation:
+// stored in FP64; K = L L^T by a blocked, right-looking FP64 Cholesky with one
+// step of look-ahead (64-wide blocks; an rsqrt per pivot, a row-parallel
+// substitution for the panel, FP64 SYRK tiles for the trailing update;
+// non-positive or non-finite pivots set IHS_DEV_NOTPD).  X = L^{-1} is formed
+// once in FP32 by recursive doubling ([L11 0; L21 L22]^{-1} has lower-left
+// block -X22 L21 X11), so every apply is a chain of parallel matrix-vector
+// products, followed by one step of iterative refinement against the exact
+// operator, with double-float (binary32 pair) vectors and dot products:
 //   u0 = X^T X t, u1 = u0 + X^T X (t - K u0)
 // with t = SA g, gt = nu^-2 (g - SA^T u1) (Woodbury) or t = g, gt = u1
 // (direct); r = 1/2 g^T gt (Lemma 4.1) in FP64.
@@ -23,44 +24,11 @@
 
 namespace {
 
-// t[j] = sum_l SA[j][l] g[l] in FP64 (products exact), one warp per row.
-__global__ void k_sa_g(const float* __restrict__ SA, int64_t m, int64_t d, const float* __restrict__ g,
-                       double* __restrict__ t) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= m) return;
-    double s = 0.0;
-    for (int64_t l = lane; l < d; l += 32) s = fma((double)SA[warp * d + l], (double)g[l], s);
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) t[warp] = s;
-}
-
-// Partial column sums of SA^T u over row chunks: part[chunk][c] (FP64).
-__global__ void k_sat_u(const float* __restrict__ SA, int64_t m, int64_t d, const double* __restrict__ u,
-                        int64_t rows_per_chunk, double* __restrict__ part) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t j0 = (int64_t)blockIdx.y * rows_per_chunk;
-    const int64_t j1 = m < j0 + rows_per_chunk ? m : j0 + rows_per_chunk;
-    if (c >= d) return;
-    double s = 0.0;
-    for (int64_t j = j0; j < j1; ++j) s = fma((double)SA[j * d + c], u[j], s);
-    part[blockIdx.y * d + c] = s;
-}
-
 __global__ void k_sum_half(const double* __restrict__ rpart, int count, double* __restrict__ r) {
     double s = 0.0;
     for (int i = 0; i < count; ++i) s += rpart[i];
     *r = 0.5 * s;
 }
-
-__global__ void k_to_double(const float* __restrict__ a, int64_t n, double* __restrict__ b) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (double)a[i];
-}
-
-
-// ---------------------------------------------------------------------------
-// Factor v2 building blocks.
 
 constexpr int FB = 64;   // block size of the FP64 Cholesky and of the inverse
 
@@ -136,24 +104,26 @@ __global__ void __launch_bounds__(256) k_gram_c32(const float* __restrict__ SA, 
         }
 }
 
-// Diagonal block [j0, j0+nb) of the FP64 Cholesky: L_jj in place and
-// W = L_jj^{-1} (lower, nb x nb, stored FB x FB at Wd).  Non-positive or
-// non-finite pivots set IHS_DEV_NOTPD (the pivot is replaced by 1 so that the
-// kernel finishes).
+// Diagonal block [j0, j0+nb) of the FP64 Cholesky, in place, and its inverse
+// W = L_jj^{-1} (FB x FB, lower, at Wd) for the panel.  One rsqrt per pivot
+// keeps the dependent FP64 chain short (FP64 division and square root are long
+// latency sequences); the inverse reuses the reciprocal pivots.  Non-positive
+// or non-finite pivots set IHS_DEV_NOTPD (the pivot is replaced by 1 so that
+// the kernel finishes).
 __global__ void __launch_bounds__(256) k_potrf64(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
                                                  double* __restrict__ Wd, unsigned* status) {
     __shared__ double a[FB][FB + 1];
     __shared__ double w[FB][FB + 1];
-    __shared__ double inv_piv;
+    __shared__ double dinv[FB];
     __shared__ int bad;
     const int tid = threadIdx.x;
     if (tid == 0) bad = 0;
     for (int e = tid; e < FB * FB; e += 256) {
         const int r = e / FB, c = e % FB;
-        a[r][c] = (r < nb && c < nb && c <= r) ? Kmat[(j0 + r) * k + j0 + c] : (r == c ? 1.0 : 0.0);
-        w[r][c] = 0.0;
+        if (r < nb && c < nb && c <= r) a[r][c] = Kmat[(j0 + r) * k + j0 + c];
     }
     __syncthreads();
+    const int tr = tid / 16, tc = tid % 16;   // 16 x 16 thread grid, no divisions in the loops
     for (int j = 0; j < nb; ++j) {
         if (tid == 0) {
             double p = a[j][j];
@@ -161,31 +131,33 @@ __global__ void __launch_bounds__(256) k_potrf64(double* __restrict__ Kmat, int6
                 bad = 1;
                 p = 1.0;
             }
-            const double dj = sqrt(p);
-            a[j][j] = dj;
-            inv_piv = 1.0 / dj;
+            const double ri = rsqrt(p);
+            a[j][j] = p * ri;
+            dinv[j] = ri;
         }
         __syncthreads();
-        const double ip = inv_piv;
-        for (int r = j + 1 + tid; r < nb; r += 256) a[r][j] *= ip;
+        const double ip = dinv[j];
+        if (tid > j && tid < nb) a[tid][j] *= ip;
         __syncthreads();
-        const int rem = nb - j - 1;
-        for (int e = tid; e < rem * rem; e += 256) {
-            const int r = j + 1 + e / rem, c = j + 1 + e % rem;
-            if (c <= r) a[r][c] = fma(-a[r][j], a[c][j], a[r][c]);
+        // only the needed FMAs are issued: predicated-off lanes still occupy the FP64 pipe
+        for (int r = j + 1 + tr; r < nb; r += 16) {
+            const double arj = a[r][j];
+            for (int c = j + 1 + tc; c <= r; c += 16) a[r][c] = fma(-arj, a[c][j], a[r][c]);
         }
         __syncthreads();
     }
-    // W = L^{-1}: thread c solves column c by forward substitution.
-    if (tid < nb) {
-        const int c = tid;
-        for (int r = c; r < nb; ++r) {
-            double s = (r == c) ? 1.0 : 0.0;
-            for (int l = c; l < r; ++l) s = fma(-a[r][l], w[l][c], s);
-            w[r][c] = s / a[r][r];
-        }
-    }
+    // W = L^{-1} by right-looking forward substitution on the identity.
+    for (int e = tid; e < FB * FB; e += 256) w[e / FB][e % FB] = (e / FB == e % FB) ? 1.0 : 0.0;
     __syncthreads();
+    for (int l = 0; l < nb; ++l) {
+        if (tid <= l) w[l][tid] *= dinv[l];
+        __syncthreads();
+        for (int r = l + 1 + tr; r < nb; r += 16) {
+            const double arl = a[r][l];
+            for (int c = tc; c <= l; c += 16) w[r][c] = fma(-arl, w[l][c], w[r][c]);
+        }
+        __syncthreads();
+    }
     for (int e = tid; e < FB * FB; e += 256) {
         const int r = e / FB, c = e % FB;
         if (r < nb && c < nb && c <= r) Kmat[(j0 + r) * k + j0 + c] = a[r][c];
@@ -194,51 +166,76 @@ __global__ void __launch_bounds__(256) k_potrf64(double* __restrict__ Kmat, int6
     if (tid == 0 && bad) atomicOr(status, IHS_DEV_NOTPD);
 }
 
-// Panel: rows i in [j0+nb, k): L[i][j0:j0+nb] = K[i][j0:j0+nb] W^T (64 rows per CTA).
+// Panel: rows i in [j0+nb, k): L[i][j0:j0+nb] = K[i][j0:j0+nb] W^T with
+// W = L_jj^{-1} (16 rows per CTA, 256 threads: 4 rows x 64 columns each).
+constexpr int kPanelRows = 16;
 __global__ void __launch_bounds__(256) k_panel64(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
                                                  const double* __restrict__ Wd) {
-    __shared__ double pr[FB][FB + 1];
+    __shared__ double pr[kPanelRows][FB + 1];
     __shared__ double wt[FB][FB + 1];
-    const int64_t r0 = j0 + nb + (int64_t)blockIdx.x * FB;
-    for (int e = threadIdx.x; e < FB * FB; e += 256) {
+    const int64_t r0 = j0 + nb + (int64_t)blockIdx.x * kPanelRows;
+    for (int e = threadIdx.x; e < FB * FB; e += 256) wt[e % FB][e / FB] = Wd[e];   // wt[c][r] = W[r][c]
+    for (int e = threadIdx.x; e < kPanelRows * FB; e += 256) {
         const int r = e / FB, c = e % FB;
         pr[r][c] = (r0 + r < k && c < nb) ? Kmat[(r0 + r) * k + j0 + c] : 0.0;
-        wt[c][r] = Wd[e];   // wt[c][r] = W[r][c]
     }
     __syncthreads();
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[4][4] = {};
+    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int q = 0; q < nb; ++q) {
-        double av[4], bv[4];
+        const double wq = wt[q][tx];   // W[tx][q]
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = pr[ty + 16 * a][q];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = wt[q][tx + 16 * b];   // W[tx+16b][q]
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        for (int a = 0; a < 4; ++a) acc[a] = fma(pr[ty + 4 * a][q], wq, acc[a]);
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int64_t r = r0 + ty + 16 * a;
-            const int c = tx + 16 * b;
-            if (r < k && c < nb) Kmat[r * k + j0 + c] = acc[a][b];
-        }
+    for (int a = 0; a < 4; ++a) {
+        const int64_t r = r0 + ty + 4 * a;
+        if (r < k && tx < nb) Kmat[r * k + j0 + tx] = acc[a];
+    }
 }
 
-// Trailing update K[j1:, j1:] -= P P^T on lower 64x64 tiles, P = L[j1:, j0:j0+nb].
-__global__ void __launch_bounds__(256) k_syrk64(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb) {
+// Look-ahead pieces of the trailing update after block step j0 (panel P =
+// L[j1:, j0:j0+nb], j1 = j0 + nb):
+//  * k_syrk_next: the next block column, K[i][j1 : j1+64] -= P_i P_{j1..}^T for
+//    i >= j1 (lower part), 16 rows per CTA (short tiles keep the critical path
+//    of the factorisation short);
+//  * k_syrk_rest: every lower 64 x 64 tile of the trailing matrix from tile
+//    column 1 on (a 2-D grid; CTAs above the diagonal exit at once).
+__global__ void __launch_bounds__(256) k_syrk_next(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb) {
+    __shared__ double pr[16][FB + 1];
+    __shared__ double pc[FB][FB + 1];
+    const int64_t j1 = j0 + nb;
+    const int64_t r0 = j1 + (int64_t)blockIdx.x * 16;
+    const int ncol = (int)min((int64_t)FB, k - j1);
+    for (int e = threadIdx.x; e < FB * FB; e += 256) {
+        const int c = e / FB, q = e % FB;
+        pc[c][q] = (c < ncol && q < nb) ? Kmat[(j1 + c) * k + j0 + q] : 0.0;
+    }
+    for (int e = threadIdx.x; e < 16 * FB; e += 256) {
+        const int r = e / FB, q = e % FB;
+        pr[r][q] = (r0 + r < k && q < nb) ? Kmat[(r0 + r) * k + j0 + q] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < nb; ++q) {
+        const double pcq = pc[tx][q];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a] = fma(pr[ty + 4 * a][q], pcq, acc[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t r = r0 + ty + 4 * a, c = j1 + tx;
+        if (r < k && tx < ncol && c <= r) Kmat[r * k + c] -= acc[a];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_syrk_rest(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb) {
+    const int64_t I = blockIdx.y, J = blockIdx.x;   // trailing tile indices
+    if (J < 1 || J > I) return;
     __shared__ double pa[FB][FB + 1];
     __shared__ double pb[FB][FB + 1];
     const int64_t j1 = j0 + nb;
-    const int64_t t = blockIdx.x;
-    int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while (I * (I + 1) / 2 > t) --I;
-    while ((I + 1) * (I + 2) / 2 <= t) ++I;
-    const int64_t J = t - I * (I + 1) / 2;
     for (int e = threadIdx.x; e < FB * FB; e += 256) {
         const int rr = e / FB, q = e % FB;
         const int64_t ra = j1 + I * FB + rr, rb = j1 + J * FB + rr;
@@ -268,17 +265,33 @@ __global__ void __launch_bounds__(256) k_syrk64(double* __restrict__ Kmat, int64
         }
 }
 
-// X (FP32, k x k, lower) <- diagonal blocks W of L^{-1} from k_potrf64; zero elsewhere.
-__global__ void k_inv_init(const double* __restrict__ Wall, int64_t k, float* __restrict__ X) {
+// X (FP32, k x k) <- zero, then each 64 x 64 diagonal block of X = the FP32
+// inverse of the matching block of L (one CTA per block, thread = column,
+// forward substitution); these start the recursive doubling below.
+__global__ void k_zero_f32(float* __restrict__ X, int64_t count) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= k * k) return;
-    const int64_t r = idx / k, c = idx % k;
-    float v = 0.f;
-    if (r / FB == c / FB && c <= r) {
-        const int64_t b = r / FB;
-        v = (float)Wall[b * FB * FB + (r % FB) * FB + (c % FB)];
+    if (idx < count) X[idx] = 0.f;
+}
+
+__global__ void __launch_bounds__(FB) k_blockinv32(const double* __restrict__ L, int64_t k, float* __restrict__ X) {
+    __shared__ float l[FB][FB + 1];
+    __shared__ float w[FB][FB + 1];
+    const int64_t b0 = (int64_t)blockIdx.x * FB;
+    const int nb = (int)(k - b0 < FB ? k - b0 : FB);
+    for (int e = threadIdx.x; e < FB * FB; e += FB) {
+        const int r = e / FB, c = e % FB;
+        l[r][c] = (r < nb && c < nb && c <= r) ? (float)L[(b0 + r) * k + b0 + c] : 0.f;
     }
-    X[idx] = v;
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c < nb) {
+        for (int r = c; r < nb; ++r) {
+            float s = (r == c) ? 1.f : 0.f;
+            for (int q = c; q < r; ++q) s = __fmaf_rn(-l[r][q], w[q][c], s);
+            w[r][c] = s / l[r][r];
+        }
+        for (int r = c; r < nb; ++r) X[(b0 + r) * k + b0 + c] = w[r][c];
+    }
 }
 
 // Batched FP32 GEMM for the recursive-doubling inverse: for pair p,
@@ -350,73 +363,147 @@ __global__ void k_transpose_f32(const float* __restrict__ X, int64_t k, float* _
     }
 }
 
-// y = M v (FP32 matrix, FP64 vector and accumulation), rows restricted to the
-// triangle: tri = 1 lower (l <= i), 2 upper (l >= i).  One warp per row.
-__global__ void k_trmv32(const float* __restrict__ M, int64_t k, int tri, const double* __restrict__ v,
-                         double* __restrict__ y) {
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= k) return;
-    const int64_t lo = tri == 2 ? warp : 0, hi = tri == 1 ? warp + 1 : k;
-    double s = 0.0;
-    for (int64_t l = lo + lane; l < hi; l += 32) s = fma((double)M[warp * k + l], v[l], s);
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) y[warp] = s;
+// ---------------------------------------------------------------------------
+// Apply kernels: vectors are double-float pairs (hi, lo) of binary32; dot
+// products use exact products (TwoProduct) and compensated sums, so every
+// dependent step is an FP32 operation (FP64 has a long dependent latency).
+
+__device__ __forceinline__ void acc_mul(Acc2& acc, float m, float2 x) {   // acc += m * (x.hi + x.lo)
+    float p, e, s, es;
+    two_prod(m, x.x, p, e);
+    two_sum(acc.hi, p, s, es);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(__fmaf_rn(m, x.y, e), es));
 }
 
-// y[j] = sum_l SA[j][l] v[l] (FP64 vector), one warp per row.
-__global__ void k_sa_v64(const float* __restrict__ SA, int64_t rows, int64_t d, const double* __restrict__ v,
-                         double* __restrict__ y) {
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= rows) return;
-    double s = 0.0;
-    for (int64_t l = lane; l < d; l += 32) s = fma((double)SA[warp * d + l], v[l], s);
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) y[warp] = s;
+__device__ __forceinline__ float2 df_norm(float hi, float lo) {   // fast renormalisation (|hi| >= |lo|)
+    const float s = __fadd_rn(hi, lo);
+    return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
 }
 
-// out[c] = sum_chunks part[chunk][c] (fixed order)
-__global__ void k_sum_chunks(const double* __restrict__ part, int chunks, int64_t d, double* __restrict__ out) {
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    return df_norm(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ float2 df_scale(float2 a, double sc) {   // a * sc with sc a double
+    const float sh = (float)sc, sl = (float)(sc - (double)sh);
+    float p, e;
+    two_prod(a.x, sh, p, e);
+    return df_norm(p, __fadd_rn(e, __fmaf_rn(a.x, sl, __fmul_rn(a.y, sh))));
+}
+
+__device__ __forceinline__ Acc2 warp_sum_acc2(Acc2 a) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const Acc2 o = acc2_shfl_xor(a, off);
+        a.add_pair(o.hi, o.lo);
+    }
+    return a;
+}
+
+// y[i] = (add ? add[i] : 0) + sum_l M[i][l] x[l], l in [lo(i), hi(i)):
+// tri 0 = all columns, 1 = l <= i (lower), 2 = l >= i (upper).  M row-major
+// FP32 with leading dimension ld; x double-float, or FP32 when xf != NULL.
+// One warp per row.
+__global__ void k_rowdot(const float* __restrict__ M, int64_t rows, int64_t cols, int64_t ld, int tri,
+                         const float2* __restrict__ x, const float* __restrict__ xf, const float2* add,
+                         float2* y) {
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= rows) return;
+    const int64_t l0 = tri == 2 ? i : 0, l1 = tri == 1 ? i + 1 : cols;
+    const float* row = M + i * ld;
+    Acc2 acc{0.f, 0.f};
+    if (xf) {
+        for (int64_t l = l0 + lane; l < l1; l += 32) acc_mul(acc, row[l], make_float2(xf[l], 0.f));
+    } else {
+        for (int64_t l = l0 + lane; l < l1; l += 32) acc_mul(acc, row[l], x[l]);
+    }
+    acc = warp_sum_acc2(acc);
+    if (lane == 0) {
+        float2 r = df_norm(acc.hi, acc.lo);
+        if (add) r = df_add(r, add[i]);
+        y[i] = r;
+    }
+}
+
+// part[chunk][c] = sum_{j in chunk} M[j][c] x[j] (column dots of a row-major
+// FP32 matrix, one thread per column, coalesced along c).
+__global__ void k_coldot_part(const float* __restrict__ M, int64_t rows, int64_t cols, const float2* __restrict__ x,
+                              int64_t rows_per_chunk, float2* __restrict__ part) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= d) return;
-    double s = 0.0;
-    for (int q = 0; q < chunks; ++q) s += part[q * d + c];
-    out[c] = s;
+    const int64_t j0 = (int64_t)blockIdx.y * rows_per_chunk;
+    const int64_t j1 = rows < j0 + rows_per_chunk ? rows : j0 + rows_per_chunk;
+    if (c >= cols) return;
+    Acc2 acc{0.f, 0.f};
+    for (int64_t j = j0; j < j1; ++j) acc_mul(acc, M[j * cols + c], x[j]);
+    part[blockIdx.y * cols + c] = df_norm(acc.hi, acc.lo);
 }
 
-// res = t - (alpha * u + w), elementwise FP64; also u1 bookkeeping done by caller.
-__global__ void k_residual(const double* __restrict__ t, const double* __restrict__ u, double alpha,
-                           const double* __restrict__ w, int64_t n, double* __restrict__ res) {
+// Reduce the column-dot partials in a fixed order into w; if g != NULL also
+// finish a Woodbury apply: gt = (g - w) / nu^2, with per-block FP64 partials
+// of g . gt for the decrement.
+__global__ void k_coldot_reduce(const float2* __restrict__ part, int chunks, int64_t cols, float2* __restrict__ w,
+                                const float* __restrict__ g, double inv_nu2, float* __restrict__ gt,
+                                double* __restrict__ rpart) {
+    __shared__ double sm[256];
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double prod = 0.0;
+    if (c < cols) {
+        float2 sum = part[c];
+        for (int q = 1; q < chunks; ++q) sum = df_add(sum, part[q * cols + c]);
+        if (w) w[c] = sum;
+        if (g) {
+            const double v = ((double)g[c] - ((double)sum.x + (double)sum.y)) * inv_nu2;
+            gt[c] = (float)v;
+            prod = (double)g[c] * v;
+        }
+    }
+    if (g) {
+        sm[threadIdx.x] = prod;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < 256; ++i) t += sm[i];
+            rpart[blockIdx.x] = t;
+        }
+    }
+}
+
+// res = t - (nu^2 u + w) in double-float.
+__global__ void k_res_df(const float2* __restrict__ t, const float2* __restrict__ u, double nu2,
+                         const float2* __restrict__ w, int64_t n, float2* __restrict__ res) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) res[i] = t[i] - (alpha * u[i] + w[i]);
+    if (i < n) res[i] = df_add(t[i], df_neg(df_add(df_scale(u[i], nu2), w[i])));
 }
 
-__global__ void k_axpy64(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+// t = g as double-float.
+__global__ void k_f2df(const float* __restrict__ g, int64_t n, float2* __restrict__ t) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) y[i] += x[i];
+    if (i < n) t[i] = make_float2(g[i], 0.f);
 }
 
-// gt = (g - w) * inv_nu2 (woodbury) or gt = u (direct) in FP64 -> FP32, and
-// per-block partials of g . gt.
-__global__ void k_apply_out(const float* __restrict__ g, const double* __restrict__ w, const double* __restrict__ u,
-                            int64_t d, double inv_nu2, float* __restrict__ gt, double* __restrict__ rpart) {
+// gt = u (direct form) and per-block FP64 partials of g . gt.
+__global__ void k_direct_out(const float* __restrict__ g, const float2* __restrict__ u, int64_t d,
+                             float* __restrict__ gt, double* __restrict__ rpart) {
     __shared__ double sm[256];
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double prod = 0.0;
     if (c < d) {
-        const double v = u ? u[c] : ((double)g[c] - w[c]) * inv_nu2;
+        const double v = (double)u[c].x + (double)u[c].y;
         gt[c] = (float)v;
         prod = (double)g[c] * v;
     }
     sm[threadIdx.x] = prod;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < 256; ++i) s += sm[i];
-        rpart[blockIdx.x] = s;
+        double t = 0.0;
+        for (int i = 0; i < 256; ++i) t += sm[i];
+        rpart[blockIdx.x] = t;
     }
 }
 
@@ -431,26 +518,50 @@ int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F) {
     const int64_t K = F->woodbury ? F->d : F->m;
     k_gram_c32<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(F->SA, F->d, F->woodbury, k, K, F->nu * F->nu, Kmat);
     IHS_LAUNCH_CHECK();
+    // Blocked right-looking Cholesky with one step of look-ahead: on the main
+    // stream, diagonal block jb, its panel and the update of block column jb+1;
+    // on the auxiliary stream, the rest of the trailing update of step jb,
+    // which overlaps the factorisation of block jb+1.  Events order the
+    // writes: the update of column jb+1 (main) follows the previous rest
+    // update (aux), and each rest update follows its panel.
+    cudaStream_t aux = ctx->aux;
+    IHS_CUDA_TRY(cudaEventRecord(ctx->fev[7], s));     // gram done
+    IHS_CUDA_TRY(cudaStreamWaitEvent(aux, ctx->fev[7], 0));
     for (int64_t jb = 0; jb < T; ++jb) {
         const int64_t j0 = jb * FB;
         const int nb = (int)std::min<int64_t>(FB, k - j0);
-        k_potrf64<<<1, 256, 0, s>>>(Kmat, k, j0, nb, Wall + jb * FB * FB, ctx->d_status);
+        double* Wj = Wall + jb * FB * FB;
+        k_potrf64<<<1, 256, 0, s>>>(Kmat, k, j0, nb, Wj, ctx->d_status);
         IHS_LAUNCH_CHECK();
         const int64_t rest = k - j0 - nb;
         if (rest > 0) {
-            k_panel64<<<(unsigned)ceil_div64(rest, FB), 256, 0, s>>>(Kmat, k, j0, nb, Wall + jb * FB * FB);
+            k_panel64<<<(unsigned)ceil_div64(rest, kPanelRows), 256, 0, s>>>(Kmat, k, j0, nb, Wj);
+            IHS_LAUNCH_CHECK();
+            cudaEvent_t panel_done = ctx->fev[jb % 3];
+            IHS_CUDA_TRY(cudaEventRecord(panel_done, s));
+            // column jb+1 must not race with the previous step's rest update
+            if (jb > 0) IHS_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fev[3 + (jb - 1) % 3], 0));
+            k_syrk_next<<<(unsigned)ceil_div64(rest, 16), 256, 0, s>>>(Kmat, k, j0, nb);
             IHS_LAUNCH_CHECK();
             const int64_t Tr = ceil_div64(rest, FB);
-            k_syrk64<<<(unsigned)(Tr * (Tr + 1) / 2), 256, 0, s>>>(Kmat, k, j0, nb);
-            IHS_LAUNCH_CHECK();
+            IHS_CUDA_TRY(cudaStreamWaitEvent(aux, panel_done, 0));
+            if (Tr > 1) {
+                k_syrk_rest<<<dim3((unsigned)Tr, (unsigned)Tr), 256, 0, aux>>>(Kmat, k, j0, nb);
+                IHS_LAUNCH_CHECK();
+            }
+            IHS_CUDA_TRY(cudaEventRecord(ctx->fev[3 + jb % 3], aux));
         }
     }
-    // X = L^{-1} in FP32 by recursive doubling: diagonal blocks come from the
-    // FP64 factorisation; for block size sz = 64, 128, ... the lower-left
+    IHS_CUDA_TRY(cudaEventRecord(ctx->fev[6], aux));
+    IHS_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fev[6], 0));
+    // X = L^{-1} in FP32 by recursive doubling: diagonal 64-blocks are FP32
+    // inverses of L's blocks; for block size sz = 64, 128, ... the lower-left
     // block of each pair is X21 = -X22 (L21 X11).
     float* X = F->X;
     float* tmp = F->XT;   // scratch for L21 X11 (overwritten by X^T at the end)
-    k_inv_init<<<(unsigned)ceil_div64(k * k, 256), 256, 0, s>>>(Wall, k, X);
+    k_zero_f32<<<(unsigned)ceil_div64(k * k, 256), 256, 0, s>>>(X, k * k);
+    IHS_LAUNCH_CHECK();
+    k_blockinv32<<<(unsigned)T, FB, 0, s>>>(F->L, k, X);
     IHS_LAUNCH_CHECK();
     for (int64_t sz = FB; sz < k; sz *= 2) {
         const int64_t pairs = ceil_div64(k, 2 * sz);
@@ -471,70 +582,71 @@ int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F) {
 
 // H_S^{-1} g with one step of iterative refinement: the FP32 inverse factor X
 // gives u0 = X^T X t; the residual t - K u0 uses the exact operator
-// (K u = nu^2 u + SA (SA^T u), or SA^T (SA u) + nu^2 u) in FP64 accumulation.
+// (K u = nu^2 u + SA (SA^T u), or SA^T (SA u) + nu^2 u); vectors and dot
+// products are double-float (binary32 pairs with compensated sums).
 int ihs_apply_enqueue(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt, double* d_r) {
     cudaStream_t s = ctx->stream;
     const int64_t k = F->k, d = F->d, m = F->m;
-    double* t = F->work;       // k
-    double* v = t + k;         // k
-    double* u = v + k;         // k (u0, then u1)
-    double* res = u + k;       // k
-    double* w = res + k;       // max(m, d)
-    double* w2 = w + std::max(m, d);   // max(m, d)
-    double* rpart = w2 + std::max(m, d);   // 4096
-    double* part = rpart + 4096;            // 32 x d
-    const unsigned kb = (unsigned)ceil_div64(k * 32, 256);
+    const int64_t mx = std::max(m, d);
+    float2* t = reinterpret_cast<float2*>(F->work);   // k
+    float2* v = t + k;                                 // k
+    float2* u = v + k;                                 // k
+    float2* res = u + k;                               // k
+    float2* w = res + k;                               // max(m, d)
+    float2* w2 = w + mx;                               // max(m, d)
+    float2* part = w2 + mx;                            // 32 x max(m, d)
+    double* rpart = reinterpret_cast<double*>(part + 32 * mx);   // 4096
+    const unsigned kw = (unsigned)ceil_div64(k * 32, 256);
+    const unsigned kb = (unsigned)ceil_div64(k, 256);
     const unsigned db = (unsigned)ceil_div64(d, 256);
-    const unsigned mb = (unsigned)ceil_div64(m * 32, 256);
-    const int64_t chunks = std::min<int64_t>(32, std::max<int64_t>(1, m / 32));
+    const unsigned mw = (unsigned)ceil_div64(m * 32, 256);
+    const int64_t chunks = std::min<int64_t>(32, std::max<int64_t>(1, m / 64));
     const int64_t rpc = ceil_div64(m, chunks);
     const int64_t nch = ceil_div64(m, rpc);
-    auto sat = [&](const double* uu, double* out) -> int {   // out = SA^T uu (d)
+    const double nu2 = F->nu * F->nu;
+    // SA^T x (d) into out; with gg != NULL the Woodbury output gt is produced instead
+    auto sat = [&](const float2* x, float2* out, const float* gg) -> int {
         dim3 grid(db, (unsigned)nch);
-        k_sat_u<<<grid, 256, 0, s>>>(F->SA, m, d, uu, rpc, part);
+        k_coldot_part<<<grid, 256, 0, s>>>(F->SA, m, d, x, rpc, part);
         IHS_LAUNCH_CHECK();
-        k_sum_chunks<<<db, 256, 0, s>>>(part, (int)nch, d, out);
-        IHS_LAUNCH_CHECK();
-        return IHS_OK;
-    };
-    auto minv = [&](const double* in, double* out) -> int {   // out = X^T X in
-        k_trmv32<<<kb, 256, 0, s>>>(F->X, k, 1, in, v);
-        IHS_LAUNCH_CHECK();
-        k_trmv32<<<kb, 256, 0, s>>>(F->XT, k, 2, v, out);
+        k_coldot_reduce<<<db, 256, 0, s>>>(part, (int)nch, d, out, gg, 1.0 / nu2, gt, rpart);
         IHS_LAUNCH_CHECK();
         return IHS_OK;
     };
-    const unsigned kvb = (unsigned)ceil_div64(k, 256);
     if (F->woodbury) {
-        k_sa_g<<<(unsigned)ceil_div64(m * 32, 256), 256, 0, s>>>(F->SA, m, d, g, t);
+        k_rowdot<<<mw, 256, 0, s>>>(F->SA, m, d, d, 0, nullptr, g, nullptr, t);   // t = SA g
+        IHS_LAUNCH_CHECK();
+        k_rowdot<<<kw, 256, 0, s>>>(F->X, k, k, k, 1, t, nullptr, nullptr, v);    // v = X t
         IHS_LAUNCH_CHECK();
     } else {
-        k_to_double<<<db, 256, 0, s>>>(g, d, t);
+        k_f2df<<<kb, 256, 0, s>>>(g, k, t);                                        // t = g
+        IHS_LAUNCH_CHECK();
+        k_rowdot<<<kw, 256, 0, s>>>(F->X, k, k, k, 1, nullptr, g, nullptr, v);    // v = X g
         IHS_LAUNCH_CHECK();
     }
-    IHS_TRY(minv(t, u));
-    // K u0
-    if (F->woodbury) {
-        IHS_TRY(sat(u, w));                                        // w = SA^T u0 (d)
-        k_sa_v64<<<mb, 256, 0, s>>>(F->SA, m, d, w, w2);             // w2 = SA w (m)
-        IHS_LAUNCH_CHECK();
-    } else {
-        k_sa_v64<<<mb, 256, 0, s>>>(F->SA, m, d, u, w);              // w = SA u0 (m)
-        IHS_LAUNCH_CHECK();
-        IHS_TRY(sat(w, w2));                                       // w2 = SA^T w (d)
-    }
-    k_residual<<<kvb, 256, 0, s>>>(t, u, F->nu * F->nu, w2, k, res);
-    IHS_LAUNCH_CHECK();
-    IHS_TRY(minv(res, w2));
-    k_axpy64<<<kvb, 256, 0, s>>>(u, w2, k);                         // u1 = u0 + X^T X res
+    k_rowdot<<<kw, 256, 0, s>>>(F->XT, k, k, k, 2, v, nullptr, nullptr, u);        // u0 = X^T v
     IHS_LAUNCH_CHECK();
     if (F->woodbury) {
-        IHS_TRY(sat(u, w));                                        // w = SA^T u1
-        k_apply_out<<<db, 256, 0, s>>>(g, w, nullptr, d, 1.0 / (F->nu * F->nu), gt, rpart);
+        IHS_TRY(sat(u, w, nullptr));                                                // w = SA^T u0
+        k_rowdot<<<mw, 256, 0, s>>>(F->SA, m, d, d, 0, w, nullptr, nullptr, w2);   // w2 = SA w
     } else {
-        k_apply_out<<<db, 256, 0, s>>>(g, nullptr, u, d, 0.0, gt, rpart);
+        k_rowdot<<<mw, 256, 0, s>>>(F->SA, m, d, d, 0, u, nullptr, nullptr, w);    // w = SA u0
+        IHS_LAUNCH_CHECK();
+        IHS_TRY(sat(w, w2, nullptr));                                               // w2 = SA^T w
     }
     IHS_LAUNCH_CHECK();
+    k_res_df<<<kb, 256, 0, s>>>(t, u, nu2, w2, k, res);                            // res = t - K u0
+    IHS_LAUNCH_CHECK();
+    k_rowdot<<<kw, 256, 0, s>>>(F->X, k, k, k, 1, res, nullptr, nullptr, v);       // v = X res
+    IHS_LAUNCH_CHECK();
+    k_rowdot<<<kw, 256, 0, s>>>(F->XT, k, k, k, 2, v, nullptr, u, u);              // u1 = u0 + X^T v
+    IHS_LAUNCH_CHECK();
+    if (F->woodbury) {
+        IHS_TRY(sat(u, nullptr, g));                                                // gt = (g - SA^T u1) / nu^2
+    } else {
+        k_direct_out<<<db, 256, 0, s>>>(g, u, d, gt, rpart);                        // gt = u1
+        IHS_LAUNCH_CHECK();
+    }
     if (d_r) {
         k_sum_half<<<1, 1, 0, s>>>(rpart, (int)db, d_r);
         IHS_LAUNCH_CHECK();
@@ -542,8 +654,40 @@ int ihs_apply_enqueue(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float
     return IHS_OK;
 }
 
+// apply scratch, in 8-byte units: t, v, u, res (k each), w, w2 (max(m, d) each),
+// 32 x max(m, d) column-dot partials, 4096 decrement partials, 64 spare
 static size_t factor_work_doubles(int64_t k, int64_t m, int64_t d) {
-    return 4 * (size_t)k + 2 * (size_t)std::max(m, d) + 4096 + 32 * (size_t)d + 64;
+    const size_t mx = (size_t)std::max(m, d);
+    return 4 * (size_t)k + 34 * mx + 4096 + 64;
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t* F) {
+    if (!ctx || !SA || !F || m < 1 || d < 1 || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
+    memset(F, 0, sizeof(*F));
+    F->ctx = ctx;
+    F->SA = SA;
+    F->m = m;
+    F->d = d;
+    F->nu = nu;
+    F->woodbury = m < d ? 1 : 0;
+    F->k = F->woodbury ? m : d;
+    F->owned = 0;
+    const int64_t k = F->k;
+    const int64_t T = ceil_div64(k, FB);
+    const size_t kk = (size_t)k * k;
+    const size_t bL = align256(kk * sizeof(double)), bW = align256((size_t)T * FB * FB * sizeof(double));
+    const size_t bX = align256(kk * sizeof(float)), bwork = align256(factor_work_doubles(k, m, d) * sizeof(double));
+    void* ws = nullptr;
+    IHS_TRY(ihs_scratch(ctx, SLOT_FACTOR, bL + bW + 2 * bX + bwork, &ws));
+    char* base = static_cast<char*>(ws);
+    F->L = reinterpret_cast<double*>(base);
+    F->W = reinterpret_cast<double*>(base + bL);
+    F->X = reinterpret_cast<float*>(base + bL + bW);
+    F->XT = reinterpret_cast<float*>(base + bL + bW + bX);
+    F->work = reinterpret_cast<double*>(base + bL + bW + 2 * bX);
+    return ihs_factor_build(ctx, F);
 }
 
 extern "C" int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** out) {
@@ -559,6 +703,7 @@ extern "C" int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, d
     F->nu = nu;
     F->woodbury = m < d ? 1 : 0;
     F->k = F->woodbury ? m : d;
+    F->owned = 1;
     const int64_t k = F->k;
     const int64_t T = ceil_div64(k, FB);
     const size_t kk = (size_t)k * k;
@@ -581,6 +726,7 @@ extern "C" int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, d
 
 extern "C" int ihs_factor_destroy(ihs_factor_t* F) {
     if (!F) return IHS_OK;
+    if (!F->owned) return IHS_EINVAL;   // scratch-backed factors belong to their context
     if (F->ctx) cudaStreamSynchronize(F->ctx->stream);
     if (F->L) cudaFree(F->L);
     if (F->W) cudaFree(F->W);

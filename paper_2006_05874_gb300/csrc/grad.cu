@@ -38,8 +38,43 @@ struct FastLayout {
     }
 };
 
-template <int TPR, int CPT, int RT>
-__global__ void __launch_bounds__(kThreads, 1)
+// Butterfly reduce-scatter of RT per-row compensated partials across the 32
+// lanes of a warp: at each of the first log2(RT) steps a lane keeps half of
+// its rows and sends the other half to its partner (xor 16, 8, ...); the
+// remaining steps are a full butterfly on the one value left.  Lane l ends
+// with the warp's sum for row `row_of_lane(l)`; all lanes sharing that row
+// hold the same value.
+template <int RT>
+__device__ __forceinline__ Acc2 warp_reduce_scatter(Acc2 (&v)[RT], int lane, int& row) {
+    int count = RT;
+    row = 0;
+#pragma unroll
+    for (int mask = 16; mask >= 1; mask >>= 1) {
+        if (count > 1) {
+            const int half = count / 2;
+            const bool up = (lane & mask) != 0;
+#pragma unroll
+            for (int i = 0; i < RT / 2; ++i) {
+                if (i < half) {
+                    const Acc2 keep = up ? v[half + i] : v[i];
+                    const Acc2 send = up ? v[i] : v[half + i];
+                    const Acc2 got = acc2_shfl_xor(send, mask);
+                    v[i] = keep;
+                    v[i].add_pair(got.hi, got.lo);
+                }
+            }
+            if (up) row += half;
+            count = half;
+        } else {
+            const Acc2 got = acc2_shfl_xor(v[0], mask);
+            v[0].add_pair(got.hi, got.lo);
+        }
+    }
+    return v[0];
+}
+
+template <int TPR, int CPT, int RT, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 k_grad_fast(const float* __restrict__ A, const float* __restrict__ b, const float* __restrict__ x,
             int64_t n, int d, int64_t ntiles, int stages, float2* __restrict__ part,
             double* __restrict__ part_ax2, unsigned* status) {
@@ -132,35 +167,27 @@ k_grad_fast(const float* __restrict__ A, const float* __restrict__ b, const floa
                 dot[j].add_prod(a[j][k].w, xr[k].w);
             }
         }
-#pragma unroll
-        for (int j = 0; j < RT; ++j) {
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) {
-                const Acc2 o = acc2_shfl_xor(dot[j], off);
-                dot[j].add_pair(o.hi, o.lo);
-            }
-        }
+        int myrow = 0;   // row (0..RT-1 within this thread's rows) whose warp sum this lane holds
+        const Acc2 wsum = warp_reduce_scatter<RT>(dot, lane, myrow);
+        // lanes holding row j: a contiguous group of 32/RT lanes starting at j*(32/RT)
+        const bool leader = (lane & (32 / RT - 1)) == 0;
         float rv[RT];
         if (W == 1) {
+            // the warp owns whole rows: lanes form r and broadcast it with shuffles
             __syncthreads();   // every thread is done with stage s
-#pragma unroll
-            for (int j = 0; j < RT; ++j) {
-                const int rr = grp + j * RP;
-                float r = 0.f;
-                if (rr < rows) {
-                    r = __fadd_rn(__fsub_rn(dot[j].hi, b[row0 + rr]), dot[j].lo);
-                    if (t == 0) {
-                        const double v = (double)dot[j].hi + (double)dot[j].lo;
-                        ax2 += v * v;
-                    }
+            const int rr = grp + myrow * RP;
+            float r = 0.f;
+            if (rr < rows) {
+                r = __fadd_rn(__fsub_rn(wsum.hi, b[row0 + rr]), wsum.lo);
+                if (leader) {
+                    const double v = (double)wsum.hi + (double)wsum.lo;
+                    ax2 += v * v;
                 }
-                rv[j] = r;
             }
-        } else {
-            if (lane == 0) {
 #pragma unroll
-                for (int j = 0; j < RT; ++j) red[(grp + j * RP) * W + wir] = dot[j];
-            }
+            for (int j = 0; j < RT; ++j) rv[j] = __shfl_sync(0xffffffffu, r, j * (32 / RT));
+        } else {
+            if (leader) red[(grp + myrow * RP) * W + wir] = wsum;
             __syncthreads();   // stage s consumed, per-warp partials visible
             if (tid < R) {
                 const int rr = tid;
@@ -354,14 +381,14 @@ FastCfg pick_fast(int d) {
     return {256, 8, 1};
 }
 
-template <int TPR, int CPT, int RT>
+template <int TPR, int CPT, int RT, int MINB>
 int launch_fast(ihs_ctx* ctx, const float* A, const float* b, const float* x, int64_t n, int d, float2* part,
                 double* part_ax2, int* G_out) {
     constexpr int RP = kThreads / TPR;
     constexpr int R = RT * RP;
     constexpr int W = TPR / 32;
     const size_t stage_bytes = (size_t)R * d * sizeof(float);
-    const size_t budget = 200 * 1024;
+    const size_t budget = MINB >= 2 ? 104 * 1024 : 200 * 1024;
     int stages = 8;
     while (stages > 2 && FastLayout(stages, R, W, d).total > budget) --stages;
     size_t smem = FastLayout(stages, R, W, d).total;
@@ -369,9 +396,9 @@ int launch_fast(ihs_ctx* ctx, const float* A, const float* b, const float* x, in
     const size_t comb = (size_t)RP * d * sizeof(Acc2);
     if (smem < comb) smem = comb;
     const int64_t ntiles = ceil_div64(n, R);
-    int64_t G = ctx->sm_count;
+    int64_t G = (int64_t)MINB * ctx->sm_count;
     if (G > ntiles) G = ntiles;
-    auto kern = k_grad_fast<TPR, CPT, RT>;
+    auto kern = k_grad_fast<TPR, CPT, RT, MINB>;
     IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)G, kThreads, smem, ctx->stream>>>(A, b, x, n, d, ntiles, stages, part, part_ax2,
                                                       ctx->d_status);
@@ -396,13 +423,13 @@ int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, in
     if (aligned && n >= 1) {
         const FastCfg c = pick_fast((int)d);
         int st;
-        if (c.tpr == 32) st = launch_fast<32, 1, 8>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (c.tpr == 64) st = launch_fast<64, 1, 8>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (c.tpr == 128) st = launch_fast<128, 1, 8>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (c.cpt == 1) st = launch_fast<256, 1, 8>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (c.cpt == 2) st = launch_fast<256, 2, 4>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (c.cpt == 4) st = launch_fast<256, 4, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else st = launch_fast<256, 8, 1>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        if (c.tpr == 32) st = launch_fast<32, 1, 8, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (c.tpr == 64) st = launch_fast<64, 1, 8, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (c.tpr == 128) st = launch_fast<128, 1, 8, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (c.cpt == 1) st = launch_fast<256, 1, 8, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (c.cpt == 2) st = launch_fast<256, 2, 4, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (c.cpt == 4) st = launch_fast<256, 4, 2, 1>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else st = launch_fast<256, 8, 1, 1>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
         IHS_TRY(st);
     } else {
         const int64_t rblocks = ceil_div64(n, 128);
@@ -550,7 +577,7 @@ int launch_fast_noalloc(cudaStream_t stream, int sm_count, const float* A, const
     if (smem < comb) smem = comb;
     const int64_t ntiles = ceil_div64(n, R);
     int64_t G = std::min<int64_t>(std::min<int64_t>(sm_count, IHS_NOALLOC_MAX_CTAS), ntiles);
-    auto kern = k_grad_fast<TPR, CPT, RT>;
+    auto kern = k_grad_fast<TPR, CPT, RT, 1>;
     IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)G, kThreads, smem, stream>>>(A, b, x, n, d, ntiles, stages, part, part_ax2, status);
     IHS_LAUNCH_CHECK();

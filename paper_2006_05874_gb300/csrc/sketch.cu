@@ -120,65 +120,91 @@ __device__ __forceinline__ void wht32(float (&v)[32]) {
     }
 }
 
-__host__ __device__ inline size_t r32_smem_bytes(int64_t m, int acc_smem) {
-    // the row list and the accumulators live in shared memory only in smem mode
-    return (size_t)32 * kR32Stride * sizeof(float) + 32 * sizeof(uint32_t) +
-           (acc_smem ? (size_t)((m + 3) & ~3ll) * sizeof(int32_t) + (size_t)m * kR32C * sizeof(float) : 0);
+// Shared memory of k_srht_r32: two TMA stages of 1024 x 16 floats, the padded
+// transpose buffer, sign words, two mbarriers, per-row offsets.
+constexpr size_t kR32Stage = 1024 * kR32C * sizeof(float);   // 64 KiB
+__host__ __device__ inline size_t r32_smem_bytes(int64_t mrows) {
+    return 2 * kR32Stage + (size_t)32 * kR32Stride * sizeof(float) + 32 * sizeof(uint32_t) + 2 * sizeof(uint64_t) +
+           2 * (size_t)mrows * sizeof(int32_t);
 }
 
-__global__ void __launch_bounds__(kR32T)
-k_srht_r32(const float* __restrict__ A, int64_t n, int d, int64_t m, int64_t P, int PG,
-           const int32_t* __restrict__ rows, uint32_t level, uint32_t k0, uint32_t k1, int acc_smem,
-           float* __restrict__ out /* PG x m x d partials */) {
-    extern __shared__ __align__(16) float sm[];
-    float* T = sm;                                                    // 32 x 528
-    uint32_t* sbits = reinterpret_cast<uint32_t*>(T + 32 * kR32Stride);   // 32 words = 1024 sign bits
-    int32_t* srows = reinterpret_cast<int32_t*>(sbits + 32);             // m selected rows (smem mode)
-    float* acc = reinterpret_cast<float*>(srows + ((m + 3) & ~3ll));     // m x 16 (smem mode)
-    const int32_t* rinfo = acc_smem ? srows : rows;
+// MA accumulators per thread: this launch handles m <= 32 MA selected rows;
+// thread (c, ql) accumulates rows ql + 32 i (i < MA) of column c in registers.
+// Blocks of 1024 x 16 arrive by TMA (four 256-row boxes) into a two-stage
+// ring; rows >= n and columns >= d read as zero.
+template <int MA>
+__global__ void __launch_bounds__(kR32T, 1)
+k_srht_r32(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t m_total, int64_t row_off, int64_t P,
+           int PG, const int32_t* __restrict__ rows, uint32_t level, uint32_t k0, uint32_t k1, unsigned* status,
+           float* __restrict__ out /* PG x m_total x d partials; this launch writes rows [row_off, row_off + m) */) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float* stage = reinterpret_cast<float*>(smraw);                                   // 2 x 1024 x 16
+    float* T = reinterpret_cast<float*>(smraw + 2 * kR32Stage);                      // 32 x 528
+    uint32_t* sbits = reinterpret_cast<uint32_t*>(T + 32 * kR32Stride);              // 32 sign words
+    uint64_t* full = reinterpret_cast<uint64_t*>(sbits + 32);                        // 2 mbarriers
+    int32_t* toff = reinterpret_cast<int32_t*>(full + 2);                            // T offset per selected row
+    uint32_t* rhi = reinterpret_cast<uint32_t*>(toff + m);                           // its block-index bits
     const int tid = threadIdx.x;
     const int c = tid & 15, ql = tid >> 4;
     const int col0 = blockIdx.x * kR32C;
     const int col = col0 + c;
-    const bool colok = col < d;
     const int pg = blockIdx.y;
     const int64_t p0 = (int64_t)pg * P / PG, p1 = (int64_t)(pg + 1) * P / PG;
-    float* outp = out + (size_t)pg * m * d;
+    const int64_t nblk = p1 - p0;
 
-    if (acc_smem) {
-        for (int64_t j = tid; j < m; j += kR32T) srows[j] = rows[j];
-        for (int64_t e = tid; e < m * kR32C; e += kR32T) acc[e] = 0.f;
-    } else {
-        for (int64_t e = tid; e < m * kR32C; e += kR32T) {
-            const int cc = (int)(e & 15);
-            if (col0 + cc < d) outp[(e >> 4) * d + col0 + cc] = 0.f;
-        }
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        fence_mbar_init();
     }
-    for (int64_t p = p0; p < p1; ++p) {
+    for (int64_t j = tid; j < m; j += kR32T) {
+        const uint32_t r = (uint32_t)rows[j];
+        const uint32_t lo = r & 1023u;
+        toff[j] = (int32_t)((lo >> 5) * kR32Stride + (lo & 31u) * 16);
+        rhi[j] = r >> 10;
+    }
+    __syncthreads();
+    auto issue = [&](int64_t b) {   // block p0 + b into stage b & 1
+        float* dst = stage + (size_t)(b & 1) * (1024 * kR32C);
+        uint64_t* bar = &full[b & 1];
+        mbar_arrive_expect_tx(bar, (uint32_t)kR32Stage);
+        const int y0 = (int)((p0 + b) * 1024);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tma_load_2d(dst + q * 256 * kR32C, &amap, col0, y0 + 256 * q, bar);
+    };
+    if (tid == 0) {
+        issue(0);
+        if (nblk > 1) issue(1);
+    }
+    float acc[MA];
+#pragma unroll
+    for (int i = 0; i < MA; ++i) acc[i] = 0.f;
+    int64_t b = 0;
+    for (; b < nblk; ++b) {
+        const int64_t p = p0 + b;
         if (tid < 8) {
-            const uint4 w = srht_sign_block((uint64_t)p * 8 + tid, level, k0, k1);
+            const uint4 w = srht_sign_words((uint64_t)p * 8 + tid, level, k0, k1);
             sbits[4 * tid + 0] = w.x;
             sbits[4 * tid + 1] = w.y;
             sbits[4 * tid + 2] = w.z;
             sbits[4 * tid + 3] = w.w;
         }
+        const bool ok = mbar_wait_bounded(&full[b & 1], (uint32_t)((b >> 1) & 1), status);
+        if (__syncthreads_or(!ok)) break;   // also: sign words ready, previous gather done with T
+        const float* st = stage + (size_t)(b & 1) * (1024 * kR32C);
         float v[32];
-        const int64_t base = p * 1024 + ql;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const int64_t row = base + 32 * k;
-            v[k] = (colok && row < n) ? __ldg(A + row * d + col) : 0.f;
-        }
-        __syncthreads();   // signs ready; previous block's gather done with T
+        for (int k = 0; k < 32; ++k) v[k] = st[(ql + 32 * k) * kR32C + c];
+        // row 32 k + ql of the block takes bit k of word ql: flip the float's sign bit
+        const uint32_t word = sbits[ql];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            // row 32k + ql of the block: word k, bit ql
-            if ((sbits[k] >> ql) & 1u) v[k] = -v[k];
-        }
+        for (int k = 0; k < 32; ++k)
+            v[k] = __int_as_float(__float_as_int(v[k]) ^ (int)((word << (31 - k)) & 0x80000000u));
         wht32(v);   // over k (high five index bits)
 #pragma unroll
         for (int k = 0; k < 32; ++k) T[k * kR32Stride + ql * 16 + c] = v[k];
-        __syncthreads();
+        __syncthreads();   // stage b & 1 fully read: refill it with block b + 2
+        if (tid == 0 && b + 2 < nblk) issue(b + 2);
 #pragma unroll
         for (int l = 0; l < 32; ++l) v[l] = T[ql * kR32Stride + l * 16 + c];
         wht32(v);   // over the low five index bits; thread now holds Y[32 ql + l]
@@ -186,26 +212,46 @@ k_srht_r32(const float* __restrict__ A, int64_t n, int d, int64_t m, int64_t P, 
 #pragma unroll
         for (int l = 0; l < 32; ++l) T[ql * kR32Stride + l * 16 + c] = v[l];
         __syncthreads();
-        for (int64_t e = tid; e < m * kR32C; e += kR32T) {
-            const int cc = (int)(e & 15);
-            const uint32_t r = (uint32_t)rinfo[e >> 4];
-            const uint32_t lo = r & 1023u;
-            const float val = T[(lo >> 5) * kR32Stride + (lo & 31u) * 16 + cc];
-            const float sv = (__popcll((uint64_t)(r >> 10) & (uint64_t)p) & 1) ? -val : val;
-            if (acc_smem) {
-                acc[e] += sv;
-            } else if (col0 + cc < d) {
-                outp[(e >> 4) * d + col0 + cc] += sv;
+        const uint32_t pb = (uint32_t)p;
+#pragma unroll
+        for (int i = 0; i < MA; ++i) {
+            const int64_t j = ql + 32 * i;
+            if (j < m) {
+                const float val = T[toff[j] + c];
+                acc[i] += (__popc(rhi[j] & pb) & 1) ? -val : val;
             }
         }
     }
-    if (acc_smem) {
+    if (b < nblk) {
+        // a wait gave up: let the copies in flight land before exiting
+        if (tid == 0) {
+            for (int64_t q = b; q < nblk && q < b + 2; ++q)
+                mbar_wait_bounded(&full[q & 1], (uint32_t)((q >> 1) & 1), status);
+        }
         __syncthreads();
-        for (int64_t e = tid; e < m * kR32C; e += kR32T) {
-            const int cc = (int)(e & 15);
-            if (col0 + cc < d) outp[(e >> 4) * d + col0 + cc] = acc[e];
+        return;
+    }
+    if (col < d) {
+        float* outp = out + ((size_t)pg * m_total + row_off) * d + col;
+#pragma unroll
+        for (int i = 0; i < MA; ++i) {
+            const int64_t j = ql + 32 * i;
+            if (j < m) outp[j * d] = acc[i];
         }
     }
+}
+
+template <int MA>
+int launch_r32(ihs_ctx* ctx, const CUtensorMap& amap, int d, int64_t mc, int64_t m, int64_t c0, int64_t P, int PG,
+               const int32_t* rows, int32_t level, uint64_t seed, float* part) {
+    const size_t smem = r32_smem_bytes(mc);
+    auto kern = k_srht_r32<MA>;
+    IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)ceil_div64(d, kR32C), (unsigned)PG);
+    kern<<<grid, kR32T, smem, ctx->stream>>>(amap, d, mc, m, c0, P, PG, rows, (uint32_t)level, (uint32_t)seed,
+                                            (uint32_t)(seed >> 32), ctx->d_status, part);
+    IHS_LAUNCH_CHECK();
+    return IHS_OK;
 }
 
 // out[e] = scale * sum_k part[k][e] in a fixed order (FP64).
@@ -321,23 +367,37 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
     void* pws = nullptr;
     IHS_TRY(ihs_scratch(ctx, SLOT_SKETCH_PART, (size_t)PG * m * d * sizeof(float), &pws));
     float* part = static_cast<float*>(pws);
-    if (Q == 1024) {
-        const int acc_smem = m <= 2048 ? 1 : 0;
-        const size_t smem = r32_smem_bytes(m, acc_smem);
-        const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+    CUtensorMap amap;
+    const bool tma = Q == 1024 && ihs_tensor_map_f32(&amap, A, n, d, d, kR32C, 256) == IHS_OK;
+    if (tma) {
+        // Selected rows go in chunks of at most 1024 (32 register accumulators
+        // per thread); each chunk re-reads A.
+        const int64_t chunk = std::min<int64_t>(m, 1024);
         const int64_t CT32 = ceil_div64(d, kR32C);
-        int64_t PG32 = std::max<int64_t>(1, ceil_div64((int64_t)per_sm * ctx->sm_count, CT32));
+        // one CTA per SM: a grid of CT32 x PG32 CTAs in whole waves when the
+        // block ranges allow it (PG32 = SMs / gcd(CT32, SMs)), else >= 1 wave
+        int64_t g = CT32, h = ctx->sm_count;
+        while (h) {
+            const int64_t t = g % h;
+            g = h;
+            h = t;
+        }
+        int64_t PG32 = ctx->sm_count / g;
+        if (PG32 > P || PG32 * m * d * 4 > ((int64_t)1 << 30)) PG32 = std::max<int64_t>(1, ceil_div64((int64_t)ctx->sm_count, CT32));
         PG32 = std::min<int64_t>(PG32, P);
         if (PG32 > PG) {
             IHS_TRY(ihs_scratch(ctx, SLOT_SKETCH_PART, (size_t)PG32 * m * d * sizeof(float), &pws));
             part = static_cast<float*>(pws);
         }
         PG = PG32;
-        IHS_CUDA_TRY(cudaFuncSetAttribute(k_srht_r32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        dim3 grid((unsigned)CT32, (unsigned)PG);
-        k_srht_r32<<<grid, kR32T, smem, ctx->stream>>>(A, n, (int)d, m, P, (int)PG, rows, (uint32_t)level,
-                                                      (uint32_t)seed, (uint32_t)(seed >> 32), acc_smem, part);
-        IHS_LAUNCH_CHECK();
+        for (int64_t c0 = 0; c0 < m; c0 += chunk) {
+            const int64_t mc = std::min<int64_t>(chunk, m - c0);
+            int st;
+            if (mc <= 32 * 4) st = launch_r32<4>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, part);
+            else if (mc <= 32 * 16) st = launch_r32<16>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, part);
+            else st = launch_r32<32>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, part);
+            IHS_TRY(st);
+        }
     } else {
         const size_t base = ((size_t)Q * (kSrhtC + 1) + Q) * sizeof(float);
         const size_t acc_bytes = (size_t)m * kSrhtC * sizeof(float);

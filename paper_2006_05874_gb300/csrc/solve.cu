@@ -100,7 +100,8 @@ struct Solver {
     double nu;
     float* vec[7];        // x, x_prev, g, gt, xc, gc, gtc
     double* dsc;          // device scalars: [0] r, [1] ax2, [2] xx, [8..] partials
-    ihs_factor_t* F;
+    ihs_factor_t* F;      // points at Fs once a level is factored
+    ihs_factor_t Fs;      // scratch-backed factor of the current level
     float* SA;
     int64_t m;
     int level;
@@ -109,16 +110,14 @@ struct Solver {
 
 int sketch_level(Solver& S, int64_t m, int level) {
     ihs_ctx* ctx = S.ctx;
-    if (S.F) {
-        ihs_factor_destroy(S.F);
-        S.F = nullptr;
-    }
+    S.F = nullptr;
     void* ws = nullptr;
     IHS_TRY(ihs_scratch(ctx, SLOT_SOLVE_SA, (size_t)m * S.d * sizeof(float), &ws));
     S.SA = static_cast<float*>(ws);
     IHS_CUDA_TRY(cudaEventRecord(ctx->ev[0], ctx->stream));
     IHS_TRY(ihs_sketch_enqueue(ctx, S.A, S.n, S.d, m, ctx->p.kind, ctx->p.seed, level, S.SA));
-    IHS_TRY(ihs_factor(ctx, S.SA, m, S.d, S.nu, &S.F));   // synchronises (pivot check)
+    IHS_TRY(ihs_factor_scratch(ctx, S.SA, m, S.d, S.nu, &S.Fs));   // synchronises (pivot check)
+    S.F = &S.Fs;
     IHS_CUDA_TRY(cudaEventRecord(ctx->ev[1], ctx->stream));
     IHS_CUDA_TRY(cudaEventSynchronize(ctx->ev[1]));
     float ms = 0.f;
@@ -310,7 +309,6 @@ extern "C" int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n
     for (int i = 1; i < 7; ++i) S.vec[i] = reinterpret_cast<float*>(base + i * vb);
     S.dsc = reinterpret_cast<double*>(base + 7 * vb);
     const int st = solve_impl(S, tol, &rep);
-    if (S.F) ihs_factor_destroy(S.F);
     if (rep_h) *rep_h = rep;
     if (st == IHS_OK || st == IHS_EMAXITER) {
         const int s2 = ihs_check_status(ctx);
