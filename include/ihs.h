@@ -202,6 +202,21 @@ int ihs_grad_noalloc(void* stream, const float* A, const float* b, int64_t n, in
 int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
               double nu, double tol, float* x, ihs_report* rep_h);
 
+/* ---- comparators (Sec. 5) ------------------------------------------------ */
+/* Conjugate gradient on the normal equations (A^T A + nu^2 I) x = A^T b, or,
+ * with precond_kind = IHS_SKETCH_SRHT / IHS_SKETCH_GAUSS, sketch-preconditioned
+ * CG whose preconditioner is H_S of a sketch of size ceil(d / rho) (Gaussian)
+ * or ceil(d ln d / rho) (SRHT) drawn at level 0 of params.seed, capped at n
+ * (Gaussian) or n_pad (SRHT); precond_kind = -1 gives plain CG.  Sec. 5 names
+ * the comparators and these sketch sizes; the preconditioner form and the
+ * stopping rule ||r|| <= tol ||A^T b|| (r = A^T b - (A^T A + nu^2 I) x) are
+ * this library's.  x (device, d): on entry x_0, on exit the last iterate.
+ * rep_h (may be NULL): iterations, grad_passes (Hessian-vector products + 2),
+ * m_final (sketch size), r_final (= ||r|| / ||A^T b||), ms_sketch
+ * (preconditioner set-up), ms_iterate.  IHS_EMAXITER if max_iter is reached. */
+int ihs_cg(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu, double tol,
+           int32_t max_iter, int32_t precond_kind, float* x, ihs_report* rep_h);
+
 #ifdef __cplusplus
 }
 #endif

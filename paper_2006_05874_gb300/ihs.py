@@ -67,6 +67,7 @@ _SIGNATURES = {
     "ihs_apply_hinv": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
     "ihs_grad": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
     "ihs_solve": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
+    "ihs_cg": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i32, _i32, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_grad_noalloc": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, _vp], ctypes.c_int),
 }
 
@@ -221,6 +222,17 @@ class Context:
         st = _lib.ihs_solve(self.handle, _ptr(A), _ptr(b), n, d, float(nu), float(tol), _ptr(x), ctypes.byref(rep))
         if st != IHS_OK and (st != IHS_EMAXITER or raise_on_maxiter):
             _check("ihs_solve", st)
+        return rep
+
+    def cg(self, A, b, nu, x, tol=1e-6, max_iter=1000, precond=None, raise_on_maxiter=False):
+        """CG (precond=None) or sketch-preconditioned CG (precond="srht"/"gauss")."""
+        n, d = A.shape
+        rep = Report()
+        kind = -1 if precond is None else KINDS.get(precond, precond)
+        st = _lib.ihs_cg(self.handle, _ptr(A), _ptr(b), n, d, float(nu), float(tol), int(max_iter), kind, _ptr(x),
+                         ctypes.byref(rep))
+        if st != IHS_OK and (st != IHS_EMAXITER or raise_on_maxiter):
+            _check("ihs_cg", st)
         return rep
 
     def destroy(self):
