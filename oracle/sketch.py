@@ -73,6 +73,22 @@ def gaussian_sketch(A, m, seed, level, block=8192):
     return out / np.sqrt(m)
 
 
+def gaussian_sketch_bf16(A, m, seed, level, block=8192):
+    """SA with both operands rounded to BF16 first: (1/sqrt(m)) bf16(z) bf16(A),
+    products and sums in float64."""
+    from .quant import bf16_round
+
+    A = np.asarray(A, dtype=np.float32)
+    n, d = A.shape
+    Aq = bf16_round(A).astype(np.float64)
+    out = np.zeros((m, d), dtype=np.float64)
+    for i0 in range(0, n, block):
+        i1 = min(n, i0 + block)
+        z = bf16_round(rng.gaussian_z_cols(m, i0, i1, seed, level).astype(np.float32)).astype(np.float64)
+        out += z @ Aq[i0:i1]
+    return out / np.sqrt(m)
+
+
 def sketch(A, m, kind, seed, level):
     if kind == "srht":
         return srht_sketch(A, m, seed, level)

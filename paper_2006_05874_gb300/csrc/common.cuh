@@ -88,6 +88,8 @@ int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, in
                      double nu, const float* x, float* g, double* d_axnorm2);
 int ihs_sketch_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m,
                        int32_t kind, uint64_t seed, int32_t level, float* SA);
+int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
+                         int32_t level, float* SA);
 int ihs_rows_enqueue(ihs_ctx* ctx, int64_t n_pad, int64_t m, uint64_t seed, int32_t level,
                      int32_t* rows);
 int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F);       // enqueue + check pivots (syncs)
@@ -158,6 +160,33 @@ __device__ __forceinline__ float4 gauss4(uint32_t i, uint32_t q, uint32_t level,
     const float2 a = box_muller(w.x, w.y);
     const float2 b = box_muller(w.z, w.w);
     return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Same draws with the fast hardware approximations of log and sin/cos (used
+// where the sketch is rounded to BF16 / FP8 anyway); differences from gauss4
+// are a few binary32 ulps.
+__device__ __forceinline__ float4 gauss4_fast(uint32_t i, uint32_t q, uint32_t level, uint32_t k0, uint32_t k1) {
+    const uint4 w = philox4x32_10(make_uint4(i, q, level, STREAM_GAUSS), k0, k1);
+    float4 z;
+    {
+        const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-8f;
+        const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-8f;
+        const float rad = sqrtf(-2.0f * __logf(u1));
+        float sn, cs;
+        __sincosf(6.283185307179586f * u2, &sn, &cs);
+        z.x = rad * cs;
+        z.y = rad * sn;
+    }
+    {
+        const float u1 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-8f;
+        const float u2 = (float)(w.w >> 8) * 5.9604644775390625e-8f;
+        const float rad = sqrtf(-2.0f * __logf(u1));
+        float sn, cs;
+        __sincosf(6.283185307179586f * u2, &sn, &cs);
+        z.z = rad * cs;
+        z.w = rad * sn;
+    }
+    return z;
 }
 
 // Error-free transformations (Knuth TwoSum; TwoProduct through FMA).  The

@@ -1,0 +1,69 @@
+"""The Gaussian sketch on tcgen05 tensor cores with BF16 operands.
+
+Parity: against the oracle's sketch of the BF16-rounded operands,
+(1/sqrt m) bf16(z) bf16(A) in FP64.  Both sides round the same FP32 A; the
+kernel's z comes from fast log/sin/cos, a few binary32 ulps from the oracle's,
+so a fraction ~2^-12 of the BF16 roundings of z can land on the neighbouring
+value (error 2^-8 |z| each): relative Frobenius error ~ 2^-8 sqrt(2^-12) = 6e-5,
+plus FP32 accumulation; tolerance 2e-4.  The error against the exact FP64
+sketch (BF16 operand rounding, ~2^-9 per product) is stated and bounded by 1e-2.
+"""
+import numpy as np
+import pytest
+
+from oracle import linalg, rng, sketch
+from oracle.quant import bf16_round
+from paper_2006_05874_gb300 import problems
+
+pytestmark = pytest.mark.gpu
+TOL_Q = 2e-4
+
+
+def _run(torch, A, m, seed, level):
+    from paper_2006_05874_gb300 import ihs
+
+    ctx = ihs.Context(kind="gauss", precision="bf16")
+    SA = torch.full((m, A.shape[1]), float("nan"), device="cuda")
+    ctx.sketch(torch.from_numpy(np.ascontiguousarray(A)).cuda(), m, "gauss", seed, level, SA)
+    out = SA.cpu().numpy().astype(np.float64)
+    ctx.destroy()
+    return out
+
+
+def _relfro(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("n,d,m", [(4096, 256, 1), (4096, 256, 64), (4096, 256, 128), (4096, 256, 300),
+                                   (3000, 100, 200), (5000, 300, 129), (64, 512, 16), (20000, 257, 40)])
+def test_gauss_bf16_parity(torch_cuda, n, d, m):
+    A = problems.random_matrix(n, d, seed=n + d + m)
+    got = _run(torch_cuda, A, m, 7, 3)
+    ref_q = sketch.gaussian_sketch_bf16(A, m, 7, 3)
+    assert _relfro(got, ref_q) <= TOL_Q
+    ref = sketch.gaussian_sketch(A, m, 7, 3)
+    assert _relfro(got, ref) <= 1e-2     # stated error against the exact FP64 sketch
+
+
+def test_gauss_bf16_full_size_sampled_rows(torch_cuda):
+    A = problems.random_matrix(131072, 2048, seed=21, scale=1.0 / 45.0)
+    m = 256
+    got = _run(torch_cuda, A, m, 2, 8)
+    which = [0, 127, 128, 255]
+    z = bf16_round(rng.gaussian_z_rows(which, 131072, 2, 8).astype(np.float32)).astype(np.float64)
+    ref = (z @ bf16_round(A).astype(np.float64)) / np.sqrt(m)
+    for k, j in enumerate(which):
+        assert _relfro(got[j], ref[k]) <= TOL_Q
+
+
+def test_solve_with_bf16_gaussian_sketch(ctx, torch_cuda):
+    """S only preconditions: the exact FP32-compensated gradient still drives the
+    iterate to the FP64 solution."""
+    torch = torch_cuda
+    p = problems.exp_decay(n=4096, d=256, seed=0)
+    xs = linalg.direct_solve(p.A, p.b, p.nu)
+    ctx.set_params(kind="gauss", variant="gd", precision="bf16", tol=1e-5)
+    x = torch.zeros(p.d, device="cuda")
+    rep = ctx.solve(torch.from_numpy(p.A).cuda(), torch.from_numpy(p.b).cuda(), p.nu, x)
+    assert rep.status == 0
+    assert linalg.relative_error(p.A, p.nu, x.cpu().numpy(), xs) <= 1e-5
