@@ -89,6 +89,34 @@ def gaussian_sketch_bf16(A, m, seed, level, block=8192):
     return out / np.sqrt(m)
 
 
+def fp8_column_scales(A):
+    """Per-column scales of the E4M3 sketch: s_j = fl32(amax_j / 448) (1 for a
+    zero column) and r_j = fl32(1 / s_j), in binary32 as the tensor-core path
+    defines them."""
+    A = np.asarray(A, dtype=np.float32)
+    amax = np.abs(A).max(axis=0).astype(np.float32)
+    s = np.where(amax > 0, amax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    r = (np.float32(1.0) / s).astype(np.float32)
+    return s, r
+
+
+def gaussian_sketch_fp8(A, m, seed, level, block=8192):
+    """SA with E4M3 operands and per-column scales:
+    (1/sqrt(m)) e4m3(z) e4m3(fl32(A r)) diag(s), sums in float64."""
+    from .quant import e4m3_round
+
+    A = np.asarray(A, dtype=np.float32)
+    n, d = A.shape
+    s, r = fp8_column_scales(A)
+    Aq = e4m3_round((A * r[None, :]).astype(np.float32).astype(np.float64))
+    out = np.zeros((m, d), dtype=np.float64)
+    for i0 in range(0, n, block):
+        i1 = min(n, i0 + block)
+        z = e4m3_round(rng.gaussian_z_cols(m, i0, i1, seed, level).astype(np.float32).astype(np.float64))
+        out += z @ Aq[i0:i1]
+    return out * s[None, :].astype(np.float64) / np.sqrt(m)
+
+
 def sketch(A, m, kind, seed, level):
     if kind == "srht":
         return srht_sketch(A, m, seed, level)

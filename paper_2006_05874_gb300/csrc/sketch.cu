@@ -446,8 +446,8 @@ int ihs_sketch_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64
     if (n < 1 || d < 1 || m < 1 || level < 0 || m > ((int64_t)1 << 31)) return IHS_EINVAL;
     if (kind == IHS_SKETCH_SRHT) return srht_enqueue(ctx, A, n, d, m, seed, level, SA);
     if (kind == IHS_SKETCH_GAUSS) {
-        if (ctx->p.precision == IHS_PREC_BF16) return ihs_gauss_tc_enqueue(ctx, A, n, d, m, seed, level, SA);
-        if (ctx->p.precision != IHS_PREC_FP32) return IHS_EINVAL;   // FP8 operands: not built
+        if (ctx->p.precision == IHS_PREC_BF16) return ihs_gauss_tc_enqueue(ctx, A, n, d, m, seed, level, SA, 0);
+        if (ctx->p.precision == IHS_PREC_FP8) return ihs_gauss_tc_enqueue(ctx, A, n, d, m, seed, level, SA, 1);
         return gauss_enqueue(ctx, A, n, d, m, seed, level, SA);
     }
     return IHS_EINVAL;

@@ -19,10 +19,10 @@ pytestmark = pytest.mark.gpu
 TOL_Q = 2e-4
 
 
-def _run(torch, A, m, seed, level):
+def _run(torch, A, m, seed, level, precision="bf16"):
     from paper_2006_05874_gb300 import ihs
 
-    ctx = ihs.Context(kind="gauss", precision="bf16")
+    ctx = ihs.Context(kind="gauss", precision=precision)
     SA = torch.full((m, A.shape[1]), float("nan"), device="cuda")
     ctx.sketch(torch.from_numpy(np.ascontiguousarray(A)).cuda(), m, "gauss", seed, level, SA)
     out = SA.cpu().numpy().astype(np.float64)
@@ -43,6 +43,36 @@ def test_gauss_bf16_parity(torch_cuda, n, d, m):
     assert _relfro(got, ref_q) <= TOL_Q
     ref = sketch.gaussian_sketch(A, m, 7, 3)
     assert _relfro(got, ref) <= 1e-2     # stated error against the exact FP64 sketch
+
+
+@pytest.mark.parametrize("n,d,m", [(4096, 256, 1), (4096, 256, 128), (4096, 256, 300), (3000, 100, 200),
+                                   (20000, 257, 40)])
+def test_gauss_fp8_parity(torch_cuda, n, d, m):
+    """E4M3 operands with per-column scales.  Both sides quantise A identically;
+    z's E4M3 rounding flips for a fraction ~2^-18 of entries (fast vs libm
+    z differ by ~2^-21 relative, E4M3 spacing 2^-3), each flip an error of one
+    E4M3 step (2^-3 |z|): relative Frobenius ~ 2^-3 sqrt(2^-18) = 2.4e-4;
+    tolerance 1e-3.  Stated error against the exact sketch: E4M3 rounding of
+    both operands, bounded by 0.1."""
+    A = problems.random_matrix(n, d, seed=n + 2 * d + m)
+    A[:, 3] *= 100.0     # columns of very different scales
+    A[:, 5] = 0.0        # and a zero column
+    got = _run(torch_cuda, A, m, 5, 2, precision="fp8")
+    ref_q = sketch.gaussian_sketch_fp8(A, m, 5, 2)
+    assert _relfro(got, ref_q) <= 1e-3
+    assert np.all(got[:, 5] == 0.0)
+    assert _relfro(got, sketch.gaussian_sketch(A, m, 5, 2)) <= 0.1
+
+
+def test_solve_with_fp8_gaussian_sketch(ctx, torch_cuda):
+    torch = torch_cuda
+    p = problems.exp_decay(n=4096, d=256, seed=0)
+    xs = linalg.direct_solve(p.A, p.b, p.nu)
+    ctx.set_params(kind="gauss", variant="gd", precision="fp8", tol=1e-5)
+    x = torch.zeros(p.d, device="cuda")
+    rep = ctx.solve(torch.from_numpy(p.A).cuda(), torch.from_numpy(p.b).cuda(), p.nu, x)
+    assert rep.status == 0
+    assert linalg.relative_error(p.A, p.nu, x.cpu().numpy(), xs) <= 1e-5
 
 
 def test_gauss_bf16_full_size_sampled_rows(torch_cuda):

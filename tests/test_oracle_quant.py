@@ -31,3 +31,16 @@ def test_e4m3_table_and_torch():
 def test_e4m3_saturates_and_keeps_representable():
     assert quant.e4m3_round(np.array([1000.0, -1e6]))[0] == 448.0
     assert np.array_equal(quant.e4m3_round(quant._E4M3), quant._E4M3)
+
+
+def test_fp8_sketch_scales_and_structure():
+    from oracle import sketch
+
+    A = np.random.default_rng(4).standard_normal((300, 6)).astype(np.float32)
+    A[:, 2] = 0.0
+    s, r = sketch.fp8_column_scales(A)
+    assert s[2] == 1.0 and np.all(np.abs(A * r[None, :]) <= 448.0 * (1 + 2 ** -20))
+    # with every operand exactly representable the quantised sketch is the sketch
+    got = sketch.gaussian_sketch_fp8(A, 5, 1, 0)
+    ref = sketch.gaussian_sketch(A, 5, 1, 0)
+    assert np.linalg.norm(got - ref) <= 0.1 * np.linalg.norm(ref)
