@@ -217,6 +217,54 @@ int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d
 int ihs_cg(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu, double tol,
            int32_t max_iter, int32_t precond_kind, float* x, ihs_report* rep_h);
 
+/* ---- learned warm start ------------------------------------------------- */
+/* Algorithm 1 may start the doubling of m at any power of two; the paper
+ * starts at m = 1.  These calls predict the level the doubling settles at
+ * (log2 m_T of a cold run) with a small network, so that a solve can start
+ * just below it.  The paper has no counterpart: this is an addition of the
+ * library.  A wrong prediction costs time only (the doubling still runs).
+ *
+ * Features (11 floats): log n, log d, log nu, then log sigma_k(P) for
+ * k = 1, 2, 3, 4, 6, 8, 12, 16, where P = G A (32 x d) is the Gaussian sketch
+ * of size 32 (N(0, 1/32) entries, the i.i.d. Gaussian draw of the sketch
+ * module at level 200 of `seed`, FP32 products) and sigma_k(P)^2 are the
+ * eigenvalues of P P^T in descending order (FP64 Gram, cyclic Jacobi),
+ * clamped below at 1e-10 lambda_1.
+ *
+ * Network (parameters: one flat FP32 device vector of ihs_mlp_num_params()
+ * entries): mu[11], sd[11], W1[64][11], b1[64], W2[64][64], b2[64], w3[64],
+ * b3; y = w3 . tanh(W2 tanh(W1 (x - mu) / sd + b1) + b2) + b3.  mu and sd are
+ * the feature normalisation, fixed by training and never updated.
+ * Every call runs one CTA on ctx's stream; X is B x 11 row-major. */
+int ihs_mlp_num_params(void);
+
+/* feat (device, 11 floats) <- the features of (A, nu).  A device FP32 n x d,
+ * nu > 0.  Asynchronous. */
+int ihs_probe_features(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, double nu,
+                       uint64_t seed, float* feat);
+
+/* y[B] <- network(X).  All device pointers.  Asynchronous. */
+int ihs_mlp_forward(ihs_ctx* ctx, const float* params, const float* X, int32_t B, float* y);
+
+/* grad (device, num_params) <- gradient of the mean squared error
+ * (1/B) sum_b (y_b - target_b)^2 with respect to params (zero for mu, sd);
+ * *loss_h (host, may be NULL) <- that loss, which makes the call synchronous. */
+int ihs_mlp_grad(ihs_ctx* ctx, const float* params, const float* X, const float* target,
+                 int32_t B, float* grad, double* loss_h);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step >= 1 the 1-based
+ * count for the bias corrections) on that loss, in place on params, adam_m and
+ * adam_v (device, num_params each, zero before step 1).  *loss_h (may be NULL)
+ * receives the loss at the parameters before the step. */
+int ihs_mlp_train_step(ihs_ctx* ctx, float* params, float* adam_m, float* adam_v, int32_t step,
+                       const float* X, const float* target, int32_t B, double lr, double* loss_h);
+
+/* *m0_h <- 2^clamp(floor(y) - 1, 0, floor(log2 n)) where y is the network's
+ * prediction for (A, nu) (optionally returned in *pred_h).  Synchronous.
+ * IHS_ENONFINITE if y is not finite. */
+int ihs_warm_start(ihs_ctx* ctx, const float* params, const float* A, int64_t n, int64_t d,
+                   double nu, uint64_t seed, int64_t* m0_h, float* pred_h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,8 @@ Each function cites the passage of the paper it restates.  Modules:
 * ``params``   - step sizes, momentum and rates (Thm 2.1, 2.2, Def 3.1, 3.2).
 * ``ihs``      - Algorithm 1 and its gradient-only variant.
 * ``cg``       - CG and sketch-preconditioned CG comparators (Sec. 5).
+* ``warmstart`` - probe features, the warm-start network, its gradient and
+                 the Adam step (an addition: no counterpart in the paper).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, library routines, published known-answer vectors or invariants

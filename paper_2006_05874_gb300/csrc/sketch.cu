@@ -441,6 +441,12 @@ int gauss_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m,
 
 }  // namespace
 
+int ihs_gauss_fp32_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
+                           int32_t level, float* SA) {
+    if (n < 1 || d < 1 || m < 1 || level < 0) return IHS_EINVAL;
+    return gauss_enqueue(ctx, A, n, d, m, seed, level, SA);
+}
+
 int ihs_sketch_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, int32_t kind,
                        uint64_t seed, int32_t level, float* SA) {
     if (n < 1 || d < 1 || m < 1 || level < 0 || m > ((int64_t)1 << 31)) return IHS_EINVAL;

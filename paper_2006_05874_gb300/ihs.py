@@ -69,6 +69,13 @@ _SIGNATURES = {
     "ihs_solve": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_cg": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i32, _i32, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_grad_noalloc": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, _vp], ctypes.c_int),
+    "ihs_mlp_num_params": ([], ctypes.c_int),
+    "ihs_probe_features": ([_vp, _vp, _i64, _i64, _dbl, _u64, _vp], ctypes.c_int),
+    "ihs_mlp_forward": ([_vp, _vp, _vp, _i32, _vp], ctypes.c_int),
+    "ihs_mlp_grad": ([_vp, _vp, _vp, _vp, _i32, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
+    "ihs_mlp_train_step": ([_vp, _vp, _vp, _vp, _i32, _vp, _vp, _i32, _dbl, ctypes.POINTER(_dbl)], ctypes.c_int),
+    "ihs_warm_start": ([_vp, _vp, _vp, _i64, _i64, _dbl, _u64, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_float)],
+                       ctypes.c_int),
 }
 
 _lib = None
@@ -234,6 +241,39 @@ class Context:
         if st != IHS_OK and (st != IHS_EMAXITER or raise_on_maxiter):
             _check("ihs_cg", st)
         return rep
+
+    # ---- learned warm start (no counterpart in the paper) ----
+    def probe_features(self, A, nu, seed, feat):
+        """feat (device float32, 11) <- the warm-start features of (A, nu)."""
+        n, d = A.shape
+        _check("ihs_probe_features", _lib.ihs_probe_features(self.handle, _ptr(A), n, d, float(nu), int(seed),
+                                                             _ptr(feat)))
+
+    def mlp_forward(self, params, X, y):
+        _check("ihs_mlp_forward", _lib.ihs_mlp_forward(self.handle, _ptr(params), _ptr(X), X.shape[0], _ptr(y)))
+
+    def mlp_grad(self, params, X, target, grad):
+        loss = ctypes.c_double(0.0)
+        _check("ihs_mlp_grad", _lib.ihs_mlp_grad(self.handle, _ptr(params), _ptr(X), _ptr(target), X.shape[0],
+                                                 _ptr(grad), ctypes.byref(loss)))
+        return loss.value
+
+    def mlp_train_step(self, params, adam_m, adam_v, step, X, target, lr, want_loss=True):
+        loss = ctypes.c_double(0.0)
+        _check("ihs_mlp_train_step", _lib.ihs_mlp_train_step(self.handle, _ptr(params), _ptr(adam_m), _ptr(adam_v),
+                                                             int(step), _ptr(X), _ptr(target), X.shape[0],
+                                                             float(lr), ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def warm_start(self, params, A, nu, seed=None):
+        """(m0, prediction): the initial sketch size the network suggests for (A, nu)."""
+        n, d = A.shape
+        m0 = ctypes.c_int64(0)
+        pred = ctypes.c_float(0.0)
+        seed = self.params.seed if seed is None else seed
+        _check("ihs_warm_start", _lib.ihs_warm_start(self.handle, _ptr(params), _ptr(A), n, d, float(nu), int(seed),
+                                                     ctypes.byref(m0), ctypes.byref(pred)))
+        return m0.value, pred.value
 
     def destroy(self):
         if getattr(self, "handle", None):

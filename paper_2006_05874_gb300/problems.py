@@ -135,3 +135,62 @@ def random_vector(d, seed, scale=1.0):
 def random_matrix(rows, cols, seed, scale=1.0):
     """A float32 N(0, scale^2) matrix (stand-alone sketches in factor tests)."""
     return (scale * np.random.default_rng(seed).standard_normal((rows, cols))).astype(np.float32)
+
+
+# Size grid of the warm-start training and held-out sets: n <= 65536,
+# n >= 16 d, n d <= 2^27 (512 MB of A).
+WARM_SIZES = tuple((n, d) for n in (2048, 4096, 8192, 16384, 32768, 65536)
+                   for d in (32, 64, 128, 256, 512, 1024, 2048) if n >= 16 * d and n * d <= (1 << 27))
+
+
+def sampled_ridge(seed, device, sizes=WARM_SIZES):
+    """One random instance of the warm-start family, built on `device`; the two
+    generators of the small and the spectral workloads with their parameters
+    drawn at random:
+
+    * "decay" (as ``exp_decay``): A = G diag(q^j), G i.i.d. N(0, 1), q ~ U[0.9, 0.999];
+    * "poly"  (as ``spectral``):  A = (G / sqrt(n)) diag(j^-p) V^T, p ~ U[0.5, 1.5],
+      V Haar; G / sqrt(n) stands in for the Haar U (its columns are orthonormal
+      up to O(sqrt(d / n))), which keeps the generation to one GEMM.
+
+    (n, d) is drawn from `sizes`; nu is set for a target effective dimension
+    drawn log-uniformly from [2, d/4] (from the nominal singular values
+    sqrt(n) q^j resp. j^-p), but nu >= 1e-3 sigma_1; b = A x0 + 0.01 N(0, I)
+    with x0 ~ N(0, I).  Returns (A, b, nu, meta) with A, b float32 torch tensors
+    on the device."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    n, d = sizes[int(rng.integers(len(sizes)))]
+    j = np.arange(1, d + 1, dtype=np.float64)
+    if rng.random() < 0.5:
+        q = float(rng.uniform(0.9, 0.999))
+        col = q ** j
+        sigma = math.sqrt(n) * col
+        fam = "decay%.4f" % q
+    else:
+        pw = float(rng.uniform(0.5, 1.5))
+        sigma = j ** (-pw)
+        fam = "poly%.3f" % pw
+    hi = max(2.5, d / 4.0)
+    target = float(math.exp(rng.uniform(math.log(2.0), math.log(hi))))
+    nu = nu_for_target(sigma, target)
+    if nu < 1e-3 * sigma[0]:
+        # keep (sigma_1 / nu)^2 <= 1e6: a float32 A cannot carry a sharper problem
+        nu = 1e-3 * float(sigma[0])
+        target = float(np.sum(sigma ** 2 / (sigma ** 2 + nu * nu)))
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(rng.integers(1 << 62)))
+    G = torch.randn(n, d, generator=gen, device=device, dtype=torch.float32)
+    if fam.startswith("decay"):
+        A = G * torch.as_tensor(col, device=device, dtype=torch.float32)[None, :]
+    else:
+        Vg = torch.randn(d, d, generator=gen, device=device, dtype=torch.float64)
+        V, R = torch.linalg.qr(Vg)
+        V = V * torch.sign(torch.diagonal(R))[None, :]
+        M = (torch.as_tensor(sigma, device=device, dtype=torch.float64)[:, None] * V.T).to(torch.float32)
+        A = (G @ M) / math.sqrt(n)
+    del G
+    x0 = torch.randn(d, generator=gen, device=device, dtype=torch.float32)
+    b = A @ x0 + 0.01 * torch.randn(n, generator=gen, device=device, dtype=torch.float32)
+    return A.contiguous(), b.contiguous(), float(nu), dict(n=n, d=d, family=fam, de_target=target, seed=seed)
