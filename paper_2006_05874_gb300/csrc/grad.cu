@@ -136,13 +136,14 @@ k_grad_fast(const float* __restrict__ A, const float* __restrict__ b, const floa
         for (; issued < min((int64_t)(stages - 1), my_tiles); ++issued) issue(issued);
     }
     int64_t consumed = 0;
-    for (int64_t l = 0; l < my_tiles; ++l) {
-        const int s = (int)(l % stages);
+    int s = 0;
+    uint32_t ph = 0;
+    for (int64_t l = 0; l < my_tiles; ++l, s = (s + 1 == stages ? 0 : s + 1), ph ^= (s == 0 ? 1u : 0u)) {
         if (tid == 0 && l + stages - 1 < my_tiles) {
             issue(l + stages - 1);
             issued = l + stages;
         }
-        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((l / stages) & 1), status);
+        const bool ok = mbar_wait_bounded(&full[s], ph, status);
         if (__syncthreads_or(!ok)) break;
         consumed = l + 1;
 
@@ -284,6 +285,359 @@ k_grad_fast(const float* __restrict__ A, const float* __restrict__ b, const floa
     }
 }
 
+// Wide-row fast path (1024 <= d <= 8192): warp-specialised, two-phase, with
+// packed FP32x2 arithmetic.
+//
+// Tiles of R rows (32 KB) stream through S shared-memory stages: a producer
+// thread issues one 1-D bulk copy for the rows and 4-byte cp.async copies for
+// their b entries, both completing on the stage's `full` mbarrier.  Sixteen
+// consumer warps split every row into NSEG column segments of 128 float4
+// chunks (warp w: row w / NSEG, segment w % NSEG) and run per tile:
+//   phase 1: per lane a compensated Dot2 partial of a_i . x over its 16
+//            columns (two at a time in packed FP32x2 registers), stored to
+//            shared memory;
+//   phase 2: for the previous tile, every consumer thread adds r_i a_i over
+//            the tile's rows into compensated accumulators for the CPT float4
+//            column chunks it owns.
+// A finaliser warp adds the 512 lane partials of a tile in a fixed tree (16
+// per lane, then a butterfly over the lanes of a row), forms
+// r_i = (hi - b_i) + lo and the FP64 ||A x||^2 terms, and publishes r.  All
+// hand-offs (tile landed, partials ready, r ready, stage free) are mbarriers
+// with bounded waits; no CTA-wide barrier sits on the streaming path.  The
+// partial layout and the final reduction are those of the path above.
+constexpr int kV3Consumers = 16;
+constexpr int kV3Threads = (kV3Consumers + 2) * 32;   // + finaliser + producer
+
+// packed FP32x2 (sm_100+): two independent IEEE binary32 operations per instruction
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_pack(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 x, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+// Two Acc2 accumulators in packed form.
+struct Acc2x2 {
+    f2 hi, lo;
+    // Dot2 step on both lanes: (hi, lo) += a * x exactly up to the final
+    // rounding of lo; xn = -x.  Same operations as Acc2::add_prod.
+    __device__ __forceinline__ void add_prod(f2 a, f2 x, f2 xn) {
+        const f2 np = f2_mul(a, xn);        // -p, p = fl(a x)
+        const f2 ep = f2_fma(a, x, np);     // a x - p
+        const f2 s = f2_sub(hi, np);        // hi + p
+        const f2 z = f2_sub(s, hi);
+        const f2 e1 = f2_sub(hi, f2_sub(s, z));
+        const f2 e2n = f2_add(np, z);       // -(p - z)
+        const f2 es = f2_sub(e1, e2n);
+        hi = s;
+        lo = f2_add(lo, f2_add(ep, es));
+    }
+    // Same operations as Acc2::add_pair.
+    __device__ __forceinline__ void add_pair(f2 h2, f2 l2) {
+        const f2 s = f2_add(hi, h2);
+        const f2 z = f2_sub(s, hi);
+        const f2 e = f2_add(f2_sub(hi, f2_sub(s, z)), f2_sub(h2, z));
+        hi = s;
+        lo = f2_add(lo, f2_add(e, l2));
+    }
+    // Same operations as Acc2::add.
+    __device__ __forceinline__ void add(f2 v) {
+        const f2 s = f2_add(hi, v);
+        const f2 z = f2_sub(s, hi);
+        const f2 e = f2_add(f2_sub(hi, f2_sub(s, z)), f2_sub(v, z));
+        hi = s;
+        lo = f2_add(lo, e);
+    }
+};
+
+struct V3Layout {
+    size_t pdot, bsh, rsh, bars, total;
+    __host__ __device__ V3Layout(int S, int R, int d) {
+        pdot = align16((size_t)S * R * d * sizeof(float));
+        bsh = pdot + (size_t)S * kV3Consumers * 32 * sizeof(Acc2);
+        rsh = align16(bsh + (size_t)S * R * sizeof(float));
+        bars = align16(rsh + (size_t)S * R * 2 * sizeof(float));
+        total = bars + 4 * (size_t)S * sizeof(uint64_t);
+    }
+};
+
+__device__ __forceinline__ void lds_f2x2(uint32_t addr, f2& a, f2& b) {
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a.v), "=l"(b.v) : "r"(addr));
+}
+__device__ __forceinline__ f2 lds_f2(uint32_t addr) {
+    f2 a;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(a.v) : "r"(addr));
+    return a;
+}
+
+template <int NSEG, int CPT, bool FULL>
+__global__ void __launch_bounds__(kV3Threads, 1)
+k_grad_v3(const float* __restrict__ A, const float* __restrict__ b, const float* __restrict__ x, int64_t n,
+          int d, int64_t ntiles, int S, float2* __restrict__ part, double* __restrict__ part_ax2,
+          unsigned* status) {
+    constexpr int R = kV3Consumers / NSEG;   // rows per tile
+    constexpr int XC = 4;                    // float4 chunks per lane per row
+    constexpr int LPR = 32 / R;              // finaliser lanes per row
+    constexpr int NP = kV3Consumers * 32;    // lane partials per tile
+    extern __shared__ __align__(128) unsigned char smem[];
+    const V3Layout lay(S, R, d);
+    float* stage_base = reinterpret_cast<float*>(smem);
+    Acc2* pdot = reinterpret_cast<Acc2*>(smem + lay.pdot);   // [S][R][NP / R]
+    float* bsh = reinterpret_cast<float*>(smem + lay.bsh);   // [S][R]
+    f2* rsh = reinterpret_cast<f2*>(smem + lay.rsh);         // [S][R], (r_i, r_i)
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
+    uint64_t* rready = full + S;
+    uint64_t* rfinal = rready + S;
+    uint64_t* empty = rfinal + S;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int chunks = d >> 2;
+    const int64_t t0 = (int64_t)blockIdx.x * ntiles / gridDim.x;
+    const int64_t t1 = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
+    const int64_t my_tiles = t1 - t0;
+    const size_t stage_floats = (size_t)R * d;
+    const uint32_t stage_bytes = (uint32_t)(stage_floats * sizeof(float));
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 2);   // bulk copy of the rows + cp.async of their b
+            mbar_init(&rready[s], kV3Consumers);
+            mbar_init(&rfinal[s], 1);
+            mbar_init(&empty[s], kV3Consumers);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == kV3Consumers + 1) {
+        // ---- producer ----
+        if (lane == 0) {
+            int64_t issued = 0;
+            bool ok = true;
+            int s = 0;
+            uint32_t ph = 0;   // parity of the stage's current use
+            for (int64_t l = 0; l < my_tiles; ++l) {
+                if (l >= S) {
+                    ok = mbar_wait_bounded(&empty[s], ph ^ 1u, status);
+                    if (!ok) break;
+                }
+                const int64_t row0 = (t0 + l) * R;
+                const int64_t rows = min((int64_t)R, n - row0);
+                const uint32_t bytes = (uint32_t)(rows * d * sizeof(float));
+                mbar_arrive_expect_tx(&full[s], bytes);
+                bulk_g2s(stage_base + (size_t)s * stage_floats, A + row0 * d, bytes, &full[s]);
+                for (int i = 0; i < (int)rows; ++i) cp_async_4(&bsh[s * R + i], b + row0 + i);
+                cp_async_mbar_arrive_noinc(&full[s]);
+                issued = l + 1;
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (!ok) {
+                // let the copies still in flight land before the CTA exits
+                for (int64_t l = max((int64_t)0, issued - S); l < issued; ++l)
+                    mbar_wait_bounded(&full[l % S], (uint32_t)((l / S) & 1), status);
+            }
+        }
+        return;
+    }
+
+    if (warp == kV3Consumers) {
+        // ---- finaliser: r_i and ||A x||^2 ----
+        // lane = row * LPR + q sums partials q, q + LPR, ... of its row, then
+        // the LPR lanes of the row combine by a butterfly.
+        const int frow = lane / LPR, q = lane % LPR;
+        double ax2 = 0.0;
+        bool ok = true;
+        int s = 0;
+        uint32_t ph = 0;
+        for (int64_t l = 0; l < my_tiles; ++l) {
+            const int rows = (int)min((int64_t)R, n - (t0 + l) * R);
+            ok = __all_sync(0xffffffffu, mbar_wait_bounded(&rready[s], ph, status));
+            if (!ok) break;
+            const Acc2* pr = pdot + ((size_t)s * R + frow) * (NP / R);
+            Acc2 acc = pr[q];
+#pragma unroll
+            for (int t = 1; t < NP / R / LPR; ++t) {
+                const Acc2 o = pr[t * LPR + q];
+                acc.add_pair(o.hi, o.lo);
+            }
+#pragma unroll
+            for (int off = LPR / 2; off >= 1; off >>= 1) {
+                const Acc2 o = acc2_shfl_xor(acc, off);
+                acc.add_pair(o.hi, o.lo);
+            }
+            if (q == 0) {
+                float r = 0.f;
+                if (frow < rows) {
+                    r = __fadd_rn(__fsub_rn(acc.hi, bsh[s * R + frow]), acc.lo);
+                    const double v = (double)acc.hi + (double)acc.lo;
+                    ax2 += v * v;
+                }
+                rsh[s * R + frow] = f2_pack(r, r);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&rfinal[s]);
+            if (++s == S) {
+                s = 0;
+                ph ^= 1u;
+            }
+        }
+        // fixed-order fold of the R row-lane sums
+        double tot = 0.0;
+        for (int i = 0; i < R; ++i) tot += __shfl_sync(0xffffffffu, ax2, i * LPR);
+        if (lane == 0) part_ax2[blockIdx.x] = ok ? tot : 0.0;
+        return;
+    }
+
+    // ---- consumers ----
+    const int seg = warp % NSEG, prow = warp / NSEG;
+    f2 xa[XC], xb[XC], xan[XC], xbn[XC];   // x chunk as (x, y) and (z, w), and negated
+    bool cv[XC];
+#pragma unroll
+    for (int k = 0; k < XC; ++k) {
+        const int c = seg * 32 + lane + NSEG * 32 * k;
+        cv[k] = FULL || c < chunks;
+        const float4 v = cv[k] ? reinterpret_cast<const float4*>(x)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        xa[k] = f2_pack(v.x, v.y);
+        xb[k] = f2_pack(v.z, v.w);
+        xan[k] = f2_pack(-v.x, -v.y);
+        xbn[k] = f2_pack(-v.z, -v.w);
+    }
+    bool pv[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) pv[k] = tid + kV3Consumers * 32 * k < chunks;
+    // shared-memory byte addresses: stage 0, this lane's phase-1 chunk 0 of its
+    // row, this thread's phase-2 chunk 0 of row 0, its pdot slot
+    const uint32_t sm0 = smem_u32(smem);
+    const uint32_t p1_off = (uint32_t)(prow * d + (seg * 32 + lane) * 4) * 4u;
+    const uint32_t p2_off = (uint32_t)tid * 16u;
+    const uint32_t row_bytes = (uint32_t)d * 4u;
+    const uint32_t pd0 = smem_u32(pdot) + (uint32_t)((prow * (NP / R) + seg * 32 + lane) * sizeof(Acc2));
+    const uint32_t pd_stage = (uint32_t)(R * (NP / R) * sizeof(Acc2));
+    const uint32_t rs0 = smem_u32(rsh);
+    Acc2x2 gacc[CPT][2];
+    const f2 zero2 = f2_pack(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < CPT; ++k)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) gacc[k][q] = Acc2x2{zero2, zero2};
+    bool ok = true;
+    int s1 = 0, s2 = 0;          // stages of phase 1 (tile l) and phase 2 (tile l - 1)
+    uint32_t ph1 = 0, ph2 = 0;   // their parities
+    for (int64_t l = 0; l <= my_tiles; ++l) {
+        if (l < my_tiles) {
+            const int rows = (int)min((int64_t)R, n - (t0 + l) * R);
+            ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s1], ph1, status));
+            if (!ok) break;
+            Acc2x2 pa{zero2, zero2}, pb{zero2, zero2};
+            if (prow < rows) {
+                const uint32_t base = sm0 + (uint32_t)s1 * stage_bytes + p1_off;
+#pragma unroll
+                for (int k = 0; k < XC; ++k) {
+                    if (cv[k]) {
+                        f2 a01, a23;
+                        lds_f2x2(base + (uint32_t)(k * NSEG * 32 * 16), a01, a23);
+                        pa.add_prod(a01, xa[k], xan[k]);
+                        pb.add_prod(a23, xb[k], xbn[k]);
+                    }
+                }
+            }
+            pa.add_pair(pb.hi, pb.lo);
+            float h0, h1, l0, l1;
+            f2_unpack(pa.hi, h0, h1);
+            f2_unpack(pa.lo, l0, l1);
+            Acc2 a0{h0, l0};
+            a0.add_pair(h1, l1);
+            asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(pd0 + (uint32_t)s1 * pd_stage), "f"(a0.hi),
+                         "f"(a0.lo)
+                         : "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&rready[s1]);
+            if (++s1 == S) {
+                s1 = 0;
+                ph1 ^= 1u;
+            }
+        }
+        if (l >= 1) {
+            const int rows = (int)min((int64_t)R, n - (t0 + l - 1) * R);
+            ok = __all_sync(0xffffffffu, mbar_wait_bounded(&rfinal[s2], ph2, status));
+            if (!ok) break;
+            const uint32_t base = sm0 + (uint32_t)s2 * stage_bytes + p2_off;
+            f2 rr[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) rr[i] = lds_f2(rs0 + (uint32_t)((s2 * R + i) * 8));
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+                if (pv[k]) {
+                    f2 s01 = zero2, s23 = zero2;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        if (i < rows) {
+                            f2 a01, a23;
+                            lds_f2x2(base + (uint32_t)i * row_bytes + (uint32_t)(k * kV3Consumers * 32 * 16), a01,
+                                     a23);
+                            s01 = f2_fma(rr[i], a01, s01);
+                            s23 = f2_fma(rr[i], a23, s23);
+                        }
+                    }
+                    gacc[k][0].add(s01);
+                    gacc[k][1].add(s23);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s2]);
+            if (++s2 == S) {
+                s2 = 0;
+                ph2 ^= 1u;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        const int c = tid + kV3Consumers * 32 * k;
+        if (pv[k]) {
+            float h0, h1, h2, h3, l0, l1, l2, l3;
+            f2_unpack(gacc[k][0].hi, h0, h1);
+            f2_unpack(gacc[k][0].lo, l0, l1);
+            f2_unpack(gacc[k][1].hi, h2, h3);
+            f2_unpack(gacc[k][1].lo, l2, l3);
+            float2* o = part + (size_t)blockIdx.x * d + 4 * c;
+            o[0] = make_float2(h0, l0);
+            o[1] = make_float2(h1, l1);
+            o[2] = make_float2(h2, l2);
+            o[3] = make_float2(h3, l3);
+        }
+    }
+    (void)ok;
+}
+
 // g[c] = fl32( sum_g (hi + lo)  + nu^2 x[c] ) over G partials in fixed order.
 __global__ void k_grad_reduce(const float2* __restrict__ part, const double* __restrict__ part_ax2, int G,
                               int d, double nu2, const float* __restrict__ x, float* __restrict__ g,
@@ -407,6 +761,35 @@ int launch_fast(ihs_ctx* ctx, const float* A, const float* b, const float* x, in
     return IHS_OK;
 }
 
+template <int NSEG, int CPT, bool FULL>
+int launch_v3(ihs_ctx* ctx, const float* A, const float* b, const float* x, int64_t n, int d, float2* part,
+              double* part_ax2, int* G_out) {
+    constexpr int R = kV3Consumers / NSEG;
+    const size_t stage_bytes = (size_t)R * d * sizeof(float);
+    int S = (int)std::min<size_t>(8, (192 * 1024) / stage_bytes);
+    if (S < 3) return IHS_EINVAL;
+    const size_t smem = V3Layout(S, R, d).total;
+    const int64_t ntiles = ceil_div64(n, R);
+    int64_t G = ctx->sm_count;
+    if (G > ntiles) G = ntiles;
+    auto kern = k_grad_v3<NSEG, CPT, FULL>;
+    IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)G, kV3Threads, smem, ctx->stream>>>(A, b, x, n, d, ntiles, S, part, part_ax2, ctx->d_status);
+    IHS_LAUNCH_CHECK();
+    *G_out = (int)G;
+    return IHS_OK;
+}
+
+// Segments per row of the wide-row path for this d: the smallest power of two
+// NSEG >= 2 with d / 4 <= 128 NSEG (0: the path does not apply).
+int pick_v3(int64_t d) {
+    if (d < 1024 || d > 8192 || d % 4) return 0;
+    const int64_t chunks = d / 4;
+    int nseg = 2;
+    while (128 * nseg < chunks) nseg *= 2;
+    return nseg;
+}
+
 }  // namespace
 
 int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
@@ -420,7 +803,20 @@ int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, in
     float2* part = static_cast<float2*>(ws);
     double* part_ax2 = reinterpret_cast<double*>(static_cast<char*>(ws) + part_bytes);
     int G = 0;
-    if (aligned && n >= 1) {
+    const int wpr = aligned ? pick_v3(d) : 0;
+    if (wpr) {
+        int st;
+        const bool full = (d % (wpr * 512)) == 0;
+        if (wpr == 2) st = full ? launch_v3<2, 1, true>(ctx, A, b, x, n, (int)d, part, part_ax2, &G)
+                                : launch_v3<2, 1, false>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (wpr == 4) st = full ? launch_v3<4, 1, true>(ctx, A, b, x, n, (int)d, part, part_ax2, &G)
+                                     : launch_v3<4, 1, false>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (wpr == 8) st = full ? launch_v3<8, 2, true>(ctx, A, b, x, n, (int)d, part, part_ax2, &G)
+                                     : launch_v3<8, 2, false>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        else st = full ? launch_v3<16, 4, true>(ctx, A, b, x, n, (int)d, part, part_ax2, &G)
+                       : launch_v3<16, 4, false>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
+        IHS_TRY(st);
+    } else if (aligned && n >= 1) {
         const FastCfg c = pick_fast((int)d);
         int st;
         if (c.tpr == 32) st = launch_fast<32, 1, 8, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);

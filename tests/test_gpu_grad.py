@@ -35,6 +35,7 @@ def _check(torch, ctx, A, b, nu, x):
 
 @pytest.mark.parametrize("n,d", [(1, 4), (7, 8), (1000, 32), (4096, 128), (4099, 256), (3000, 512),
                                  (2500, 1024), (1000, 2048), (700, 4096), (300, 8192),
+                                 (1001, 2048), (333, 1056), (5, 2048), (701, 4096), (3, 8192),
                                  (100, 37), (513, 3), (50, 9000)])
 def test_grad_random_point(ctx, torch_cuda, n, d):
     A = problems.random_matrix(n, d, seed=n + d)
@@ -51,14 +52,15 @@ def test_grad_near_solution_exp_decay(ctx, torch_cuda):
     assert np.linalg.norm(g) < 1e-3 * np.linalg.norm(p.A.astype(np.float64).T @ p.b)
 
 
-def test_grad_deterministic(ctx, torch_cuda):
+@pytest.mark.parametrize("d", [512, 2048])
+def test_grad_deterministic(ctx, torch_cuda, d):
     torch = torch_cuda
-    A = torch.from_numpy(problems.random_matrix(20000, 512, seed=1)).cuda()
+    A = torch.from_numpy(problems.random_matrix(20000, d, seed=1)).cuda()
     b = torch.from_numpy(problems.random_vector(20000, seed=2)).cuda()
-    x = torch.from_numpy(problems.random_vector(512, seed=3)).cuda()
+    x = torch.from_numpy(problems.random_vector(d, seed=3)).cuda()
     outs = []
     for _ in range(3):
-        g = torch.empty(512, device="cuda")
+        g = torch.empty(d, device="cuda")
         ctx.grad(A, b, 0.1, x, g)
         outs.append(g.cpu().numpy())
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
