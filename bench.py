@@ -192,7 +192,7 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_profile(what):
+def run_profile(what, rows=N_ROWS):
     """Warm up, then run the named piece once inside the NVTX range "profiled"
     (for ncu --nvtx --nvtx-include "profiled/" or -k/-s/-c captures)."""
     import torch
@@ -212,9 +212,9 @@ def run_profile(what):
     else:
         gen = torch.Generator(device="cuda")
         gen.manual_seed(0)
-        A = torch.randn(N_ROWS, D_COLS, device="cuda", generator=gen) / 45.0
+        A = torch.randn(rows, D_COLS, device="cuda", generator=gen) / 45.0
         if what == "grad":
-            b = torch.randn(N_ROWS, device="cuda", generator=gen) * 0.01
+            b = torch.randn(rows, device="cuda", generator=gen) * 0.01
             x = torch.randn(D_COLS, device="cuda", generator=gen)
             g = torch.empty(D_COLS, device="cuda")
             fn = lambda: ctx.grad(A, b, 0.015, x, g, want_axnorm2=False)
@@ -231,6 +231,57 @@ def run_profile(what):
     torch.cuda.nvtx.range_pop()
     ctx.destroy()
     print("profiled", what)
+
+
+def solver_forms(ihs, ctx, p, A, b, x_star, stream, steps):
+    """The same solve in the forms this library adds: the learned warm start
+    (m0 from the trained network, probe included in the time) with the SRHT
+    sketch and with the BF16 / FP8 Gaussian sketch on tensor cores, and the
+    BF16 Gaussian sketch from m = 1.  Each form's tolerance is tightened until
+    its verified error is <= 1e-5; times are device time per solve."""
+    import torch
+
+    from oracle import linalg
+    from paper_2006_05874_gb300 import warmstart
+
+    out = {}
+    forms = (("srht_warm", "srht", "fp32", True), ("gauss_bf16_warm", "gauss", "bf16", True),
+             ("gauss_fp8_warm", "gauss", "fp8", True), ("gauss_bf16_cold", "gauss", "bf16", False))
+    for name, kind, prec, warm in forms:
+        c2 = ihs.Context(kind=kind, variant="gd", precision=prec, tol=TOL, stream=stream)
+        ws2 = warmstart.WarmStart(c2) if warm else None
+        x = torch.zeros(p.d, device="cuda")
+
+        def run():
+            x.zero_()
+            if warm:
+                m0, _ = ws2.m0(A, p.nu)
+                c2.set_params(m_init=m0)
+            return c2.solve(A, b, p.nu, x)
+
+        tol = TOL
+        for _ in range(6):
+            c2.set_params(tol=tol)
+            run()
+            torch.cuda.synchronize()
+            err = linalg.relative_error(p.A, p.nu, x.cpu().numpy(), x_star)
+            if err <= TOL:
+                break
+            tol *= 0.5
+        run()
+        reps = max(1, min(5, steps))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            rep = run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms": e0.elapsed_time(e1) / reps, "rel_error": err, "tol": tol, "levels": rep.levels(),
+                     "iterations": rep.iterations, "grad_passes": rep.grad_passes,
+                     "ms_sketch_factor": rep.ms_sketch, "ms_iterate": rep.ms_iterate}
+        c2.destroy()
+    return out
 
 
 def _has_cuda():
@@ -250,12 +301,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["solve", "grad", "srht", "gauss"], default=None)
+    ap.add_argument("--profile-rows", type=int, default=N_ROWS,
+                    help="rows of A for --profile grad|srht|gauss (a smaller case for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.profile:
-        run_profile(args.profile)
+        run_profile(args.profile, args.profile_rows)
         return
     import torch
 
@@ -376,6 +429,8 @@ def main():
                              "residual_tol": rtol, "rel_error": cerr, "sketch_m": int(crep.m_final),
                              "ms_precond_setup": crep.ms_sketch}
 
+    forms = solver_forms(ihs, ctx, p, A, b, x_star, stream, args.steps)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(p)
@@ -397,10 +452,10 @@ def main():
                    "variant": "gd", "l2": "inputs larger than L2 (A is 1 GiB)",
                    "rel_error": err, "rel_error_e2e": err_e2e, "levels": r0.levels(), "iterations": r0.iterations,
                    "grad_passes_per_solve": r0.grad_passes, "ms_sketch_factor": r0.ms_sketch,
-                   "ms_iterate": r0.ms_iterate, "comparators_same_gpu": comparators},
+                   "ms_iterate": r0.ms_iterate, "comparators_same_gpu": comparators, "forms_same_gpu": forms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(), "peak_source": peak_kind,
-                     "kernel": "gradient pass (k_grad_fast + k_grad_reduce)", "ms_per_launch": ms_grad,
+                     "kernel": "gradient pass (k_grad_v3 + k_grad_reduce)", "ms_per_launch": ms_grad,
                      "algorithmic_bytes": bytes_per_pass},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * p.n * p.d + 4 * p.n,
                 "d2h_bytes_per_step": 4 * p.d},

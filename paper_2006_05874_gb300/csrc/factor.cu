@@ -36,8 +36,12 @@ constexpr int FB = 64;   // block size of the FP64 Cholesky and of the inverse
 // compensated FP32 accumulation: FMA chains over 4 terms, each chain added to
 // a (hi, lo) pair by TwoSum; K stored in FP64.  X(r, k) = SA[r][k] (Woodbury)
 // or SA[k][r] (direct).
+// Split-K: blockIdx.y takes rows [y * kchunk, (y + 1) * kchunk) of the inner
+// dimension; with gridDim.y > 1 the (hi, lo) pairs go to `part` (one 64 x 64
+// tile of float2 per (split, tile)) for k_gram_reduce, else straight to G.
 __global__ void __launch_bounds__(256) k_gram_c32(const float* __restrict__ SA, int64_t d, int woodbury,
-                                                  int64_t kdim, int64_t K, double nu2, double* __restrict__ G) {
+                                                  int64_t kdim, int64_t K, int64_t kchunk, double nu2,
+                                                  double* __restrict__ G, float2* __restrict__ part) {
     __shared__ float xa[32][FB + 4];
     __shared__ float xb[32][FB + 4];
     const int64_t t = blockIdx.x;
@@ -51,21 +55,23 @@ __global__ void __launch_bounds__(256) k_gram_c32(const float* __restrict__ SA, 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = 0.f;
-    for (int64_t k0 = 0; k0 < K; k0 += 32) {
+    const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
+    const int64_t kend = min(K, kbeg + kchunk);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += 32) {
         __syncthreads();
         if (woodbury) {
             for (int e = threadIdx.x; e < 32 * FB; e += 256) {
                 const int rr = e / 32, kk = e % 32;
                 const int64_t ra = I * FB + rr, rb = J * FB + rr, k = k0 + kk;
-                xa[kk][rr] = (ra < kdim && k < K) ? SA[ra * d + k] : 0.f;
-                xb[kk][rr] = (rb < kdim && k < K) ? SA[rb * d + k] : 0.f;
+                xa[kk][rr] = (ra < kdim && k < kend) ? SA[ra * d + k] : 0.f;
+                xb[kk][rr] = (rb < kdim && k < kend) ? SA[rb * d + k] : 0.f;
             }
         } else {
             for (int e = threadIdx.x; e < 32 * FB; e += 256) {
                 const int kk = e / FB, rr = e % FB;
                 const int64_t ra = I * FB + rr, rb = J * FB + rr, k = k0 + kk;
-                xa[kk][rr] = (ra < kdim && k < K) ? SA[k * d + ra] : 0.f;
-                xb[kk][rr] = (rb < kdim && k < K) ? SA[k * d + rb] : 0.f;
+                xa[kk][rr] = (ra < kdim && k < kend) ? SA[k * d + ra] : 0.f;
+                xb[kk][rr] = (rb < kdim && k < kend) ? SA[k * d + rb] : 0.f;
             }
         }
         __syncthreads();
@@ -94,6 +100,14 @@ __global__ void __launch_bounds__(256) k_gram_c32(const float* __restrict__ SA, 
                 }
         }
     }
+    if (gridDim.y > 1) {
+        float2* pt = part + ((size_t)blockIdx.y * gridDim.x + t) * FB * FB;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) pt[(ty + 16 * a) * FB + tx + 16 * b] = make_float2(hi[a][b], lo[a][b]);
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -104,26 +118,55 @@ __global__ void __launch_bounds__(256) k_gram_c32(const float* __restrict__ SA, 
         }
 }
 
+// G tile t = sum over the KS splits (fixed order, FP64) of hi + lo, + nu^2 I.
+__global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ part, int KS, int64_t ntiles,
+                                                     int64_t kdim, double nu2, double* __restrict__ G) {
+    const int64_t t = blockIdx.x;
+    int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (I * (I + 1) / 2 > t) --I;
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    const int64_t J = t - I * (I + 1) / 2;
+    for (int e = threadIdx.x; e < FB * FB; e += 256) {
+        const int rr = e / FB, cc = e % FB;
+        const int64_t r = I * FB + rr, c = J * FB + cc;
+        if (r >= kdim || c >= kdim || c > r) continue;
+        double acc = 0.0;
+        for (int y = 0; y < KS; ++y) {
+            const float2 v = part[((size_t)y * ntiles + t) * FB * FB + e];
+            acc += (double)v.x + (double)v.y;
+        }
+        G[r * kdim + c] = acc + (r == c ? nu2 : 0.0);
+    }
+}
+
+// The FP64 Cholesky runs on CB x CB blocks (CB = 32): with FP64 at a small
+// fraction of the FP32 rate, the diagonal-block factorisation on one SM sits
+// on the critical path, and its cost grows as CB^3 per block step.
+constexpr int CB = 32;
+
 // Diagonal block [j0, j0+nb) of the FP64 Cholesky, in place, and its inverse
-// W = L_jj^{-1} (FB x FB, lower, at Wd) for the panel.  One rsqrt per pivot
-// keeps the dependent FP64 chain short (FP64 division and square root are long
-// latency sequences); the inverse reuses the reciprocal pivots.  Non-positive
-// or non-finite pivots set IHS_DEV_NOTPD (the pivot is replaced by 1 so that
-// the kernel finishes).
-__global__ void __launch_bounds__(256) k_potrf64(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
+// W = L_jj^{-1} (CB x CB, lower, at Wd) for the panel.  Per column: thread 0
+// forms the reciprocal pivot with one rsqrt (FP64 division and square root
+// are long dependent sequences); then every thread updates its trailing
+// entries with the unscaled column and 1/pivot, while column j is scaled in
+// the next column's first phase.  Non-positive or non-finite pivots set
+// IHS_DEV_NOTPD (the pivot is replaced by 1 so that the kernel finishes).
+__global__ void __launch_bounds__(256) k_potrf32(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
                                                  double* __restrict__ Wd, unsigned* status) {
-    __shared__ double a[FB][FB + 1];
-    __shared__ double w[FB][FB + 1];
-    __shared__ double dinv[FB];
+    __shared__ double a[CB][CB + 1];
+    __shared__ double w[CB][CB + 1];
+    __shared__ double dinv[CB];
     __shared__ int bad;
     const int tid = threadIdx.x;
     if (tid == 0) bad = 0;
-    for (int e = tid; e < FB * FB; e += 256) {
-        const int r = e / FB, c = e % FB;
-        if (r < nb && c < nb && c <= r) a[r][c] = Kmat[(j0 + r) * k + j0 + c];
+    for (int e = tid; e < CB * CB; e += 256) {
+        const int r = e / CB, c = e % CB;
+        a[r][c] = (r < nb && c < nb && c <= r) ? Kmat[(j0 + r) * k + j0 + c] : 0.0;
+        w[r][c] = (r == c) ? 1.0 : 0.0;
     }
     __syncthreads();
-    const int tr = tid / 16, tc = tid % 16;   // 16 x 16 thread grid, no divisions in the loops
+    // thread -> (row r, two columns c, c + 16) of the lower triangle
+    const int tr = tid >> 3, tc = tid & 7;
     for (int j = 0; j < nb; ++j) {
         if (tid == 0) {
             double p = a[j][j];
@@ -135,31 +178,36 @@ __global__ void __launch_bounds__(256) k_potrf64(double* __restrict__ Kmat, int6
             a[j][j] = p * ri;
             dinv[j] = ri;
         }
+        if (j > 0 && tid >= j && tid < nb) a[tid][j - 1] *= dinv[j - 1];   // scale column j-1
         __syncthreads();
         const double ip = dinv[j];
-        if (tid > j && tid < nb) a[tid][j] *= ip;
-        __syncthreads();
-        // only the needed FMAs are issued: predicated-off lanes still occupy the FP64 pipe
-        for (int r = j + 1 + tr; r < nb; r += 16) {
-            const double arj = a[r][j];
-            for (int c = j + 1 + tc; c <= r; c += 16) a[r][c] = fma(-arj, a[c][j], a[r][c]);
+        const double ip2 = ip * ip;
+        if (tr > j && tr < nb) {
+            const double arj = a[tr][j] * ip2;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int c = tc + 8 * h;
+                if (c > j && c <= tr) a[tr][c] = fma(-arj, a[c][j], a[tr][c]);
+            }
         }
         __syncthreads();
     }
     // W = L^{-1} by right-looking forward substitution on the identity.
-    for (int e = tid; e < FB * FB; e += 256) w[e / FB][e % FB] = (e / FB == e % FB) ? 1.0 : 0.0;
-    __syncthreads();
     for (int l = 0; l < nb; ++l) {
         if (tid <= l) w[l][tid] *= dinv[l];
         __syncthreads();
-        for (int r = l + 1 + tr; r < nb; r += 16) {
-            const double arl = a[r][l];
-            for (int c = tc; c <= l; c += 16) w[r][c] = fma(-arl, w[l][c], w[r][c]);
+        if (tr > l && tr < nb) {
+            const double arl = a[tr][l];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int c = tc + 8 * h;
+                if (c <= l) w[tr][c] = fma(-arl, w[l][c], w[tr][c]);
+            }
         }
         __syncthreads();
     }
-    for (int e = tid; e < FB * FB; e += 256) {
-        const int r = e / FB, c = e % FB;
+    for (int e = tid; e < CB * CB; e += 256) {
+        const int r = e / CB, c = e % CB;
         if (r < nb && c < nb && c <= r) Kmat[(j0 + r) * k + j0 + c] = a[r][c];
         Wd[e] = (r < nb && c < nb && c <= r) ? w[r][c] : 0.0;
     }
@@ -167,100 +215,87 @@ __global__ void __launch_bounds__(256) k_potrf64(double* __restrict__ Kmat, int6
 }
 
 // Panel: rows i in [j0+nb, k): L[i][j0:j0+nb] = K[i][j0:j0+nb] W^T with
-// W = L_jj^{-1} (16 rows per CTA, 256 threads: 4 rows x 64 columns each).
-constexpr int kPanelRows = 16;
-__global__ void __launch_bounds__(256) k_panel64(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
+// W = L_jj^{-1} (8 rows per CTA, thread = one entry).
+constexpr int kPanelRows = 8;
+__global__ void __launch_bounds__(256) k_panel32(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
                                                  const double* __restrict__ Wd) {
-    __shared__ double pr[kPanelRows][FB + 1];
-    __shared__ double wt[FB][FB + 1];
+    __shared__ double pr[kPanelRows][CB + 1];
+    __shared__ double wt[CB][CB + 1];
     const int64_t r0 = j0 + nb + (int64_t)blockIdx.x * kPanelRows;
-    for (int e = threadIdx.x; e < FB * FB; e += 256) wt[e % FB][e / FB] = Wd[e];   // wt[c][r] = W[r][c]
-    for (int e = threadIdx.x; e < kPanelRows * FB; e += 256) {
-        const int r = e / FB, c = e % FB;
+    for (int e = threadIdx.x; e < CB * CB; e += 256) wt[e % CB][e / CB] = Wd[e];   // wt[c][r] = W[r][c]
+    {
+        const int r = threadIdx.x / CB, c = threadIdx.x % CB;
         pr[r][c] = (r0 + r < k && c < nb) ? Kmat[(r0 + r) * k + j0 + c] : 0.0;
     }
     __syncthreads();
-    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int q = 0; q < nb; ++q) {
-        const double wq = wt[q][tx];   // W[tx][q]
-#pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a] = fma(pr[ty + 4 * a][q], wq, acc[a]);
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int64_t r = r0 + ty + 4 * a;
-        if (r < k && tx < nb) Kmat[r * k + j0 + tx] = acc[a];
-    }
+    const int tx = threadIdx.x % CB, ty = threadIdx.x / CB;
+    double acc = 0.0;
+    for (int q = 0; q < nb; ++q) acc = fma(pr[ty][q], wt[q][tx], acc);   // W[tx][q]
+    const int64_t r = r0 + ty;
+    if (r < k && tx < nb) Kmat[r * k + j0 + tx] = acc;
 }
 
 // Look-ahead pieces of the trailing update after block step j0 (panel P =
 // L[j1:, j0:j0+nb], j1 = j0 + nb):
-//  * k_syrk_next: the next block column, K[i][j1 : j1+64] -= P_i P_{j1..}^T for
-//    i >= j1 (lower part), 16 rows per CTA (short tiles keep the critical path
+//  * k_syrk_next: the next block column, K[i][j1 : j1+CB] -= P_i P_{j1..}^T for
+//    i >= j1 (lower part), 8 rows per CTA (short tiles keep the critical path
 //    of the factorisation short);
-//  * k_syrk_rest: every lower 64 x 64 tile of the trailing matrix from tile
-//    column 1 on (a 2-D grid; CTAs above the diagonal exit at once).
+//  * k_syrk_rest: every lower CB x CB tile of the trailing matrix from tile
+//    column 1 on (a 1-D grid over the lower tiles).
 __global__ void __launch_bounds__(256) k_syrk_next(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb) {
-    __shared__ double pr[16][FB + 1];
-    __shared__ double pc[FB][FB + 1];
+    __shared__ double pr[8][CB + 1];
+    __shared__ double pc[CB][CB + 1];
     const int64_t j1 = j0 + nb;
-    const int64_t r0 = j1 + (int64_t)blockIdx.x * 16;
-    const int ncol = (int)min((int64_t)FB, k - j1);
-    for (int e = threadIdx.x; e < FB * FB; e += 256) {
-        const int c = e / FB, q = e % FB;
+    const int64_t r0 = j1 + (int64_t)blockIdx.x * 8;
+    const int ncol = (int)min((int64_t)CB, k - j1);
+    for (int e = threadIdx.x; e < CB * CB; e += 256) {
+        const int c = e / CB, q = e % CB;
         pc[c][q] = (c < ncol && q < nb) ? Kmat[(j1 + c) * k + j0 + q] : 0.0;
     }
-    for (int e = threadIdx.x; e < 16 * FB; e += 256) {
-        const int r = e / FB, q = e % FB;
+    {
+        const int r = threadIdx.x / CB, q = threadIdx.x % CB;
         pr[r][q] = (r0 + r < k && q < nb) ? Kmat[(r0 + r) * k + j0 + q] : 0.0;
     }
     __syncthreads();
-    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int q = 0; q < nb; ++q) {
-        const double pcq = pc[tx][q];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a] = fma(pr[ty + 4 * a][q], pcq, acc[a]);
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int64_t r = r0 + ty + 4 * a, c = j1 + tx;
-        if (r < k && tx < ncol && c <= r) Kmat[r * k + c] -= acc[a];
-    }
+    const int tx = threadIdx.x % CB, ty = threadIdx.x / CB;
+    double acc = 0.0;
+    for (int q = 0; q < nb; ++q) acc = fma(pr[ty][q], pc[tx][q], acc);
+    const int64_t r = r0 + ty, c = j1 + tx;
+    if (r < k && tx < ncol && c <= r) Kmat[r * k + c] -= acc;
 }
 
 __global__ void __launch_bounds__(256) k_syrk_rest(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb) {
-    const int64_t I = blockIdx.y, J = blockIdx.x;   // trailing tile indices
-    if (J < 1 || J > I) return;
-    __shared__ double pa[FB][FB + 1];
-    __shared__ double pb[FB][FB + 1];
+    const int64_t t = blockIdx.x;
+    int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (I * (I + 1) / 2 > t) --I;
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    const int64_t J = t - I * (I + 1) / 2;   // trailing tile (I, J), J <= I
+    if (J < 1) return;
+    __shared__ double pa[CB][CB + 1];
+    __shared__ double pb[CB][CB + 1];
     const int64_t j1 = j0 + nb;
-    for (int e = threadIdx.x; e < FB * FB; e += 256) {
-        const int rr = e / FB, q = e % FB;
-        const int64_t ra = j1 + I * FB + rr, rb = j1 + J * FB + rr;
+    for (int e = threadIdx.x; e < CB * CB; e += 256) {
+        const int rr = e / CB, q = e % CB;
+        const int64_t ra = j1 + I * CB + rr, rb = j1 + J * CB + rr;
         pa[rr][q] = (ra < k && q < nb) ? Kmat[ra * k + j0 + q] : 0.0;
         pb[rr][q] = (rb < k && q < nb) ? Kmat[rb * k + j0 + q] : 0.0;
     }
     __syncthreads();
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[4][4] = {};
+    double acc[2][2] = {};
     for (int q = 0; q < nb; ++q) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = pa[ty + 16 * a][q];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = pb[tx + 16 * b][q];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        const double a0 = pa[ty][q], a1 = pa[ty + 16][q];
+        const double b0 = pb[tx][q], b1 = pb[tx + 16][q];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int64_t r = j1 + I * FB + ty + 16 * a, c = j1 + J * FB + tx + 16 * b;
+        for (int b = 0; b < 2; ++b) {
+            const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
             if (r < k && c <= r) Kmat[r * k + c] -= acc[a][b];
         }
 }
@@ -516,8 +551,28 @@ int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F) {
     double* Kmat = F->L;
     double* Wall = F->W;
     const int64_t K = F->woodbury ? F->d : F->m;
-    k_gram_c32<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(F->SA, F->d, F->woodbury, k, K, F->nu * F->nu, Kmat);
-    IHS_LAUNCH_CHECK();
+    {
+        // split the inner dimension so that at least two CTAs per SM work on
+        // the Gram, with at least 256 inner rows per split
+        const int64_t ntiles = T * (T + 1) / 2;
+        int64_t KS = std::max<int64_t>(1, ceil_div64(2 * (int64_t)ctx->sm_count, ntiles));
+        KS = std::min<int64_t>(KS, std::max<int64_t>(1, K / 256));
+        const int64_t kchunk = ceil_div64(ceil_div64(K, KS), 32) * 32;
+        KS = ceil_div64(K, kchunk);
+        float2* gpart = nullptr;
+        if (KS > 1) {
+            void* ws = nullptr;
+            IHS_TRY(ihs_scratch(ctx, SLOT_SKETCH_PART, (size_t)KS * ntiles * FB * FB * sizeof(float2), &ws));
+            gpart = static_cast<float2*>(ws);
+        }
+        k_gram_c32<<<dim3((unsigned)ntiles, (unsigned)KS), 256, 0, s>>>(F->SA, F->d, F->woodbury, k, K, kchunk,
+                                                                        F->nu * F->nu, Kmat, gpart);
+        IHS_LAUNCH_CHECK();
+        if (KS > 1) {
+            k_gram_reduce<<<(unsigned)ntiles, 256, 0, s>>>(gpart, (int)KS, ntiles, k, F->nu * F->nu, Kmat);
+            IHS_LAUNCH_CHECK();
+        }
+    }
     // Blocked right-looking Cholesky with one step of look-ahead: on the main
     // stream, diagonal block jb, its panel and the update of block column jb+1;
     // on the auxiliary stream, the rest of the trailing update of step jb,
@@ -527,26 +582,27 @@ int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F) {
     cudaStream_t aux = ctx->aux;
     IHS_CUDA_TRY(cudaEventRecord(ctx->fev[7], s));     // gram done
     IHS_CUDA_TRY(cudaStreamWaitEvent(aux, ctx->fev[7], 0));
-    for (int64_t jb = 0; jb < T; ++jb) {
-        const int64_t j0 = jb * FB;
-        const int nb = (int)std::min<int64_t>(FB, k - j0);
-        double* Wj = Wall + jb * FB * FB;
-        k_potrf64<<<1, 256, 0, s>>>(Kmat, k, j0, nb, Wj, ctx->d_status);
+    const int64_t TC = ceil_div64(k, CB);
+    for (int64_t jb = 0; jb < TC; ++jb) {
+        const int64_t j0 = jb * CB;
+        const int nb = (int)std::min<int64_t>(CB, k - j0);
+        double* Wj = Wall + jb * CB * CB;
+        k_potrf32<<<1, 256, 0, s>>>(Kmat, k, j0, nb, Wj, ctx->d_status);
         IHS_LAUNCH_CHECK();
         const int64_t rest = k - j0 - nb;
         if (rest > 0) {
-            k_panel64<<<(unsigned)ceil_div64(rest, kPanelRows), 256, 0, s>>>(Kmat, k, j0, nb, Wj);
+            k_panel32<<<(unsigned)ceil_div64(rest, kPanelRows), 256, 0, s>>>(Kmat, k, j0, nb, Wj);
             IHS_LAUNCH_CHECK();
             cudaEvent_t panel_done = ctx->fev[jb % 3];
             IHS_CUDA_TRY(cudaEventRecord(panel_done, s));
             // column jb+1 must not race with the previous step's rest update
             if (jb > 0) IHS_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fev[3 + (jb - 1) % 3], 0));
-            k_syrk_next<<<(unsigned)ceil_div64(rest, 16), 256, 0, s>>>(Kmat, k, j0, nb);
+            k_syrk_next<<<(unsigned)ceil_div64(rest, 8), 256, 0, s>>>(Kmat, k, j0, nb);
             IHS_LAUNCH_CHECK();
-            const int64_t Tr = ceil_div64(rest, FB);
+            const int64_t Tr = ceil_div64(rest, CB);
             IHS_CUDA_TRY(cudaStreamWaitEvent(aux, panel_done, 0));
             if (Tr > 1) {
-                k_syrk_rest<<<dim3((unsigned)Tr, (unsigned)Tr), 256, 0, aux>>>(Kmat, k, j0, nb);
+                k_syrk_rest<<<(unsigned)(Tr * (Tr + 1) / 2), 256, 0, aux>>>(Kmat, k, j0, nb);
                 IHS_LAUNCH_CHECK();
             }
             IHS_CUDA_TRY(cudaEventRecord(ctx->fev[3 + jb % 3], aux));
