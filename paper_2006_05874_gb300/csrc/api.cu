@@ -24,6 +24,8 @@ void ihs_set_last_cuda_error(cudaError_t e, const char* what, const char* file, 
              line, what);
 }
 
+void ihs_set_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 extern "C" const char* ihs_last_error(void) { return g_last_error; }
 
 extern "C" const char* ihs_version(void) { return "ihs-gb300 0.1 (sm_103a)"; }

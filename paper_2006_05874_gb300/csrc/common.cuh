@@ -32,6 +32,7 @@ void ihs_count_launch();
     } while (0)
 
 void ihs_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void ihs_set_error(const char* msg);   // message for ihs_last_error()
 
 // ---------------------------------------------------------------------------
 // Scratch arena: grow-only device buffers keyed by slot.
