@@ -202,6 +202,37 @@ int ihs_grad_noalloc(void* stream, const float* A, const float* b, int64_t n, in
 int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
               double nu, double tol, float* x, ihs_report* rep_h);
 
+/* ---- batched solves ------------------------------------------------------- */
+/* One ridge problem of a batch.  A (n x d, row-major FP32), b (n) and x (d)
+ * are device buffers owned by the caller; x holds x_1 on entry and x_T on
+ * exit.  Problems may share A (a regularisation path: one A, many nu and b). */
+typedef struct ihs_problem {
+    const float* A;
+    const float* b;
+    int64_t n, d;
+    double nu;
+    float* x;
+} ihs_problem;
+
+/* Solves every problem of probs_h[0..count) with the gradient-IHS variant
+ * (Sec. 5) under the context's parameters (kind, precision, rho, eta, m_init,
+ * max_iter, floor, seed; params.variant must be IHS_VARIANT_GD, else
+ * IHS_EINVAL).  Each problem runs the controller of ihs_solve, sketches keyed
+ * by (seed, level) as there; the batch advances all problems one iteration
+ * per round.  Problems that share A (same pointer, n and d; up to 64 per
+ * group) share each level's sketch and take one multi-right-hand-side
+ * gradient pass over A per round; the others take one launch over a work list
+ * of their row tiles, whose height is autotuned on the first round.  The round
+ * is captured once as a CUDA graph and replayed.  FP64 factorisations of
+ * level changes run concurrently on internal streams.  tol > 0 overrides
+ * params.tol.  reps_h (count entries, may be NULL): per-problem reports
+ * (ms_iterate = device time of all rounds of the batch).  Returns IHS_OK when
+ * the batch ran; per-problem outcomes (IHS_OK, IHS_EMAXITER, IHS_ENONFINITE)
+ * are in reps_h[i].status.  Synchronous.  Device memory: the problems'
+ * factors and sketches live at the same time. */
+int ihs_solve_batched(ihs_ctx* ctx, const ihs_problem* probs_h, int32_t count, double tol,
+                      ihs_report* reps_h);
+
 /* ---- comparators (Sec. 5) ------------------------------------------------ */
 /* Conjugate gradient on the normal equations (A^T A + nu^2 I) x = A^T b, or,
  * with precond_kind = IHS_SKETCH_SRHT / IHS_SKETCH_GAUSS, sketch-preconditioned

@@ -16,6 +16,7 @@ std::atomic<int64_t> g_launches{0};
 }
 
 void ihs_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void ihs_count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 extern "C" int64_t ihs_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 

@@ -25,6 +25,7 @@
     } while (0)
 
 void ihs_count_launch();
+void ihs_count_launches(int64_t n);   // kernels of one replayed CUDA graph
 #define IHS_LAUNCH_CHECK()                    \
     do {                                      \
         ihs_count_launch();                   \
@@ -96,6 +97,8 @@ int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int
 int ihs_rows_enqueue(ihs_ctx* ctx, int64_t n_pad, int64_t m, uint64_t seed, int32_t level,
                      int32_t* rows);
 int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F);       // enqueue + check pivots (syncs)
+int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F);     // enqueue only (pivot failures in d_status)
+int ihs_factor_alloc(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** out);
 // Factor into the context's scratch (no allocation once the slot is large
 // enough); F is caller storage, valid until the next call with the same ctx.
 int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t* F);

@@ -545,6 +545,11 @@ __global__ void k_direct_out(const float* __restrict__ g, const float2* __restri
 }  // namespace
 
 int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F) {
+    IHS_TRY(ihs_factor_enqueue(ctx, F));
+    return ihs_check_status(ctx);
+}
+
+int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
     const int64_t k = F->k;
     cudaStream_t s = ctx->stream;
     const int64_t T = ceil_div64(k, FB);
@@ -633,7 +638,7 @@ int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F) {
     dim3 tg((unsigned)ceil_div64(k, 32), (unsigned)ceil_div64(k, 32));
     k_transpose_f32<<<tg, 256, 0, s>>>(X, k, F->XT);
     IHS_LAUNCH_CHECK();
-    return ihs_check_status(ctx);
+    return IHS_OK;
 }
 
 // H_S^{-1} g with one step of iterative refinement: the FP32 inverse factor X
@@ -746,7 +751,7 @@ int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, doub
     return ihs_factor_build(ctx, F);
 }
 
-extern "C" int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** out) {
+int ihs_factor_alloc(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** out) {
     if (!ctx || !SA || !out || m < 1 || d < 1 || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
     *out = nullptr;
     ihs_factor_t* F = new (std::nothrow) ihs_factor_t;
@@ -771,6 +776,15 @@ extern "C" int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, d
         ihs_factor_destroy(F);
         return IHS_ENOMEM;
     }
+    *out = F;
+    return IHS_OK;
+}
+
+extern "C" int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** out) {
+    if (!out) return IHS_EINVAL;
+    *out = nullptr;
+    ihs_factor_t* F = nullptr;
+    IHS_TRY(ihs_factor_alloc(ctx, SA, m, d, nu, &F));
     const int st = ihs_factor_build(ctx, F);
     if (st != IHS_OK) {
         ihs_factor_destroy(F);

@@ -69,6 +69,7 @@ _SIGNATURES = {
     "ihs_solve": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_cg": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i32, _i32, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_grad_noalloc": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, _vp], ctypes.c_int),
+    "ihs_solve_batched": ([_vp, _vp, _i32, _dbl, _vp], ctypes.c_int),
     "ihs_mlp_num_params": ([], ctypes.c_int),
     "ihs_probe_features": ([_vp, _vp, _i64, _i64, _dbl, _u64, _vp], ctypes.c_int),
     "ihs_mlp_forward": ([_vp, _vp, _vp, _i32, _vp], ctypes.c_int),
@@ -172,6 +173,12 @@ class Factor:
             pass
 
 
+class Problem(ctypes.Structure):
+    """One problem of ihs_solve_batched (device pointers)."""
+    _fields_ = [("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int64),
+                ("nu", ctypes.c_double), ("x", ctypes.c_void_p)]
+
+
 class Context:
     """An ihs_ctx bound to a CUDA stream (torch's current stream by default)."""
 
@@ -230,6 +237,18 @@ class Context:
         if st != IHS_OK and (st != IHS_EMAXITER or raise_on_maxiter):
             _check("ihs_solve", st)
         return rep
+
+    def solve_batched(self, problems, tol=0.0):
+        """problems: sequence of (A, b, nu, x) device tensors (A may be shared).
+        Returns one Report per problem (each with its own status)."""
+        arr = (Problem * len(problems))()
+        for i, (A, b, nu, x) in enumerate(problems):
+            n, d = A.shape
+            arr[i] = Problem(_ptr(A).value, _ptr(b).value, n, d, float(nu), _ptr(x).value)
+        reps = (Report * len(problems))()
+        _check("ihs_solve_batched", _lib.ihs_solve_batched(self.handle, ctypes.byref(arr), len(problems),
+                                                           float(tol), ctypes.byref(reps)))
+        return list(reps)
 
     def cg(self, A, b, nu, x, tol=1e-6, max_iter=1000, precond=None, raise_on_maxiter=False):
         """CG (precond=None) or sketch-preconditioned CG (precond="srht"/"gauss")."""

@@ -1,0 +1,130 @@
+"""Batched solves (ihs_solve_batched): every problem of a batch against the FP64
+oracle's direct solution at the single solver's bar (1e-5 relative prediction
+norm), the schedule against the single solver's, and the edge cases."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import linalg
+from paper_2006_05874_gb300 import problems
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def _independent(seed, count, nmax=4096, dmax=256):
+    """Gaussian-entry problems with n >= 16 d (a Gaussian sketch needs room to
+    grow to about d_e / rho rows below its cap m = n)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        d = int(rng.integers(8, dmax + 1))
+        n = int(rng.integers(16 * d, max(16 * d, nmax) + 1))
+        A = rng.standard_normal((n, d)).astype(np.float32)
+        x0 = rng.standard_normal(d)
+        b = (A @ x0 + 0.1 * rng.standard_normal(n)).astype(np.float32)
+        out.append((A, b, 1.0))
+    return out
+
+
+def _path(n=8192, d=256, K=8, seed=3):
+    rng = np.random.default_rng(seed)
+    p = problems.spectral(n, d, sigma=np.arange(1, d + 1) ** -0.5, nu=0.1, seed=seed)
+    nus = np.logspace(-3, 1, K)
+    bs = []
+    for k in range(K):
+        x0 = rng.standard_normal(d)
+        bs.append((p.A.astype(np.float64) @ x0 + 0.01 * rng.standard_normal(n)).astype(np.float32))
+    return p.A, bs, nus
+
+
+@pytest.mark.parametrize("kind", ["srht", "gauss"])
+def test_batch_independent_matches_oracle_and_single(ctx, torch_cuda, kind):
+    torch = torch_cuda
+    ctx.set_params(kind=kind, variant="gd")
+    probs = _independent(11, 7, nmax=4096, dmax=128)
+    dev = [(_dev(torch, A), _dev(torch, b), nu, torch.zeros(A.shape[1], device="cuda")) for A, b, nu in probs]
+    reps = ctx.solve_batched(dev)
+    for (A, b, nu), (Ad, bd, _, x), rep in zip(probs, dev, reps):
+        assert rep.status == 0
+        xs = linalg.direct_solve(A, b, nu)
+        assert linalg.relative_error(A, nu, x.cpu().numpy(), xs) <= 1e-5
+        # the single solver on the same problem takes the same schedule
+        x1 = torch.zeros(A.shape[1], device="cuda")
+        r1 = ctx.solve(Ad, bd, nu, x1)
+        assert rep.levels() == r1.levels()
+        assert rep.iterations == r1.iterations
+
+
+def test_batch_ridge_path_shared_A(ctx, torch_cuda):
+    torch = torch_cuda
+    ctx.set_params(kind="srht", variant="gd")
+    A, bs, nus = _path()
+    Ad = _dev(torch, A)
+    dev = [(Ad, _dev(torch, b), nu, torch.zeros(A.shape[1], device="cuda")) for b, nu in zip(bs, nus)]
+    reps = ctx.solve_batched(dev)
+    for b, nu, (_, _, _, x), rep in zip(bs, nus, dev, reps):
+        assert rep.status == 0
+        xs = linalg.direct_solve(A, b, nu)
+        assert linalg.relative_error(A, nu, x.cpu().numpy(), xs) <= 1e-5, nu
+    # larger nu: smaller effective dimension, the doubling stops earlier
+    assert reps[-1].m_final <= reps[0].m_final
+
+
+def test_batch_mixed_groups_and_singletons(ctx, torch_cuda):
+    torch = torch_cuda
+    ctx.set_params(kind="gauss", variant="gd")
+    A, bs, nus = _path(n=4096, d=128, K=3, seed=5)
+    Ad = _dev(torch, A)
+    dev = [(Ad, _dev(torch, b), nu, torch.zeros(A.shape[1], device="cuda")) for b, nu in zip(bs, nus)]
+    ind = _independent(12, 3, nmax=3000, dmax=96)
+    dev += [(_dev(torch, a), _dev(torch, b), nu, torch.zeros(a.shape[1], device="cuda")) for a, b, nu in ind]
+    host = [(A, b, nu) for b, nu in zip(bs, nus)] + ind
+    reps = ctx.solve_batched(dev)
+    for (Ah, b, nu), (_, _, _, x), rep in zip(host, dev, reps):
+        assert rep.status == 0
+        assert linalg.relative_error(Ah, nu, x.cpu().numpy(), linalg.direct_solve(Ah, b, nu)) <= 1e-5
+
+
+def test_batch_edge_cases(ctx, torch_cuda):
+    torch = torch_cuda
+    ctx.set_params(kind="srht", variant="gd")
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((500, 20)).astype(np.float32)
+    b0 = np.zeros(500, dtype=np.float32)                      # x = 0 is the solution
+    b1 = (A @ rng.standard_normal(20)).astype(np.float32)
+    dev = [(_dev(torch, A), _dev(torch, b0), 0.5, torch.zeros(20, device="cuda")),
+           (_dev(torch, A.copy()), _dev(torch, b1), 0.5, torch.zeros(20, device="cuda"))]
+    reps = ctx.solve_batched(dev)
+    assert reps[0].status == 0 and reps[0].iterations == 1
+    assert np.all(dev[0][3].cpu().numpy() == 0.0)
+    assert linalg.relative_error(A, 0.5, dev[1][3].cpu().numpy(), linalg.direct_solve(A, b1, 0.5)) <= 1e-5
+    # a single problem in a batch
+    x = torch.zeros(20, device="cuda")
+    rep = ctx.solve_batched([(dev[1][0], dev[1][1], 0.5, x)])[0]
+    assert rep.status == 0
+    # iteration limit reported per problem
+    ctx.set_params(max_iter=2)
+    x = torch.zeros(20, device="cuda")
+    rep = ctx.solve_batched([(dev[1][0], dev[1][1], 1e-3, x)])[0]
+    assert rep.status == -6 and rep.iterations == 2
+    ctx.set_params(max_iter=1000)
+
+
+def test_batch_rejects_polyak_and_bad_args(ctx, torch_cuda):
+    from paper_2006_05874_gb300 import ihs
+
+    torch = torch_cuda
+    A = torch.zeros(16, 4, device="cuda")
+    b = torch.zeros(16, device="cuda")
+    x = torch.zeros(4, device="cuda")
+    ctx.set_params(variant="polyak")
+    with pytest.raises(ihs.IHSError):
+        ctx.solve_batched([(A, b, 1.0, x)])
+    ctx.set_params(variant="gd")
+    with pytest.raises(ihs.IHSError):
+        ctx.solve_batched([(A, b, -1.0, x)])
