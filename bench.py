@@ -284,6 +284,97 @@ def solver_forms(ihs, ctx, p, A, b, x_star, stream, steps):
     return out
 
 
+def batched_workload(ihs, stream, seed=0):
+    """The batched form: a 64-point ridge path on one A (262144 x 1024, sigma_j =
+    j^-1/2, nu log-spaced 1e-4..1e1, 64 distinct b) plus 256 independent
+    problems (n ~ U{2^10..2^14}, d ~ U{32..512}, Gaussian-entry A, nu = 1), all
+    in one ihs_solve_batched call (SRHT, gradient-IHS), from m = 1 and with the
+    learned warm start (its probe and prediction inside the time), against the
+    same problems solved one by one with ihs_solve from m = 1.  The warm-started
+    batch's solutions are checked on a sample against the FP64 direct solve."""
+    import torch
+
+    from oracle import linalg
+    from paper_2006_05874_gb300 import problems
+
+    rng = np.random.default_rng(seed)
+    n_p, d_p, K = 262144, 1024, 64
+    pp = problems.spectral(n=n_p, d=d_p, sigma=np.arange(1, d_p + 1) ** -0.5, nu=1.0, seed=seed, device="cuda")
+    Ap = torch.from_numpy(pp.A).cuda()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed + 1)
+    nus = np.logspace(-4, 1, K)
+    path = []
+    for k in range(K):
+        x0 = torch.randn(d_p, generator=gen, device="cuda")
+        b = Ap @ x0 + 0.01 * torch.randn(n_p, generator=gen, device="cuda")
+        path.append((Ap, b.contiguous(), float(nus[k])))
+    ind = []
+    for i in range(256):
+        n = int(rng.integers(1 << 10, (1 << 14) + 1))
+        d = int(rng.integers(32, 513))
+        A = torch.randn(n, d, generator=gen, device="cuda")
+        x0 = torch.randn(d, generator=gen, device="cuda")
+        b = A @ x0 + 0.1 * torch.randn(n, generator=gen, device="cuda")
+        ind.append((A, b.contiguous(), 1.0))
+    allp = path + ind
+    from paper_2006_05874_gb300 import warmstart
+
+    ctx = ihs.Context(kind="srht", variant="gd", tol=TOL, stream=stream)
+    ws = warmstart.WarmStart(ctx)
+    xs = [torch.zeros(A.shape[1], device="cuda") for A, _, _ in allp]
+
+    def batch(warm):
+        for x in xs:
+            x.zero_()
+        m0 = ctx.warm_start_batched(ws.params, allp)[0] if warm else None
+        return ctx.solve_batched([(A, b, nu, x) for (A, b, nu), x in zip(allp, xs)], m_init=m0)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    timed = {}
+    for warm in (False, True):
+        batch(warm)   # warm-up (allocations, graph capture, autotuning)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        reps = batch(warm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        timed[warm] = (e0.elapsed_time(e1), reps)
+    ms_batch, reps_cold = timed[False]
+    ms_batch_warm, reps = timed[True]
+    # one by one
+    xq = [torch.zeros(A.shape[1], device="cuda") for A, _, _ in allp]
+    ctx.solve(*allp[0][:3], xq[0])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for (A, b, nu), x in zip(allp, xq):
+        ctx.solve(A, b, nu, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    # parity on a sample: both ends of the path and eight independent problems
+    sample = [0, K - 1] + [K + int(i) for i in rng.choice(256, 8, replace=False)]
+    errs = []
+    for i in sample:
+        A, b, nu = allp[i]
+        Ah, bh = A.cpu().numpy(), b.cpu().numpy()
+        xstar = linalg.direct_solve(Ah, bh, nu)
+        errs.append(linalg.relative_error(Ah, nu, xs[i].cpu().numpy(), xstar))
+    ctx.destroy()
+    return {"workload": "ridge path 262144x1024 (64 nu, 64 b) + 256 independent Gaussian problems "
+                        "n~U[2^10,2^14], d~U[32,512], nu=1; srht gd",
+            "problems": len(allp), "ms_batch_warm_start": ms_batch_warm, "ms_batch_from_m1": ms_batch,
+            "ms_one_by_one_from_m1": ms_seq, "speedup_warm_batch_vs_one_by_one": ms_seq / ms_batch_warm,
+            "speedup_batch_vs_one_by_one": ms_seq / ms_batch,
+            "statuses_ok": int(sum(1 for r in reps if r.status == 0)),
+            "statuses_ok_from_m1": int(sum(1 for r in reps_cold if r.status == 0)),
+            "max_rel_error_sampled": float(max(errs)), "sampled": len(sample),
+            "path_m_final": [int(reps[0].m_final), int(reps[K - 1].m_final)],
+            "grad_passes_total": int(sum(r.grad_passes for r in reps)),
+            "rounds": int(max(r.grad_passes for r in reps)),
+            "ms_rounds_device": float(reps[0].ms_iterate), "ms_level_changes_wall": float(reps[0].ms_sketch)}
+
+
 def _has_cuda():
     try:
         import torch
@@ -430,6 +521,7 @@ def main():
                              "ms_precond_setup": crep.ms_sketch}
 
     forms = solver_forms(ihs, ctx, p, A, b, x_star, stream, args.steps)
+    batched = batched_workload(ihs, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -452,7 +544,8 @@ def main():
                    "variant": "gd", "l2": "inputs larger than L2 (A is 1 GiB)",
                    "rel_error": err, "rel_error_e2e": err_e2e, "levels": r0.levels(), "iterations": r0.iterations,
                    "grad_passes_per_solve": r0.grad_passes, "ms_sketch_factor": r0.ms_sketch,
-                   "ms_iterate": r0.ms_iterate, "comparators_same_gpu": comparators, "forms_same_gpu": forms},
+                   "ms_iterate": r0.ms_iterate, "comparators_same_gpu": comparators, "forms_same_gpu": forms,
+                   "batched_same_gpu": batched},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(), "peak_source": peak_kind,
                      "kernel": "gradient pass (k_grad_v3 + k_grad_reduce)", "ms_per_launch": ms_grad,

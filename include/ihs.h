@@ -212,6 +212,8 @@ typedef struct ihs_problem {
     int64_t n, d;
     double nu;
     float* x;
+    int64_t m_init;   /* initial sketch size of this problem (a power of two),
+                         e.g. from ihs_warm_start; 0 = params.m_init */
 } ihs_problem;
 
 /* Solves every problem of probs_h[0..count) with the gradient-IHS variant
@@ -226,12 +228,20 @@ typedef struct ihs_problem {
  * is captured once as a CUDA graph and replayed.  FP64 factorisations of
  * level changes run concurrently on internal streams.  tol > 0 overrides
  * params.tol.  reps_h (count entries, may be NULL): per-problem reports
- * (ms_iterate = device time of all rounds of the batch).  Returns IHS_OK when
+ * (for the whole batch: ms_iterate = device time of all rounds, ms_sketch =
+ * wall time of all level changes).  Returns IHS_OK when
  * the batch ran; per-problem outcomes (IHS_OK, IHS_EMAXITER, IHS_ENONFINITE)
  * are in reps_h[i].status.  Synchronous.  Device memory: the problems'
  * factors and sketches live at the same time. */
 int ihs_solve_batched(ihs_ctx* ctx, const ihs_problem* probs_h, int32_t count, double tol,
                       ihs_report* reps_h);
+
+/* m0_h[i] (and pred_h[i], may be NULL) as ihs_warm_start for every problem of
+ * a batch (the x, b and m_init fields are not read): the features of all
+ * problems, one forward pass of the network over them, one copy back.
+ * Synchronous.  The result can be passed as the problems' m_init. */
+int ihs_warm_start_batched(ihs_ctx* ctx, const float* params, const ihs_problem* probs_h, int32_t count,
+                           uint64_t seed, int64_t* m0_h, float* pred_h);
 
 /* ---- comparators (Sec. 5) ------------------------------------------------ */
 /* Conjugate gradient on the normal equations (A^T A + nu^2 I) x = A^T b, or,

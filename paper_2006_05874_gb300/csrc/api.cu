@@ -101,6 +101,7 @@ extern "C" int ihs_ctx_create(ihs_ctx** out, void* stream, const ihs_params* p) 
 extern "C" int ihs_ctx_destroy(ihs_ctx* c) {
     if (!c) return IHS_OK;
     cudaStreamSynchronize(c->stream);
+    if (c->lanes) ihs_lanes_destroy(c->lanes);
     for (int i = 0; i < SLOT_COUNT; ++i)
         if (c->buf[i]) cudaFree(c->buf[i]);
     if (c->pinned) cudaFreeHost(c->pinned);

@@ -27,14 +27,18 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <new>
 #include <map>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
 
 namespace {
 
-constexpr int kLanes = 8;
+constexpr int kLanes = 32;
 
 // ---------------------------------------------------------------------------
 // Per-problem descriptors (device)
@@ -579,7 +583,8 @@ struct Prob {
     int t;
     double r, r1, ax2, xx;
     float* SA;             // own sketch (independent problems)
-    ihs_factor_t* F;
+    ihs_factor_t Fs;       // factor of the current level (storage from the batch's pool)
+    ihs_factor_t* F;       // &Fs once built
     ihs_report rep;
     int lane;
     int group;             // shared-A group or -1
@@ -600,16 +605,28 @@ struct Group {             // problems sharing one A
     int64_t rows_per_split = 0;
 };
 
+// Sub-contexts (each with its own scratch arena), their streams and events,
+// and the memory pool of level changes: created on the first batched solve of
+// a context and kept until the context is destroyed, so that later batches
+// find grown arenas and a warm pool.
+struct Lanes {
+    ihs_ctx* lane[kLanes] = {};
+    cudaStream_t lstream[kLanes] = {};
+    cudaEvent_t lev[kLanes] = {};
+    cudaMemPool_t pool = nullptr;
+};
+
 struct Batch {
     ihs_ctx* ctx = nullptr;
     int P = 0;
     std::vector<Prob> pr;
     std::vector<Group> gr;
-    ihs_ctx* lane[kLanes] = {};
-    cudaStream_t lstream[kLanes] = {};
-    cudaEvent_t lev[kLanes] = {};
+    ihs_ctx** lane = nullptr;       // the context's lanes
+    cudaStream_t* lstream = nullptr;
+    cudaEvent_t* lev = nullptr;
     cudaEvent_t mev = nullptr;
     cudaStream_t sm = nullptr;  // the batch's own stream (capturable; ordered after the context's stream)
+    cudaMemPool_t pool = nullptr;   // stream-ordered pool for sketches and factors of level changes (the lanes')
     // device tables
     BVec* dV = nullptr;
     std::vector<BVec> hV;
@@ -635,6 +652,7 @@ struct Batch {
     bool have_graph = false;
     int64_t graph_kernels = 0;
     float ms_rounds = 0.f;
+    double ms_levels = 0.0;     // wall time of level changes (sketches, factors, re-applies)
 };
 
 // b of the group's members as the n x K right-hand-side matrix.
@@ -647,12 +665,14 @@ __global__ void kb_gather_b(const BVec* __restrict__ V, const int* __restrict__ 
 
 void free_batch(Batch& B) {
     if (B.sm) cudaStreamSynchronize(B.sm);
+    cudaStream_t fs = B.lstream ? B.lstream[0] : B.sm;
     for (auto& p : B.pr) {
-        if (p.F) ihs_factor_destroy(p.F);
-        if (p.SA) cudaFree(p.SA);
+        if (p.F) ihs_factor_release_pool(&p.Fs, fs);
+        p.F = nullptr;
+        if (p.SA) cudaFreeAsync(p.SA, fs);
     }
     for (auto& g : B.gr) {
-        for (auto& kv : g.sa) cudaFree(kv.second);
+        for (auto& kv : g.sa) cudaFreeAsync(kv.second, fs);
         cudaFree(g.X);
         cudaFree(g.B);
         cudaFree(g.R);
@@ -660,14 +680,8 @@ void free_batch(Batch& B) {
         cudaFree(g.pax2);
         cudaFree(g.dmembers);
     }
-    for (int l = 0; l < kLanes; ++l) {
-        if (B.lane[l]) {
-            cudaStreamSynchronize(B.lstream[l]);
-            ihs_ctx_destroy(B.lane[l]);
-        }
-        if (B.lstream[l]) cudaStreamDestroy(B.lstream[l]);
-        if (B.lev[l]) cudaEventDestroy(B.lev[l]);
-    }
+    if (B.lstream)
+        for (int l = 0; l < kLanes; ++l) cudaStreamSynchronize(B.lstream[l]);
     if (B.mev) cudaEventDestroy(B.mev);
     if (B.sm) cudaStreamDestroy(B.sm);
     cudaFree(B.dV);
@@ -897,7 +911,18 @@ int autotune_tiles(Batch& B) {
 // Sketch and factor the problems in NEED_LEVEL state at their (new) m, on the
 // lanes; shared-A groups sketch each level once.  Then re-apply the new
 // factors to the current gradients (gt_t and r_t).
+int level_change_impl(Batch& B, bool first);
+
 int level_change(Batch& B, bool first) {
+    IHS_CUDA_TRY(cudaStreamSynchronize(B.sm));
+    const auto t0 = std::chrono::steady_clock::now();
+    const int st = level_change_impl(B, first);
+    cudaStreamSynchronize(B.sm);
+    B.ms_levels += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+int level_change_impl(Batch& B, bool first) {
     ihs_ctx* ctx = B.ctx;
     const ihs_params& prm = ctx->p;
     std::vector<int> todo;
@@ -913,40 +938,44 @@ int level_change(Batch& B, bool first) {
         if (q.group < 0) continue;
         Group& g = B.gr[q.group];
         if (g.sa.count(q.level)) continue;
-        float* SA = nullptr;
-        if (cudaMalloc(&SA, (size_t)q.m * g.d * sizeof(float)) != cudaSuccess) {
+        void* SA0 = nullptr;
+        if (cudaMallocFromPoolAsync(&SA0, (size_t)q.m * g.d * sizeof(float), B.pool, B.lstream[0]) != cudaSuccess) {
             cudaGetLastError();
             return IHS_ENOMEM;
         }
+        float* SA = static_cast<float*>(SA0);
         IHS_TRY(ihs_sketch_enqueue(B.lane[0], g.A, g.n, g.d, q.m, prm.kind, prm.seed, q.level, SA));
         g.sa[q.level] = SA;
     }
     IHS_CUDA_TRY(cudaEventRecord(B.lev[0], B.lstream[0]));
-    int next = 0;
-    for (int p : todo) {
+    // one host thread per lane enqueues the sketches and factorisations of its
+    // problems (each factorisation is dozens of small launches)
+    auto work = [&](int p, int l) -> int {
         Prob& q = B.pr[p];
-        const int l = next;
-        next = (next + 1) % kLanes;
         ihs_ctx* lc = B.lane[l];
         if (q.group >= 0) IHS_CUDA_TRY(cudaStreamWaitEvent(B.lstream[l], B.lev[0], 0));
         if (q.F) {
-            ihs_factor_destroy(q.F);
+            ihs_factor_release_pool(&q.Fs, B.lstream[l]);
             q.F = nullptr;
         }
         const float* SA;
         if (q.group >= 0) {
-            SA = B.gr[q.group].sa[q.level];
+            SA = B.gr[q.group].sa.find(q.level)->second;
         } else {
-            if (q.SA) cudaFree(q.SA);
+            if (q.SA) cudaFreeAsync(q.SA, B.lstream[l]);
             q.SA = nullptr;
-            if (cudaMalloc(&q.SA, (size_t)q.m * q.in.d * sizeof(float)) != cudaSuccess) {
+            void* sa = nullptr;
+            if (cudaMallocFromPoolAsync(&sa, (size_t)q.m * q.in.d * sizeof(float), B.pool, B.lstream[l]) !=
+                cudaSuccess) {
                 cudaGetLastError();
                 return IHS_ENOMEM;
             }
+            q.SA = static_cast<float*>(sa);
             IHS_TRY(ihs_sketch_enqueue(lc, q.in.A, q.in.n, q.in.d, q.m, prm.kind, prm.seed, q.level, q.SA));
             SA = q.SA;
         }
-        IHS_TRY(ihs_factor_alloc(lc, SA, q.m, q.in.d, q.in.nu, &q.F));
+        IHS_TRY(ihs_factor_alloc_pool(lc, B.pool, SA, q.m, q.in.d, q.in.nu, &q.Fs));
+        q.F = &q.Fs;
         IHS_TRY(ihs_factor_enqueue(lc, q.F));
         q.lane = l;
         if (!first) {
@@ -958,6 +987,38 @@ int level_change(Batch& B, bool first) {
         }
         B.hD[p] = make_apply(q, B.hV[p].gc, B.hV[p].gtc, B.hV[p].sc + 0);
         B.hR[p] = make_apply(q, B.hV[p].g, B.hV[p].gt, B.hV[p].sc + 0);
+        return IHS_OK;
+    };
+    std::vector<int> lane_st(kLanes, IHS_OK);
+    std::vector<std::string> lane_msg(kLanes);
+    {
+        std::vector<std::thread> th;
+        const int nl = (int)std::min<size_t>(kLanes, todo.size());
+        for (int l = 0; l < nl; ++l) {
+            th.emplace_back([&, l]() {
+                const cudaError_t e = cudaSetDevice(ctx->device);
+                if (e != cudaSuccess) {
+                    ihs_set_last_cuda_error(e, "lane thread device", __FILE__, __LINE__);
+                    lane_st[l] = IHS_ECUDA;
+                    return;
+                }
+                for (size_t i = l; i < todo.size(); i += nl) {
+                    const int st = work(todo[i], l);
+                    if (st != IHS_OK) {
+                        lane_st[l] = st;
+                        lane_msg[l] = ihs_last_error();   // thread-local: carried to the caller below
+                        return;
+                    }
+                }
+            });
+        }
+        for (auto& t : th) t.join();
+    }
+    for (int l = 0; l < kLanes; ++l) {
+        if (lane_st[l] != IHS_OK) {
+            ihs_set_error(lane_msg[l].c_str());
+            return lane_st[l];
+        }
     }
     for (int l = 0; l < kLanes; ++l) {
         IHS_CUDA_TRY(cudaEventRecord(B.lev[l], B.lstream[l]));
@@ -970,7 +1031,7 @@ int level_change(Batch& B, bool first) {
             bool used = false;
             for (int p : g.members) used |= B.pr[p].level == it->first && B.pr[p].state != DONE;
             if (!used) {
-                cudaFree(it->second);
+                cudaFreeAsync(it->second, B.lstream[0]);
                 it = g.sa.erase(it);
             } else {
                 ++it;
@@ -1041,7 +1102,7 @@ int solve_batched(Batch& B, double tol) {
     const Params pp = make_params(prm.kind, prm.rho, prm.eta);
     // level of every problem at m_init
     for (auto& q : B.pr) {
-        q.m = std::min<int64_t>(prm.m_init, q.m_cap);
+        q.m = std::min<int64_t>(q.in.m_init > 0 ? q.in.m_init : prm.m_init, q.m_cap);
         q.level = 0;
         while (((int64_t)1 << q.level) < q.m) ++q.level;
         q.state = NEED_LEVEL;
@@ -1161,11 +1222,27 @@ int solve_batched(Batch& B, double tol) {
         q.rep.r_final = q.r;
         q.rep.axnorm_final = sqrt(q.ax2 + q.in.nu * q.in.nu * q.xx);
         q.rep.ms_iterate = B.ms_rounds;
+        q.rep.ms_sketch = B.ms_levels;
     }
     return IHS_OK;
 }
 
 }  // namespace
+
+void ihs_lanes_destroy(void* lanes) {
+    Lanes* L = static_cast<Lanes*>(lanes);
+    if (!L) return;
+    for (int l = 0; l < kLanes; ++l) {
+        if (L->lane[l]) {
+            cudaStreamSynchronize(L->lstream[l]);
+            ihs_ctx_destroy(L->lane[l]);
+        }
+        if (L->lstream[l]) cudaStreamDestroy(L->lstream[l]);
+        if (L->lev[l]) cudaEventDestroy(L->lev[l]);
+    }
+    if (L->pool) cudaMemPoolDestroy(L->pool);
+    delete L;
+}
 
 extern "C" int ihs_solve_batched(ihs_ctx* ctx, const ihs_problem* probs_h, int32_t count, double tol,
                                  ihs_report* reps_h) {
@@ -1178,6 +1255,7 @@ extern "C" int ihs_solve_batched(ihs_ctx* ctx, const ihs_problem* probs_h, int32
         const ihs_problem& q = probs_h[i];
         if (!q.A || !q.b || !q.x || q.n < 1 || q.d < 1 || q.n < q.d || !(q.nu > 0.0) || !isfinite(q.nu))
             return IHS_EINVAL;
+        if (q.m_init < 0 || (q.m_init > 0 && (q.m_init & (q.m_init - 1)) != 0)) return IHS_EINVAL;
     }
     if (!(tol > 0.0)) tol = ctx->p.tol;
     Batch B;
@@ -1188,11 +1266,18 @@ extern "C" int ihs_solve_batched(ihs_ctx* ctx, const ihs_problem* probs_h, int32
     B.hD.resize(count);
     B.hR.resize(count);
     int st = IHS_OK;
+    // false (and the error recorded for ihs_last_error) when e is not cudaSuccess
+    auto ok = [](cudaError_t e, const char* what) {
+        if (e == cudaSuccess) return true;
+        ihs_set_last_cuda_error(e, what, __FILE__, __LINE__);
+        return false;
+    };
     do {
         // the batch runs on its own stream, after the work queued on the context's
-        if (cudaStreamCreateWithFlags(&B.sm, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&B.mev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventRecord(B.mev, ctx->stream) != cudaSuccess || cudaStreamWaitEvent(B.sm, B.mev, 0) != cudaSuccess) {
+        if (!ok(cudaStreamCreateWithFlags(&B.sm, cudaStreamNonBlocking), "batch stream") ||
+            !ok(cudaEventCreateWithFlags(&B.mev, cudaEventDisableTiming), "batch event") ||
+            !ok(cudaEventRecord(B.mev, ctx->stream), "record on the context stream") ||
+            !ok(cudaStreamWaitEvent(B.sm, B.mev, 0), "batch stream wait")) {
             st = IHS_ECUDA;
             break;
         }
@@ -1269,10 +1354,10 @@ extern "C" int ihs_solve_batched(ihs_ctx* ctx, const ihs_problem* probs_h, int32
             v.path = B.pr[i].group;
             v.col = -1;
         }
-        if (cudaMemsetAsync(B.arena, 0, tot, B.sm) != cudaSuccess ||
-            cudaMemsetAsync(B.sc_all, 0, (size_t)count * 8 * sizeof(double), B.sm) != cudaSuccess ||
-            cudaMemcpyAsync(B.dV, B.hV.data(), count * sizeof(BVec), cudaMemcpyHostToDevice, B.sm) !=
-                cudaSuccess) {
+        if (!ok(cudaMemsetAsync(B.arena, 0, tot, B.sm), "arena clear") ||
+            !ok(cudaMemsetAsync(B.sc_all, 0, (size_t)count * 8 * sizeof(double), B.sm), "scalars clear") ||
+            !ok(cudaMemcpyAsync(B.dV, B.hV.data(), count * sizeof(BVec), cudaMemcpyHostToDevice, B.sm),
+                "descriptor upload")) {
             st = IHS_ECUDA;
             break;
         }
@@ -1297,27 +1382,61 @@ extern "C" int ihs_solve_batched(ihs_ctx* ctx, const ihs_problem* probs_h, int32
                 st = IHS_ENOMEM;
                 break;
             }
-            if (cudaMemcpy(g.dmembers, g.members.data(), K * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+            if (!ok(cudaMemcpy(g.dmembers, g.members.data(), K * sizeof(int), cudaMemcpyHostToDevice), "members")) {
                 st = IHS_ECUDA;
                 break;
             }
             kb_gather_b<<<(unsigned)ceil_div64(g.n * K, 256), 256, 0, B.sm>>>(B.dV, g.dmembers, K, g.n, g.B);
-            if (cudaGetLastError() != cudaSuccess) {
+            if (!ok(cudaGetLastError(), "gather of right-hand sides")) {
                 st = IHS_ECUDA;
                 break;
             }
         }
         if (st != IHS_OK) break;
-        // lanes
-        for (int l = 0; l < kLanes && st == IHS_OK; ++l) {
-            if (cudaStreamCreateWithFlags(&B.lstream[l], cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&B.lev[l], cudaEventDisableTiming) != cudaSuccess) {
-                st = IHS_ECUDA;
+        // lanes (created once per context)
+        if (!ctx->lanes) {
+            Lanes* L = new (std::nothrow) Lanes;
+            if (!L) {
+                st = IHS_ENOMEM;
                 break;
             }
-            st = ihs_ctx_create(&B.lane[l], B.lstream[l], &ctx->p);
+            ctx->lanes = L;
+            for (int l = 0; l < kLanes && st == IHS_OK; ++l) {
+                if (!ok(cudaStreamCreateWithFlags(&L->lstream[l], cudaStreamNonBlocking), "lane stream") ||
+                    !ok(cudaEventCreateWithFlags(&L->lev[l], cudaEventDisableTiming), "lane event")) {
+                    st = IHS_ECUDA;
+                    break;
+                }
+                st = ihs_ctx_create(&L->lane[l], L->lstream[l], &ctx->p);
+            }
+            if (st == IHS_OK) {
+                cudaMemPoolProps pp;
+                memset(&pp, 0, sizeof(pp));
+                pp.allocType = cudaMemAllocationTypePinned;
+                pp.handleTypes = cudaMemHandleTypeNone;
+                pp.location.type = cudaMemLocationTypeDevice;
+                pp.location.id = ctx->device;
+                if (!ok(cudaMemPoolCreate(&L->pool, &pp), "memory pool")) {
+                    st = IHS_ECUDA;
+                } else {
+                    uint64_t keep = ~0ull;   // keep freed blocks for reuse
+                    cudaMemPoolSetAttribute(L->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+                }
+            }
+            if (st != IHS_OK) {
+                ihs_lanes_destroy(L);
+                ctx->lanes = nullptr;
+                break;
+            }
         }
-        if (st != IHS_OK) break;
+        {
+            Lanes* L = static_cast<Lanes*>(ctx->lanes);
+            B.lane = L->lane;
+            B.lstream = L->lstream;
+            B.lev = L->lev;
+            B.pool = L->pool;
+            for (int l = 0; l < kLanes; ++l) L->lane[l]->p = ctx->p;   // the batch's parameters
+        }
         st = solve_batched(B, tol);
     } while (0);
     if (reps_h)

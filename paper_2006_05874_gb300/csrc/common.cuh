@@ -66,7 +66,10 @@ struct ihs_ctx {
     cudaEvent_t ev[4];
     cudaStream_t aux;        // private stream for the look-ahead Cholesky (joined back before return)
     cudaEvent_t fev[8];      // fork/join events of the look-ahead Cholesky
+    void* lanes;             // batched solves: sub-contexts, streams and memory pool kept across calls
 };
+
+void ihs_lanes_destroy(void* lanes);   // batch.cu
 
 struct ihs_factor {
     ihs_ctx* ctx;
@@ -83,6 +86,20 @@ struct ihs_factor {
 };
 
 int ihs_scratch(ihs_ctx* ctx, int slot, size_t bytes, void** out);
+
+// Let `kern` use up to the device's opt-in maximum of dynamic shared memory
+// (`need` must fit).  The attribute is per function: setting it to one fixed
+// value keeps launches from several host threads with different sizes from
+// racing on it.
+template <typename K>
+inline cudaError_t ihs_allow_smem(K kern, size_t need) {
+    int dev = 0, mx = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (need > (size_t)mx) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
 int ihs_check_status(ihs_ctx* ctx);   // reads and clears the device status word
 
 // Internal launch helpers (enqueue only, no synchronisation).
@@ -99,6 +116,9 @@ int ihs_rows_enqueue(ihs_ctx* ctx, int64_t n_pad, int64_t m, uint64_t seed, int3
 int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F);       // enqueue + check pivots (syncs)
 int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F);     // enqueue only (pivot failures in d_status)
 int ihs_factor_alloc(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** out);
+int ihs_factor_alloc_pool(ihs_ctx* ctx, cudaMemPool_t pool, const float* SA, int64_t m, int64_t d, double nu,
+                          ihs_factor_t* F);
+void ihs_factor_release_pool(ihs_factor_t* F, cudaStream_t s);
 // Factor into the context's scratch (no allocation once the slot is large
 // enough); F is caller storage, valid until the next call with the same ctx.
 int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t* F);

@@ -780,6 +780,44 @@ int ihs_factor_alloc(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double
     return IHS_OK;
 }
 
+// Factor storage in one block from a stream-ordered memory pool, allocated
+// on ctx's stream (owned = 2; release with ihs_factor_release_pool).
+int ihs_factor_alloc_pool(ihs_ctx* ctx, cudaMemPool_t pool, const float* SA, int64_t m, int64_t d, double nu,
+                          ihs_factor_t* F) {
+    if (!ctx || !SA || !F || m < 1 || d < 1 || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
+    memset(F, 0, sizeof(*F));
+    F->ctx = ctx;
+    F->SA = SA;
+    F->m = m;
+    F->d = d;
+    F->nu = nu;
+    F->woodbury = m < d ? 1 : 0;
+    F->k = F->woodbury ? m : d;
+    F->owned = 2;
+    const int64_t k = F->k;
+    const int64_t T = ceil_div64(k, FB);
+    const size_t kk = (size_t)k * k;
+    const size_t bL = align256(kk * sizeof(double)), bW = align256((size_t)T * FB * FB * sizeof(double));
+    const size_t bX = align256(kk * sizeof(float)), bwork = align256(factor_work_doubles(k, m, d) * sizeof(double));
+    void* base = nullptr;
+    if (cudaMallocFromPoolAsync(&base, bL + bW + 2 * bX + bwork, pool, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return IHS_ENOMEM;
+    }
+    char* b = static_cast<char*>(base);
+    F->L = reinterpret_cast<double*>(b);
+    F->W = reinterpret_cast<double*>(b + bL);
+    F->X = reinterpret_cast<float*>(b + bL + bW);
+    F->XT = reinterpret_cast<float*>(b + bL + bW + bX);
+    F->work = reinterpret_cast<double*>(b + bL + bW + 2 * bX);
+    return IHS_OK;
+}
+
+void ihs_factor_release_pool(ihs_factor_t* F, cudaStream_t s) {
+    if (F && F->owned == 2 && F->L) cudaFreeAsync(F->L, s);
+    if (F) memset(F, 0, sizeof(*F));
+}
+
 extern "C" int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** out) {
     if (!out) return IHS_EINVAL;
     *out = nullptr;
@@ -796,7 +834,7 @@ extern "C" int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, d
 
 extern "C" int ihs_factor_destroy(ihs_factor_t* F) {
     if (!F) return IHS_OK;
-    if (!F->owned) return IHS_EINVAL;   // scratch-backed factors belong to their context
+    if (F->owned != 1) return IHS_EINVAL;   // scratch- or pool-backed factors are released by their owner
     if (F->ctx) cudaStreamSynchronize(F->ctx->stream);
     if (F->L) cudaFree(F->L);
     if (F->W) cudaFree(F->W);

@@ -385,7 +385,7 @@ int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int
     dim3 grid((unsigned)MT, (unsigned)NT, (unsigned)KS);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     auto launch = [&](auto kern, int fmt, const float* crec) -> int {
-        IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(fmt)));
+        IHS_CUDA_TRY(ihs_allow_smem(kern, tc_smem(fmt)));
         kern<<<grid, TC_THREADS, tc_smem(fmt), ctx->stream>>>(amap, A, n, (int)d, m, rows_per_split, (uint32_t)level,
                                                               k0, k1, crec, ctx->d_status, part);
         return IHS_OK;

@@ -753,7 +753,7 @@ int launch_fast(ihs_ctx* ctx, const float* A, const float* b, const float* x, in
     int64_t G = (int64_t)MINB * ctx->sm_count;
     if (G > ntiles) G = ntiles;
     auto kern = k_grad_fast<TPR, CPT, RT, MINB>;
-    IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
     kern<<<(unsigned)G, kThreads, smem, ctx->stream>>>(A, b, x, n, d, ntiles, stages, part, part_ax2,
                                                       ctx->d_status);
     IHS_LAUNCH_CHECK();
@@ -773,7 +773,7 @@ int launch_v3(ihs_ctx* ctx, const float* A, const float* b, const float* x, int6
     int64_t G = ctx->sm_count;
     if (G > ntiles) G = ntiles;
     auto kern = k_grad_v3<NSEG, CPT, FULL>;
-    IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
     kern<<<(unsigned)G, kV3Threads, smem, ctx->stream>>>(A, b, x, n, d, ntiles, S, part, part_ax2, ctx->d_status);
     IHS_LAUNCH_CHECK();
     *G_out = (int)G;
@@ -974,7 +974,7 @@ int launch_fast_noalloc(cudaStream_t stream, int sm_count, const float* A, const
     const int64_t ntiles = ceil_div64(n, R);
     int64_t G = std::min<int64_t>(std::min<int64_t>(sm_count, IHS_NOALLOC_MAX_CTAS), ntiles);
     auto kern = k_grad_fast<TPR, CPT, RT, 1>;
-    IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
     kern<<<(unsigned)G, kThreads, smem, stream>>>(A, b, x, n, d, ntiles, stages, part, part_ax2, status);
     IHS_LAUNCH_CHECK();
     *G_out = (int)G;

@@ -18,6 +18,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
@@ -44,8 +46,13 @@ __global__ void k_probe_gram(const float* __restrict__ P, int d, double* __restr
 // Eigenvalues of the symmetric 32 x 32 Q by cyclic Jacobi (round-robin pairs,
 // 16 disjoint rotations per round, 31 rounds per sweep, at most 16 sweeps,
 // stopping when the off-diagonal part is negligible), then the 11 features.
-__global__ void __launch_bounds__(256) k_probe_features(const double* __restrict__ Q, double logn, double logd,
-                                                        double lognu, float* __restrict__ feat) {
+// One CTA per problem (blockIdx.x): Q of problem i at Q + 1024 i, its three
+// size features at logs + 3 i, its features to feat + 11 i.
+__global__ void __launch_bounds__(256) k_probe_features(const double* __restrict__ Qall,
+                                                        const double* __restrict__ logs, float* __restrict__ featall) {
+    const double* Q = Qall + (size_t)blockIdx.x * 1024;
+    float* feat = featall + (size_t)blockIdx.x * NF;
+    const double logn = logs[3 * blockIdx.x], logd = logs[3 * blockIdx.x + 1], lognu = logs[3 * blockIdx.x + 2];
     __shared__ double a[32][33];
     __shared__ double cs[16], sn[16];
     __shared__ int pp[16], qq[16];
@@ -290,6 +297,14 @@ __global__ void __launch_bounds__(256) k_mlp(float* __restrict__ params, const f
 
 extern "C" int ihs_mlp_num_params(void) { return NPARAM; }
 
+// The probe Gram of (A, d) into Q (32 x 32 FP64), using P (32 x d FP32).
+static int probe_gram(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, uint64_t seed, float* P, double* Q) {
+    IHS_TRY(ihs_gauss_fp32_enqueue(ctx, A, n, d, 32, seed, 200, P));
+    k_probe_gram<<<(32 * 32 * 32 + 255) / 256, 256, 0, ctx->stream>>>(P, (int)d, Q);
+    IHS_LAUNCH_CHECK();
+    return IHS_OK;
+}
+
 extern "C" int ihs_probe_features(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, double nu, uint64_t seed,
                                   float* feat) {
     if (!ctx || !A || !feat || n < 1 || d < 1 || !(nu > 0.0)) return IHS_EINVAL;
@@ -298,11 +313,13 @@ extern "C" int ihs_probe_features(ihs_ctx* ctx, const float* A, int64_t n, int64
     IHS_TRY(ihs_scratch(ctx, SLOT_MISC, pbytes + 32 * 32 * sizeof(double) + 256, &ws));
     float* P = static_cast<float*>(ws);
     double* Q = reinterpret_cast<double*>(static_cast<char*>(ws) + pbytes);
-    IHS_TRY(ihs_gauss_fp32_enqueue(ctx, A, n, d, 32, seed, 200, P));
-    k_probe_gram<<<(32 * 32 * 32 + 255) / 256, 256, 0, ctx->stream>>>(P, (int)d, Q);
+    double* logs = Q + 32 * 32;
+    IHS_TRY(probe_gram(ctx, A, n, d, seed, P, Q));
+    const double hl[3] = {log((double)n), log((double)d), log(nu)};
+    IHS_CUDA_TRY(cudaMemcpyAsync(logs, hl, sizeof(hl), cudaMemcpyHostToDevice, ctx->stream));
+    k_probe_features<<<1, 256, 0, ctx->stream>>>(Q, logs, feat);
     IHS_LAUNCH_CHECK();
-    k_probe_features<<<1, 256, 0, ctx->stream>>>(Q, log((double)n), log((double)d), log(nu), feat);
-    IHS_LAUNCH_CHECK();
+    IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));   // hl lives on this stack frame
     return IHS_OK;
 }
 
@@ -377,4 +394,95 @@ extern "C" int ihs_warm_start(ihs_ctx* ctx, const float* params, const float* A,
     *m0 = (int64_t)1 << lvl;
     if (pred_h) *pred_h = pred;
     return IHS_OK;
+}
+
+extern "C" int ihs_warm_start_batched(ihs_ctx* ctx, const float* params, const ihs_problem* probs_h, int32_t count,
+                                      uint64_t seed, int64_t* m0_h, float* pred_h) {
+    if (!ctx || !params || !probs_h || !m0_h || count < 1) return IHS_EINVAL;
+    for (int i = 0; i < count; ++i)
+        if (!probs_h[i].A || probs_h[i].n < 1 || probs_h[i].d < 1 || !(probs_h[i].nu > 0.0)) return IHS_EINVAL;
+    // features of all problems (one row each), then one forward pass and one copy
+    float* feat = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&feat), (size_t)count * 16 * sizeof(float), ctx->stream) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return IHS_ENOMEM;
+    }
+    float* y = feat + (size_t)count * NF;
+    int st = IHS_OK;
+    // probe Grams one by one (P reused in stream order), then the eigenvalues of
+    // all problems in one launch (one CTA each)
+    int64_t dmax = 1;
+    for (int i = 0; i < count; ++i) dmax = probs_h[i].d > dmax ? probs_h[i].d : dmax;
+    double* Qall = nullptr;
+    float* P = nullptr;
+    std::vector<double> hl(3 * (size_t)count);
+    for (int i = 0; i < count; ++i) {
+        hl[3 * i] = log((double)probs_h[i].n);
+        hl[3 * i + 1] = log((double)probs_h[i].d);
+        hl[3 * i + 2] = log(probs_h[i].nu);
+    }
+    if (cudaMallocAsync(reinterpret_cast<void**>(&Qall), (size_t)count * (1024 + 3) * sizeof(double), ctx->stream) !=
+            cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&P), (size_t)32 * dmax * sizeof(float), ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        st = IHS_ENOMEM;
+    }
+    double* logs = Qall + (size_t)count * 1024;
+    // the probe depends on (A, seed) only: problems sharing A share its Gram
+    std::vector<int> first(count, -1);
+    for (int i = 0; i < count; ++i)
+        for (int j = 0; j < i && first[i] < 0; ++j)
+            if (first[j] < 0 && probs_h[j].A == probs_h[i].A && probs_h[j].n == probs_h[i].n &&
+                probs_h[j].d == probs_h[i].d)
+                first[i] = j;
+    for (int i = 0; i < count && st == IHS_OK; ++i) {
+        if (first[i] < 0) {
+            st = probe_gram(ctx, probs_h[i].A, probs_h[i].n, probs_h[i].d, seed, P, Qall + (size_t)i * 1024);
+        } else if (cudaMemcpyAsync(Qall + (size_t)i * 1024, Qall + (size_t)first[i] * 1024, 1024 * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+            st = IHS_ECUDA;
+        }
+    }
+    if (st == IHS_OK &&
+        cudaMemcpyAsync(logs, hl.data(), hl.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        st = IHS_ECUDA;
+    if (st == IHS_OK) {
+        k_probe_features<<<(unsigned)count, 256, 0, ctx->stream>>>(Qall, logs, feat);
+        if (cudaGetLastError() != cudaSuccess) st = IHS_ECUDA;
+        ihs_count_launch();
+    }
+    if (st == IHS_OK) {
+        k_mlp<<<1, 256, 0, ctx->stream>>>(const_cast<float*>(params), feat, nullptr, count, 0, y, nullptr, nullptr,
+                                          nullptr, 0, 0.f, nullptr);
+        if (cudaGetLastError() != cudaSuccess) st = IHS_ECUDA;
+        ihs_count_launch();
+    }
+    float* hy = nullptr;
+    if (st == IHS_OK && cudaMallocHost(reinterpret_cast<void**>(&hy), (size_t)count * sizeof(float)) != cudaSuccess)
+        st = IHS_ENOMEM;
+    if (st == IHS_OK && (cudaMemcpyAsync(hy, y, (size_t)count * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream) !=
+                             cudaSuccess ||
+                         cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+        st = IHS_ECUDA;
+    cudaFreeAsync(feat, ctx->stream);
+    if (Qall) cudaFreeAsync(Qall, ctx->stream);
+    if (P) cudaFreeAsync(P, ctx->stream);
+    if (st == IHS_OK) {
+        for (int i = 0; i < count; ++i) {
+            const float pred = hy[i];
+            if (!isfinite(pred)) {
+                st = IHS_ENONFINITE;
+                break;
+            }
+            int lvl = (int)floorf(pred) - 1;
+            int cap = 0;
+            while (cap < 62 && ((int64_t)1 << (cap + 1)) <= probs_h[i].n) ++cap;
+            lvl = lvl < 0 ? 0 : (lvl > cap ? cap : lvl);
+            m0_h[i] = (int64_t)1 << lvl;
+            if (pred_h) pred_h[i] = pred;
+        }
+    }
+    if (hy) cudaFreeHost(hy);
+    return st;
 }

@@ -246,7 +246,7 @@ int launch_r32(ihs_ctx* ctx, const CUtensorMap& amap, int d, int64_t mc, int64_t
                const int32_t* rows, int32_t level, uint64_t seed, float* part) {
     const size_t smem = r32_smem_bytes(mc);
     auto kern = k_srht_r32<MA>;
-    IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
     dim3 grid((unsigned)ceil_div64(d, kR32C), (unsigned)PG);
     kern<<<grid, kR32T, smem, ctx->stream>>>(amap, d, mc, m, c0, P, PG, rows, (uint32_t)level, (uint32_t)seed,
                                             (uint32_t)(seed >> 32), ctx->d_status, part);
@@ -403,7 +403,7 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
         const size_t acc_bytes = (size_t)m * kSrhtC * sizeof(float);
         const int acc_in_smem = (base + acc_bytes <= 200 * 1024) ? 1 : 0;
         const size_t smem = base + (acc_in_smem ? acc_bytes : 0);
-        IHS_CUDA_TRY(cudaFuncSetAttribute(k_srht_fwht, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        IHS_CUDA_TRY(ihs_allow_smem(k_srht_fwht, smem));
         dim3 grid((unsigned)CT, (unsigned)PG);
         k_srht_fwht<<<grid, kSrhtThreads, smem, ctx->stream>>>(A, n, (int)d, m, Q, logQ, P, (int)PG, rows,
                                                               (uint32_t)level, (uint32_t)seed,

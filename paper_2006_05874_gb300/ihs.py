@@ -70,6 +70,7 @@ _SIGNATURES = {
     "ihs_cg": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i32, _i32, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_grad_noalloc": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, _vp], ctypes.c_int),
     "ihs_solve_batched": ([_vp, _vp, _i32, _dbl, _vp], ctypes.c_int),
+    "ihs_warm_start_batched": ([_vp, _vp, _vp, _i32, _u64, _vp, _vp], ctypes.c_int),
     "ihs_mlp_num_params": ([], ctypes.c_int),
     "ihs_probe_features": ([_vp, _vp, _i64, _i64, _dbl, _u64, _vp], ctypes.c_int),
     "ihs_mlp_forward": ([_vp, _vp, _vp, _i32, _vp], ctypes.c_int),
@@ -176,7 +177,7 @@ class Factor:
 class Problem(ctypes.Structure):
     """One problem of ihs_solve_batched (device pointers)."""
     _fields_ = [("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int64),
-                ("nu", ctypes.c_double), ("x", ctypes.c_void_p)]
+                ("nu", ctypes.c_double), ("x", ctypes.c_void_p), ("m_init", ctypes.c_int64)]
 
 
 class Context:
@@ -238,17 +239,34 @@ class Context:
             _check("ihs_solve", st)
         return rep
 
-    def solve_batched(self, problems, tol=0.0):
-        """problems: sequence of (A, b, nu, x) device tensors (A may be shared).
+    def solve_batched(self, problems, tol=0.0, m_init=None):
+        """problems: sequence of (A, b, nu, x) device tensors (A may be shared);
+        m_init: optional per-problem initial sketch sizes (powers of two).
         Returns one Report per problem (each with its own status)."""
         arr = (Problem * len(problems))()
         for i, (A, b, nu, x) in enumerate(problems):
             n, d = A.shape
-            arr[i] = Problem(_ptr(A).value, _ptr(b).value, n, d, float(nu), _ptr(x).value)
+            m0 = 0 if m_init is None else int(m_init[i])
+            arr[i] = Problem(_ptr(A).value, _ptr(b).value, n, d, float(nu), _ptr(x).value, m0)
         reps = (Report * len(problems))()
         _check("ihs_solve_batched", _lib.ihs_solve_batched(self.handle, ctypes.byref(arr), len(problems),
                                                            float(tol), ctypes.byref(reps)))
         return list(reps)
+
+    def warm_start_batched(self, params, problems, seed=None):
+        """m0 for every (A, nu) (or (A, b, nu, x)) of a batch: one forward pass over all."""
+        arr = (Problem * len(problems))()
+        for i, pr in enumerate(problems):
+            A, nu = pr[0], pr[2] if len(pr) > 2 else pr[1]
+            n, d = A.shape
+            arr[i] = Problem(_ptr(A).value, None, n, d, float(nu), None, 0)
+        m0 = (ctypes.c_int64 * len(problems))()
+        pred = (ctypes.c_float * len(problems))()
+        seed = self.params.seed if seed is None else seed
+        _check("ihs_warm_start_batched", _lib.ihs_warm_start_batched(self.handle, _ptr(params), ctypes.byref(arr),
+                                                                     len(problems), int(seed), ctypes.byref(m0),
+                                                                     ctypes.byref(pred)))
+        return list(m0), list(pred)
 
     def cg(self, A, b, nu, x, tol=1e-6, max_iter=1000, precond=None, raise_on_maxiter=False):
         """CG (precond=None) or sketch-preconditioned CG (precond="srht"/"gauss")."""

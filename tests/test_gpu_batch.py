@@ -128,3 +128,20 @@ def test_batch_rejects_polyak_and_bad_args(ctx, torch_cuda):
     ctx.set_params(variant="gd")
     with pytest.raises(ihs.IHSError):
         ctx.solve_batched([(A, b, -1.0, x)])
+
+
+def test_batch_per_problem_initial_sizes(ctx, torch_cuda):
+    """m_init per problem (as a warm start supplies it): same accuracy, and the
+    schedule starts at the given size."""
+    torch = torch_cuda
+    ctx.set_params(kind="srht", variant="gd")
+    probs = _independent(21, 4, nmax=4096, dmax=128)
+    dev = [(_dev(torch, A), _dev(torch, b), nu, torch.zeros(A.shape[1], device="cuda")) for A, b, nu in probs]
+    m0 = [64, 128, 1, 256]
+    reps = ctx.solve_batched(dev, m_init=m0)
+    for (A, b, nu), (_, _, _, x), rep, m in zip(probs, dev, reps, m0):
+        assert rep.status == 0
+        assert rep.levels()[0] == m
+        assert linalg.relative_error(A, nu, x.cpu().numpy(), linalg.direct_solve(A, b, nu)) <= 1e-5
+    with pytest.raises(Exception):
+        ctx.solve_batched(dev[:1], m_init=[3])

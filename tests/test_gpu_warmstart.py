@@ -192,3 +192,17 @@ def test_warm_start_gain_on_heldout(ctx, torch_cuda, trained):
         warm_p += runs["warm"][1].grad_passes
     assert warm_p < cold_p
     assert warm_t < cold_t, (warm_t, cold_t)
+
+
+def test_warm_start_batched_matches_single(ctx, torch_cuda, trained):
+    torch = torch_cuda
+    params, _ = trained
+    pd = _dev(torch, params)
+    probs = [problems.exp_decay(4096, 256, seed=3), problems.spectral(8192, 128, de_target=20.0, seed=4),
+             problems.exp_decay(2048, 64, decay=0.9, nu=1.0, seed=6)]
+    dev = [(_dev(torch, p.A), p.nu) for p in probs]
+    m0s, preds = ctx.warm_start_batched(pd, dev)
+    for (A, nu), m0b, pb in zip(dev, m0s, preds):
+        m0, pred = ctx.warm_start(pd, A, nu)
+        assert pb == pytest.approx(pred, abs=1e-5)
+        assert m0b == m0
