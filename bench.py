@@ -203,7 +203,7 @@ def run_profile(what, rows=N_ROWS):
     from paper_2006_05874_gb300 import ihs
 
     torch.cuda.set_device(0)
-    ctx = ihs.Context(kind="srht", variant="gd", tol=TOL)
+    ctx = ihs.Context(kind="srht", variant="gd", tol=TOL, precision="bf16" if what == "gauss" else "fp32")
     if what == "solve":
         p = make_problem("cuda")
         A, b = torch.from_numpy(p.A).cuda(), torch.from_numpy(p.b).cuda()
@@ -219,7 +219,7 @@ def run_profile(what, rows=N_ROWS):
             g = torch.empty(D_COLS, device="cuda")
             fn = lambda: ctx.grad(A, b, 0.015, x, g, want_axnorm2=False)
         else:
-            m = 1024 if what == "srht" else 256
+            m = 1024   # the sketch size the solves settle at (SRHT level 10; BF16 Gaussian warm start)
             SA = torch.empty(m, D_COLS, device="cuda")
             fn = lambda: ctx.sketch(A, m, what, 0, 10, SA)
     for _ in range(2):
@@ -375,6 +375,16 @@ def batched_workload(ihs, stream, seed=0):
             "ms_rounds_device": float(reps[0].ms_iterate), "ms_level_changes_wall": float(reps[0].ms_sketch)}
 
 
+def max_over_ranks(value, dist, device):
+    """The slowest rank's value (every rank gets it): the timing rule of
+    replicated runs (each rank solves the same problem on its own GPU)."""
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _has_cuda():
     try:
         import torch
@@ -460,9 +470,7 @@ def main():
     launches = ihs.kernel_launches() - launches0
     ms_total = ev0.elapsed_time(ev1)
     if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = max_over_ranks(ms_total, dist, "cuda")
         dist.barrier()
     ms_per = ms_total / args.steps
 
