@@ -385,6 +385,62 @@ def max_over_ranks(value, dist, device):
     return float(t.item())
 
 
+def precision_workload(ihs, stream):
+    """The precision form at full size: A 1048576 x 4096 FP32 (16 GB, sigma_j =
+    exp(-j/300)), nu for d_e in {50, 200, 1000}; Gaussian sketch in BF16 and in
+    FP8-e4m3 with per-column scales on tensor cores, FP32 compensated gradient,
+    FP64 Cholesky; gradient-IHS from m = 1.  Verification in FP64 on the host:
+    ||Abar (x - x*)|| = ||H^-1/2 grad f(x)|| <= ||grad f(x)|| / nu (H >= nu^2 I),
+    so err <= ||grad f(x)||_FP64 / (nu ||Abar x||) bounds the relative prediction
+    error without a 16 GB direct solve."""
+    import torch
+
+    from paper_2006_05874_gb300 import problems
+
+    A, b, sigma = problems.precision_instance()
+    n, d = A.shape
+    Ah = A.cpu().numpy()
+    bh = b.cpu().numpy().astype(np.float64)
+    out = {}
+    for de in (50, 200, 1000):
+        nu = problems.nu_for_target(sigma, de)
+        for prec in ("bf16", "fp8"):
+            ctx = ihs.Context(kind="gauss", variant="gd", precision=prec, tol=TOL, stream=stream)
+            x = torch.zeros(d, device="cuda")
+            ctx.solve(A, b, nu, x)   # warm-up (scratch)
+            # the solver's stopping rule decides; tol shrinks until the FP64 bound is <= 1e-5
+            tol = TOL
+            for attempt in range(5):
+                ctx.set_params(tol=tol)
+                x.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                rep = ctx.solve(A, b, nu, x)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                xh = x.cpu().numpy().astype(np.float64)
+                # FP64 gradient and ||A x||, streamed over row blocks of the host copy
+                g = nu * nu * xh
+                ax2 = 0.0
+                for r0 in range(0, n, 65536):
+                    Ab = Ah[r0:r0 + 65536].astype(np.float64)
+                    ax = Ab @ xh
+                    ax2 += float(ax @ ax)
+                    g += Ab.T @ (ax - bh[r0:r0 + 65536])
+                bound = float(np.linalg.norm(g)) / (nu * math.sqrt(ax2 + nu * nu * float(xh @ xh)))
+                if bound <= TOL:
+                    break
+                tol *= 0.3
+            out["de%d_%s" % (de, prec)] = {"nu": nu, "ms": ms, "tol": tol, "err_bound": bound,
+                                           "levels": rep.levels(), "iterations": rep.iterations,
+                                           "grad_passes": rep.grad_passes, "status": int(rep.status)}
+            ctx.destroy()
+    del A
+    return {"workload": "precision 1048576x4096 (16 GB), sigma_j=exp(-j/300), gauss gd from m=1", "cases": out}
+
+
 def _has_cuda():
     try:
         import torch
@@ -530,6 +586,7 @@ def main():
 
     forms = solver_forms(ihs, ctx, p, A, b, x_star, stream, args.steps)
     batched = batched_workload(ihs, stream)
+    precision = precision_workload(ihs, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -553,7 +610,7 @@ def main():
                    "rel_error": err, "rel_error_e2e": err_e2e, "levels": r0.levels(), "iterations": r0.iterations,
                    "grad_passes_per_solve": r0.grad_passes, "ms_sketch_factor": r0.ms_sketch,
                    "ms_iterate": r0.ms_iterate, "comparators_same_gpu": comparators, "forms_same_gpu": forms,
-                   "batched_same_gpu": batched},
+                   "batched_same_gpu": batched, "precision_same_gpu": precision},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(), "peak_source": peak_kind,
                      "kernel": "gradient pass (k_grad_v3 + k_grad_reduce)", "ms_per_launch": ms_grad,

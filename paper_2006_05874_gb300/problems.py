@@ -194,3 +194,33 @@ def sampled_ridge(seed, device, sizes=WARM_SIZES):
     x0 = torch.randn(d, generator=gen, device=device, dtype=torch.float32)
     b = A @ x0 + 0.01 * torch.randn(n, generator=gen, device=device, dtype=torch.float32)
     return A.contiguous(), b.contiguous(), float(nu), dict(n=n, d=d, family=fam, de_target=target, seed=seed)
+
+
+def precision_instance(n=1048576, d=4096, scale=300.0, seed=0, device="cuda"):
+    """The precision workload's matrix: A = (G / sqrt(n)) diag(sigma) V^T with
+    sigma_j = exp(-j / scale), G i.i.d. N(0, 1) (n x d, float32 on the device;
+    its columns are orthonormal up to O(sqrt(d / n)), standing in for a Haar U
+    that a QR of a 16 GB matrix would give), V Haar (FP64 QR of a d x d Gaussian);
+    x0 ~ N(0, I), b = A x0 + 0.01 N(0, I).  Returns (A, b, sigma) with A, b
+    float32 torch tensors on the device; nu is chosen by the caller with
+    nu_for_target(sigma, d_e)."""
+    import torch
+
+    sigma = np.exp(-np.arange(1, d + 1, dtype=np.float64) / scale)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    Vg = torch.randn(d, d, generator=gen, device=device, dtype=torch.float64)
+    V, R = torch.linalg.qr(Vg)
+    V = V * torch.sign(torch.diagonal(R))[None, :]
+    M = (torch.as_tensor(sigma, device=device, dtype=torch.float64)[:, None] * V.T).to(torch.float32)
+    del Vg, V, R
+    A = torch.empty(n, d, device=device, dtype=torch.float32)
+    rows = 65536
+    for r0 in range(0, n, rows):
+        r1 = min(n, r0 + rows)
+        G = torch.randn(r1 - r0, d, generator=gen, device=device, dtype=torch.float32)
+        torch.matmul(G, M, out=A[r0:r1])
+    A /= math.sqrt(n)
+    x0 = torch.randn(d, generator=gen, device=device, dtype=torch.float32)
+    b = A @ x0 + 0.01 * torch.randn(n, generator=gen, device=device, dtype=torch.float32)
+    return A, b.contiguous(), sigma
