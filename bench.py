@@ -441,6 +441,43 @@ def precision_workload(ihs, stream):
     return {"workload": "precision 1048576x4096 (16 GB), sigma_j=exp(-j/300), gauss gd from m=1", "cases": out}
 
 
+def minimal_iteration_run(ctx, A, b, p, x_star, stream, t_rule, tol):
+    """The same solve stopped at the smallest iteration count t whose iterate is
+    within 1e-5 of the FP64 direct solution (found by bisection on max_iter,
+    checked against the oracle), and its time."""
+    import torch
+
+    from oracle import linalg
+
+    max_iter0 = int(ctx.params.max_iter)
+
+    def run(t):
+        ctx.set_params(max_iter=int(t), tol=1e-30)
+        x = torch.zeros(p.d, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rep = ctx.solve(A, b, p.nu, x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return linalg.relative_error(p.A, p.nu, x.cpu().numpy(), x_star), e0.elapsed_time(e1), rep
+
+    lo, hi = 1, max(2, t_rule)
+    while run(hi)[0] > TOL and hi < 4 * t_rule + 8:
+        hi *= 2
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if run(mid)[0] <= TOL:
+            hi = mid
+        else:
+            lo = mid + 1
+    run(hi)
+    err, ms, rep = run(hi)
+    ctx.set_params(max_iter=max_iter0, tol=tol)
+    return {"iterations": hi, "ms": ms, "rel_error": err, "iterations_by_stopping_rule": t_rule,
+            "levels": rep.levels()}
+
+
 def _has_cuda():
     try:
         import torch
@@ -531,6 +568,7 @@ def main():
     ms_per = ms_total / args.steps
 
     err = linalg.relative_error(p.A, p.nu, x.cpu().numpy(), x_star)
+    min_iter = minimal_iteration_run(ctx, A, b, p, x_star, stream, reps[-1].iterations, tol)
     grad_passes = sum(r.grad_passes for r in reps)
     ms_grad = sum(r.ms_grad for r in reps) / grad_passes
     bytes_per_pass = 4.0 * p.n * p.d + 4.0 * p.n + 8.0 * p.d
@@ -609,6 +647,7 @@ def main():
                    "variant": "gd", "l2": "inputs larger than L2 (A is 1 GiB)",
                    "rel_error": err, "rel_error_e2e": err_e2e, "levels": r0.levels(), "iterations": r0.iterations,
                    "grad_passes_per_solve": r0.grad_passes, "ms_sketch_factor": r0.ms_sketch,
+                   "oracle_minimal_iterations": min_iter,
                    "ms_iterate": r0.ms_iterate, "comparators_same_gpu": comparators, "forms_same_gpu": forms,
                    "batched_same_gpu": batched, "precision_same_gpu": precision},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
