@@ -421,7 +421,6 @@ k_grad_v3(const float* __restrict__ A, const float* __restrict__ b, const float*
     const int64_t t1 = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
     const int64_t my_tiles = t1 - t0;
     const size_t stage_floats = (size_t)R * d;
-    const uint32_t stage_bytes = (uint32_t)(stage_floats * sizeof(float));
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -530,15 +529,20 @@ k_grad_v3(const float* __restrict__ A, const float* __restrict__ b, const float*
         xan[k] = f2_pack(-v.x, -v.y);
         xbn[k] = f2_pack(-v.z, -v.w);
     }
+    // FULL: d = 512 NSEG is a compile-time constant, and so is every shared-memory
+    // offset below (no per-tile integer arithmetic beyond the stage step)
+    const int dd = FULL ? 512 * NSEG : d;
+    constexpr bool ALLP = FULL && NSEG >= 4;   // every consumer thread owns CPT full chunks
     bool pv[CPT];
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) pv[k] = tid + kV3Consumers * 32 * k < chunks;
+    for (int k = 0; k < CPT; ++k) pv[k] = ALLP || tid + kV3Consumers * 32 * k < chunks;
     // shared-memory byte addresses: stage 0, this lane's phase-1 chunk 0 of its
     // row, this thread's phase-2 chunk 0 of row 0, its pdot slot
     const uint32_t sm0 = smem_u32(smem);
-    const uint32_t p1_off = (uint32_t)(prow * d + (seg * 32 + lane) * 4) * 4u;
+    const uint32_t sbytes = (uint32_t)(R * dd * 4);
+    const uint32_t p1_off = (uint32_t)(prow * dd + (seg * 32 + lane) * 4) * 4u;
     const uint32_t p2_off = (uint32_t)tid * 16u;
-    const uint32_t row_bytes = (uint32_t)d * 4u;
+    const uint32_t row_bytes = (uint32_t)dd * 4u;
     const uint32_t pd0 = smem_u32(pdot) + (uint32_t)((prow * (NP / R) + seg * 32 + lane) * sizeof(Acc2));
     const uint32_t pd_stage = (uint32_t)(R * (NP / R) * sizeof(Acc2));
     const uint32_t rs0 = smem_u32(rsh);
@@ -551,14 +555,15 @@ k_grad_v3(const float* __restrict__ A, const float* __restrict__ b, const float*
     bool ok = true;
     int s1 = 0, s2 = 0;          // stages of phase 1 (tile l) and phase 2 (tile l - 1)
     uint32_t ph1 = 0, ph2 = 0;   // their parities
-    for (int64_t l = 0; l <= my_tiles; ++l) {
+    int64_t row0 = t0 * R;   // first row of tile l
+    for (int64_t l = 0; l <= my_tiles; ++l, row0 += R) {
         if (l < my_tiles) {
-            const int rows = (int)min((int64_t)R, n - (t0 + l) * R);
+            const int rows = (int)min((int64_t)R, n - row0);
             ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s1], ph1, status));
             if (!ok) break;
             Acc2x2 pa{zero2, zero2}, pb{zero2, zero2};
             if (prow < rows) {
-                const uint32_t base = sm0 + (uint32_t)s1 * stage_bytes + p1_off;
+                const uint32_t base = sm0 + (uint32_t)s1 * sbytes + p1_off;
 #pragma unroll
                 for (int k = 0; k < XC; ++k) {
                     if (cv[k]) {
@@ -586,29 +591,49 @@ k_grad_v3(const float* __restrict__ A, const float* __restrict__ b, const float*
             }
         }
         if (l >= 1) {
-            const int rows = (int)min((int64_t)R, n - (t0 + l - 1) * R);
+            const int rows = (int)min((int64_t)R, n - (row0 - R));
             ok = __all_sync(0xffffffffu, mbar_wait_bounded(&rfinal[s2], ph2, status));
             if (!ok) break;
-            const uint32_t base = sm0 + (uint32_t)s2 * stage_bytes + p2_off;
+            const uint32_t base = sm0 + (uint32_t)s2 * sbytes + p2_off;
             f2 rr[R];
 #pragma unroll
             for (int i = 0; i < R; ++i) rr[i] = lds_f2(rs0 + (uint32_t)((s2 * R + i) * 8));
+            if (rows == R) {
+                // full tile: no per-row predicates
 #pragma unroll
-            for (int k = 0; k < CPT; ++k) {
-                if (pv[k]) {
-                    f2 s01 = zero2, s23 = zero2;
+                for (int k = 0; k < CPT; ++k) {
+                    if (pv[k]) {
+                        f2 s01 = zero2, s23 = zero2;
 #pragma unroll
-                    for (int i = 0; i < R; ++i) {
-                        if (i < rows) {
+                        for (int i = 0; i < R; ++i) {
                             f2 a01, a23;
                             lds_f2x2(base + (uint32_t)i * row_bytes + (uint32_t)(k * kV3Consumers * 32 * 16), a01,
                                      a23);
                             s01 = f2_fma(rr[i], a01, s01);
                             s23 = f2_fma(rr[i], a23, s23);
                         }
+                        gacc[k][0].add(s01);
+                        gacc[k][1].add(s23);
                     }
-                    gacc[k][0].add(s01);
-                    gacc[k][1].add(s23);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < CPT; ++k) {
+                    if (pv[k]) {
+                        f2 s01 = zero2, s23 = zero2;
+#pragma unroll
+                        for (int i = 0; i < R; ++i) {
+                            if (i < rows) {
+                                f2 a01, a23;
+                                lds_f2x2(base + (uint32_t)i * row_bytes + (uint32_t)(k * kV3Consumers * 32 * 16),
+                                         a01, a23);
+                                s01 = f2_fma(rr[i], a01, s01);
+                                s23 = f2_fma(rr[i], a23, s23);
+                            }
+                        }
+                        gacc[k][0].add(s01);
+                        gacc[k][1].add(s23);
+                    }
                 }
             }
             __syncwarp();
