@@ -1408,6 +1408,7 @@ extern "C" int ihs_solve_batched(ihs_ctx* ctx, const ihs_problem* probs_h, int32
                     break;
                 }
                 st = ihs_ctx_create(&L->lane[l], L->lstream[l], &ctx->p);
+                if (st == IHS_OK) L->lane[l]->no_coop = 1;   // 32 lanes factor side by side
             }
             if (st == IHS_OK) {
                 cudaMemPoolProps pp;

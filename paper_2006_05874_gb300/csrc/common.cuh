@@ -67,6 +67,7 @@ struct ihs_ctx {
     cudaStream_t aux;        // private stream for the look-ahead Cholesky (joined back before return)
     cudaEvent_t fev[8];      // fork/join events of the look-ahead Cholesky
     void* lanes;             // batched solves: sub-contexts, streams and memory pool kept across calls
+    int no_coop;             // 1: factorisations use the multi-launch form (many run side by side)
 };
 
 void ihs_lanes_destroy(void* lanes);   // batch.cu

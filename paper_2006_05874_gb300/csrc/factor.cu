@@ -300,6 +300,219 @@ __global__ void __launch_bounds__(256) k_syrk_rest(double* __restrict__ Kmat, in
         }
 }
 
+// ---------------------------------------------------------------------------
+// The same blocked Cholesky as one cooperative (persistent) launch: every CTA
+// stays resident and the block steps are separated by grid barriers instead
+// of kernel boundaries and stream events.  Step j:
+//   phase P: CTA 0 factors diagonal block j (and its inverse W_j) while the
+//            other CTAs apply panel j-1 to the trailing tiles of column
+//            blocks >= j+1 (the look-ahead overlap of the stream version);
+//   phase N: all CTAs form panel j (rows below block j) = K W_j^T;
+//   phase S: all CTAs update column block j+1 with panel j.
+// Matrix reads go through L2 (__ldcg): other SMs wrote them since the last
+// barrier.  Every barrier wait is bounded; a wait that gives up sets
+// IHS_DEV_TIMEOUT and the CTAs leave.
+
+// Grid barrier over gridDim.x CTAs: bar[0] arrivals, bar[1] generation.
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, unsigned* status) {
+    __shared__ int gs_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        gs_ok = 1;
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = global_timer_ns();
+            while (*vgen == gen) {
+                if (global_timer_ns() - t0 > 1000000000ull) {
+                    atomicOr(status, IHS_DEV_TIMEOUT);
+                    gs_ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return gs_ok != 0;
+}
+
+struct CholSmem {
+    double a[CB][CB + 1];
+    double w[CB][CB + 1];
+    double dinv[CB];
+    int bad;
+};
+
+__device__ void chol_potrf(CholSmem& S, double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
+                           double* __restrict__ Wd, unsigned* status) {
+    const int tid = threadIdx.x;
+    if (tid == 0) S.bad = 0;
+    for (int e = tid; e < CB * CB; e += 256) {
+        const int r = e / CB, c = e % CB;
+        S.a[r][c] = (r < nb && c < nb && c <= r) ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : 0.0;
+        S.w[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int tr = tid >> 3, tc = tid & 7;
+    for (int j = 0; j < nb; ++j) {
+        if (tid == 0) {
+            double p = S.a[j][j];
+            if (!(p > 0.0) || !isfinite(p)) {
+                S.bad = 1;
+                p = 1.0;
+            }
+            const double ri = rsqrt(p);
+            S.a[j][j] = p * ri;
+            S.dinv[j] = ri;
+        }
+        if (j > 0 && tid >= j && tid < nb) S.a[tid][j - 1] *= S.dinv[j - 1];
+        __syncthreads();
+        const double ip = S.dinv[j];
+        const double ip2 = ip * ip;
+        if (tr > j && tr < nb) {
+            const double arj = S.a[tr][j] * ip2;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int c = tc + 8 * h;
+                if (c > j && c <= tr) S.a[tr][c] = fma(-arj, S.a[c][j], S.a[tr][c]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int l = 0; l < nb; ++l) {
+        if (tid <= l) S.w[l][tid] *= S.dinv[l];
+        __syncthreads();
+        if (tr > l && tr < nb) {
+            const double arl = S.a[tr][l];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int c = tc + 8 * h;
+                if (c <= l) S.w[tr][c] = fma(-arl, S.w[l][c], S.w[tr][c]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < CB * CB; e += 256) {
+        const int r = e / CB, c = e % CB;
+        if (r < nb && c < nb && c <= r) Kmat[(j0 + r) * k + j0 + c] = S.a[r][c];
+        Wd[e] = (r < nb && c < nb && c <= r) ? S.w[r][c] : 0.0;
+    }
+    if (tid == 0 && S.bad) atomicOr(status, IHS_DEV_NOTPD);
+}
+
+__global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Kmat, int64_t k,
+                                                         double* __restrict__ Wall, unsigned* bar,
+                                                         unsigned* status) {
+    __shared__ CholSmem S;
+    __shared__ double pa[CB][CB + 1];
+    __shared__ double pb[CB][CB + 1];
+    const int tid = threadIdx.x;
+    const int G = gridDim.x, cta = blockIdx.x;
+    const int64_t T = ceil_div64(k, CB);
+    for (int64_t jb = 0; jb < T; ++jb) {
+        const int64_t j0 = jb * CB;
+        const int nb = (int)min((int64_t)CB, k - j0);
+        // ---- phase P: diagonal block jb | rest of the update by panel jb-1
+        if (cta == 0) chol_potrf(S, Kmat, k, j0, nb, Wall + jb * CB * CB, status);
+        if (jb > 0 && (cta > 0 || G == 1)) {
+            const int64_t jp0 = j0 - CB;          // panel jb-1 columns [jp0, jp0 + CB)
+            const int64_t j1 = j0;                 // trailing region starts at block jb
+            const int64_t Tr = ceil_div64(k - j1, CB);
+            const int64_t ntile = Tr * (Tr + 1) / 2;
+            const int workers = G > 1 ? G - 1 : 1, me = G > 1 ? cta - 1 : 0;
+            for (int64_t t = me; t < ntile; t += workers) {
+                int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+                while (I * (I + 1) / 2 > t) --I;
+                while ((I + 1) * (I + 2) / 2 <= t) ++I;
+                const int64_t J = t - I * (I + 1) / 2;
+                if (J < 1) continue;   // column block jb: done in phase S of step jb-1
+                __syncthreads();
+                for (int e = tid; e < CB * CB; e += 256) {
+                    const int rr = e / CB, q = e % CB;
+                    const int64_t ra = j1 + I * CB + rr, rb = j1 + J * CB + rr;
+                    pa[rr][q] = ra < k ? __ldcg(Kmat + ra * k + jp0 + q) : 0.0;
+                    pb[rr][q] = rb < k ? __ldcg(Kmat + rb * k + jp0 + q) : 0.0;
+                }
+                __syncthreads();
+                const int tx = tid % 16, ty = tid / 16;
+                double acc[2][2] = {};
+#pragma unroll 8
+                for (int q = 0; q < CB; ++q) {
+                    const double a0 = pa[ty][q], a1 = pa[ty + 16][q];
+                    const double b0 = pb[tx][q], b1 = pb[tx + 16][q];
+                    acc[0][0] = fma(a0, b0, acc[0][0]);
+                    acc[0][1] = fma(a0, b1, acc[0][1]);
+                    acc[1][0] = fma(a1, b0, acc[1][0]);
+                    acc[1][1] = fma(a1, b1, acc[1][1]);
+                }
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
+                        if (r < k && c <= r) Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - acc[a][b];
+                    }
+            }
+        }
+        if (!grid_sync_bounded(bar, status)) return;
+        const int64_t rest = k - j0 - nb;
+        if (rest <= 0) break;
+        // ---- phase N: panel jb, 8 rows per work item
+        {
+            const double* Wd = Wall + jb * CB * CB;
+            const int64_t items = ceil_div64(rest, 8);
+            for (int64_t it = cta; it < items; it += G) {
+                const int64_t r0 = j0 + nb + it * 8;
+                __syncthreads();
+                for (int e = tid; e < CB * CB; e += 256) pb[e % CB][e / CB] = __ldcg(Wd + e);   // pb[c][r] = W[r][c]
+                {
+                    const int r = tid / CB, c = tid % CB;
+                    pa[r][c] = (r0 + r < k && c < nb) ? __ldcg(Kmat + (r0 + r) * k + j0 + c) : 0.0;
+                }
+                __syncthreads();
+                const int tx = tid % CB, ty = tid / CB;
+                double acc = 0.0;
+                for (int q = 0; q < nb; ++q) acc = fma(pa[ty][q], pb[q][tx], acc);
+                const int64_t r = r0 + ty;
+                if (r < k && tx < nb) Kmat[r * k + j0 + tx] = acc;
+            }
+        }
+        if (!grid_sync_bounded(bar, status)) return;
+        // ---- phase S: column block jb+1 updated by panel jb
+        {
+            const int64_t j1 = j0 + nb;
+            const int ncol = (int)min((int64_t)CB, k - j1);
+            const int64_t items = ceil_div64(k - j1, 8);
+            for (int64_t it = cta; it < items; it += G) {
+                const int64_t r0 = j1 + it * 8;
+                __syncthreads();
+                for (int e = tid; e < CB * CB; e += 256) {
+                    const int c = e / CB, q = e % CB;
+                    pb[c][q] = (c < ncol && q < nb) ? __ldcg(Kmat + (j1 + c) * k + j0 + q) : 0.0;
+                }
+                {
+                    const int r = tid / CB, q = tid % CB;
+                    pa[r][q] = (r0 + r < k && q < nb) ? __ldcg(Kmat + (r0 + r) * k + j0 + q) : 0.0;
+                }
+                __syncthreads();
+                const int tx = tid % CB, ty = tid / CB;
+                double acc = 0.0;
+                for (int q = 0; q < nb; ++q) acc = fma(pa[ty][q], pb[tx][q], acc);
+                const int64_t r = r0 + ty, c = j1 + tx;
+                if (r < k && tx < ncol && c <= r) Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - acc;
+            }
+        }
+        if (!grid_sync_bounded(bar, status)) return;
+    }
+}
+
 // X (FP32, k x k) <- zero, then each 64 x 64 diagonal block of X = the FP32
 // inverse of the matching block of L (one CTA per block, thread = column,
 // forward substitution); these start the recursive doubling below.
@@ -584,10 +797,30 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
     // which overlaps the factorisation of block jb+1.  Events order the
     // writes: the update of column jb+1 (main) follows the previous rest
     // update (aux), and each rest update follows its panel.
+    const int64_t TC = ceil_div64(k, CB);
+    // One cooperative launch when the context allows it (contexts that run many
+    // factorisations side by side take the stream version below).
+    if (!ctx->no_coop && TC > 1) {
+        int per_sm = 0;
+        IHS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_persistent, 256, 0));
+        const int64_t first_tiles = (TC - 1) * TC / 2;
+        int G = (int)std::min<int64_t>(ctx->sm_count, std::max<int64_t>(1, (first_tiles + 1) / 2));
+        G = std::min(G, per_sm * ctx->sm_count);
+        if (G >= 1) {
+            unsigned* bar = ctx->d_status + 16;
+            IHS_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+            int64_t kk = k;
+            void* args[] = {&Kmat, &kk, &Wall, &bar, &ctx->d_status};
+            IHS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_chol_persistent, dim3((unsigned)G), dim3(256),
+                                                     args, 0, s));
+            ihs_count_launch();
+            goto inverse;
+        }
+    }
+    {
     cudaStream_t aux = ctx->aux;
     IHS_CUDA_TRY(cudaEventRecord(ctx->fev[7], s));     // gram done
     IHS_CUDA_TRY(cudaStreamWaitEvent(aux, ctx->fev[7], 0));
-    const int64_t TC = ceil_div64(k, CB);
     for (int64_t jb = 0; jb < TC; ++jb) {
         const int64_t j0 = jb * CB;
         const int nb = (int)std::min<int64_t>(CB, k - j0);
@@ -615,6 +848,8 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
     }
     IHS_CUDA_TRY(cudaEventRecord(ctx->fev[6], aux));
     IHS_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fev[6], 0));
+    }
+inverse:
     // X = L^{-1} in FP32 by recursive doubling: diagonal 64-blocks are FP32
     // inverses of L's blocks; for block size sz = 64, 128, ... the lower-left
     // block of each pair is X21 = -X22 (L21 X11).
