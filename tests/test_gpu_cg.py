@@ -25,15 +25,18 @@ def test_cg_reaches_direct_solution(ctx, torch_cuda, spec_problem):
     assert linalg.relative_error(p.A, p.nu, x.cpu().numpy(), xs) < 1e-5
 
 
-def test_cg_iterations_match_oracle(ctx, torch_cuda, spec_problem):
+@pytest.mark.parametrize("tol", [1e-3, 1e-4])
+def test_cg_iterations_match_oracle(ctx, torch_cuda, spec_problem, tol):
     """Same algorithm, same stopping rule: iteration counts agree where FP32
-    vectors are not yet limiting (residual tolerance 1e-6)."""
+    vectors are not limiting.  The attainable relative residual of FP32 CG is
+    about u kappa(H) (u = 2^-24; kappa(H) = (1 + nu^2) / (sigma_d^2 + nu^2) ~ 400
+    here, so ~ 2.4e-5): the counts are compared at tolerances well above it."""
     torch = torch_cuda
     p, xs = spec_problem
     x = torch.zeros(p.d, device="cuda")
-    rep = ctx.cg(torch.from_numpy(p.A).cuda(), torch.from_numpy(p.b).cuda(), p.nu, x, tol=1e-6, max_iter=5000)
-    _, it_ref, _ = oracle_cg.cg(p.A, p.b, p.nu, tol=1e-6, max_iter=5000)
-    assert abs(rep.iterations - it_ref) <= max(3, 0.25 * it_ref)
+    rep = ctx.cg(torch.from_numpy(p.A).cuda(), torch.from_numpy(p.b).cuda(), p.nu, x, tol=tol, max_iter=5000)
+    _, it_ref, _ = oracle_cg.cg(p.A, p.b, p.nu, tol=tol, max_iter=5000)
+    assert abs(rep.iterations - it_ref) <= max(2, 0.1 * it_ref)
 
 
 @pytest.mark.parametrize("kind", ["srht", "gauss"])
