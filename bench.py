@@ -192,7 +192,7 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_profile(what, rows=N_ROWS):
+def run_profile(what, rows=N_ROWS, m=1024):
     """Warm up, then run the named piece once inside the NVTX range "profiled"
     (for ncu --nvtx --nvtx-include "profiled/" or -k/-s/-c captures)."""
     import torch
@@ -219,7 +219,7 @@ def run_profile(what, rows=N_ROWS):
             g = torch.empty(D_COLS, device="cuda")
             fn = lambda: ctx.grad(A, b, 0.015, x, g, want_axnorm2=False)
         else:
-            m = 1024   # the sketch size the solves settle at (SRHT level 10; BF16 Gaussian warm start)
+            # default m = 1024: the sketch size the solves settle at (SRHT level 10; BF16 Gaussian warm start)
             SA = torch.empty(m, D_COLS, device="cuda")
             fn = lambda: ctx.sketch(A, m, what, 0, 10, SA)
     for _ in range(2):
@@ -497,12 +497,13 @@ def main():
     ap.add_argument("--profile", choices=["solve", "grad", "srht", "gauss"], default=None)
     ap.add_argument("--profile-rows", type=int, default=N_ROWS,
                     help="rows of A for --profile grad|srht|gauss (a smaller case for ncu captures)")
+    ap.add_argument("--profile-m", type=int, default=1024, help="sketch size for --profile srht|gauss")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.profile:
-        run_profile(args.profile, args.profile_rows)
+        run_profile(args.profile, args.profile_rows, args.profile_m)
         return
     import torch
 

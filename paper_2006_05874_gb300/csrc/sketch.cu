@@ -106,26 +106,46 @@ k_srht_fwht(const float* __restrict__ A, int64_t n, int d, int64_t m, int Q, int
 // index bits against the block index p.
 constexpr int kR32C = 16, kR32T = 512, kR32Stride = 528;   // 528 = 33 x 16: conflict-free transposes
 
+// (x, y) <- (x + y, x - y) lane-wise on two packed FP32x2 registers (sm_100+:
+// two IEEE binary32 operations per instruction, each rounded as a scalar one).
+__device__ __forceinline__ void bfly_x2(unsigned long long& x, unsigned long long& y) {
+    unsigned long long s, t;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s) : "l"(x), "l"(y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(x), "l"(y));
+    x = s;
+    y = t;
+}
+
+// 32-point unnormalised WHT in registers.  The stages on index bits 0..3 run
+// on the packed pairs (v[i], v[i + 16]), the stage on bit 4 last on scalars;
+// every output is the same sequence of rounded additions as the radix-2
+// stages taken in the order h = 1, 2, 4, 8, 16.
 __device__ __forceinline__ void wht32(float (&v)[32]) {
+    unsigned long long q[16];
 #pragma unroll
-    for (int h = 1; h < 32; h <<= 1) {
+    for (int i = 0; i < 16; ++i) asm("mov.b64 %0, {%1, %2};" : "=l"(q[i]) : "f"(v[i]), "f"(v[i + 16]));
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            if ((i & h) == 0) {
-                const float a = v[i], b = v[i + h];
-                v[i] = __fadd_rn(a, b);
-                v[i + h] = __fsub_rn(a, b);
-            }
-        }
+    for (int h = 1; h < 16; h <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if ((i & h) == 0) bfly_x2(q[i], q[i + h]);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        float a, b;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(q[i]));
+        v[i] = __fadd_rn(a, b);
+        v[i + 16] = __fsub_rn(a, b);
     }
 }
 
 // Shared memory of k_srht_r32: two TMA stages of 1024 x 16 floats, the padded
-// transpose buffer, sign words, two mbarriers, per-row offsets.
+// transpose buffer, sign words, two mbarriers, one (T byte offset, block-index
+// bits) pair per accumulator slot (32 MA slots; slots >= m point at T[0]).
 constexpr size_t kR32Stage = 1024 * kR32C * sizeof(float);   // 64 KiB
-__host__ __device__ inline size_t r32_smem_bytes(int64_t mrows) {
+__host__ __device__ inline size_t r32_smem_bytes(int ma) {
     return 2 * kR32Stage + (size_t)32 * kR32Stride * sizeof(float) + 32 * sizeof(uint32_t) + 2 * sizeof(uint64_t) +
-           2 * (size_t)mrows * sizeof(int32_t);
+           (size_t)32 * ma * sizeof(int2);
 }
 
 // MA accumulators per thread: this launch handles m <= 32 MA selected rows;
@@ -142,8 +162,7 @@ k_srht_r32(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t m
     float* T = reinterpret_cast<float*>(smraw + 2 * kR32Stage);                      // 32 x 528
     uint32_t* sbits = reinterpret_cast<uint32_t*>(T + 32 * kR32Stride);              // 32 sign words
     uint64_t* full = reinterpret_cast<uint64_t*>(sbits + 32);                        // 2 mbarriers
-    int32_t* toff = reinterpret_cast<int32_t*>(full + 2);                            // T offset per selected row
-    uint32_t* rhi = reinterpret_cast<uint32_t*>(toff + m);                           // its block-index bits
+    int2* sel = reinterpret_cast<int2*>(full + 2);                                  // 32 MA slots
     const int tid = threadIdx.x;
     const int c = tid & 15, ql = tid >> 4;
     const int col0 = blockIdx.x * kR32C;
@@ -157,11 +176,15 @@ k_srht_r32(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t m
         mbar_init(&full[1], 1);
         fence_mbar_init();
     }
-    for (int64_t j = tid; j < m; j += kR32T) {
-        const uint32_t r = (uint32_t)rows[j];
-        const uint32_t lo = r & 1023u;
-        toff[j] = (int32_t)((lo >> 5) * kR32Stride + (lo & 31u) * 16);
-        rhi[j] = r >> 10;
+    for (int j = tid; j < 32 * MA; j += kR32T) {
+        int2 e = make_int2(0, 0);
+        if (j < m) {
+            const uint32_t r = (uint32_t)rows[j];
+            const uint32_t lo = r & 1023u;
+            e.x = (int)(((lo >> 5) * kR32Stride + (lo & 31u) * 16) * sizeof(float));
+            e.y = (int)(r >> 10);
+        }
+        sel[j] = e;
     }
     __syncthreads();
     auto issue = [&](int64_t b) {   // block p0 + b into stage b & 1
@@ -212,14 +235,15 @@ k_srht_r32(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t m
 #pragma unroll
         for (int l = 0; l < 32; ++l) T[ql * kR32Stride + l * 16 + c] = v[l];
         __syncthreads();
-        const uint32_t pb = (uint32_t)p;
+        // every slot accumulates (slots >= m read T[0] and are never stored):
+        // no branches on the gather path
+        const int pb = (int)p;
+        const unsigned char* Tc = reinterpret_cast<const unsigned char*>(T + c);
 #pragma unroll
         for (int i = 0; i < MA; ++i) {
-            const int64_t j = ql + 32 * i;
-            if (j < m) {
-                const float val = T[toff[j] + c];
-                acc[i] += (__popc(rhi[j] & pb) & 1) ? -val : val;
-            }
+            const int2 e = sel[ql + 32 * i];
+            const float val = *reinterpret_cast<const float*>(Tc + e.x);
+            acc[i] += __int_as_float(__float_as_int(val) ^ (int)((unsigned)__popc(e.y & pb) << 31));
         }
     }
     if (b < nblk) {
@@ -241,10 +265,196 @@ k_srht_r32(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t m
     }
 }
 
+// Small-m variant: blocks of 512 rows (H_512 = H_32 (x) H_16, row 16 k + ql
+// with k the high five and ql the low four index bits), CTAs of 256 threads
+// = 16 columns x 16 ql, two CTAs per SM so that one CTA's shared-memory phases
+// overlap the other's arithmetic.  Each TMA stage (512 x 16 floats) is also
+// its block's transpose buffer: Z[K][ql] and then Y[16 K + L] sit at float
+// offset q5_pos(K, L) + c, swizzled (L ^ (K & 1)) so that both the transposed
+// reads and writes are free of bank conflicts.  The selected rows are then
+// summed with the sign (-1)^popc(hi & q) of their high bits hi = r >> 9
+// against the 512-row block index q (H_n = H_{n/512} (x) H_512).  The sign of
+// row 512 q + 16 k + ql is bit 16 (q & 1) + (k >> 1) of word 16 (k & 1) + ql of
+// the 1024-row block q >> 1: the same signs as every other SRHT path.
+constexpr int kQ5C = 16, kQ5T = 256, kQ5S = 3;
+constexpr size_t kQ5Stage = 512 * kQ5C * sizeof(float);   // 32 KiB
+__host__ __device__ constexpr int q5_pos(int K, int L) { return K * 256 + ((L ^ (K & 1)) * 16); }
+__host__ __device__ inline size_t q5_smem_bytes(int ma) {
+    return kQ5S * kQ5Stage + 32 * sizeof(uint32_t) + kQ5S * sizeof(uint64_t) + (size_t)16 * ma * sizeof(int2);
+}
+
+// 16-point WHTs of two independent vectors a and b, packed lane-wise: every
+// stage on (a[i], b[i]) pairs, stages in the order h = 1, 2, 4, 8.
+__device__ __forceinline__ void wht16_pair(float (&a)[16], float (&b)[16]) {
+    unsigned long long q[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) asm("mov.b64 %0, {%1, %2};" : "=l"(q[i]) : "f"(a[i]), "f"(b[i]));
+#pragma unroll
+    for (int h = 1; h < 16; h <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if ((i & h) == 0) bfly_x2(q[i], q[i + h]);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) asm("mov.b64 {%0, %1}, %2;" : "=f"(a[i]), "=f"(b[i]) : "l"(q[i]));
+}
+
+// MA accumulators per thread: m <= 16 MA selected rows, thread (c, ql)
+// accumulating rows ql + 16 i of column c; slots >= m read T[0] and are never
+// stored.  Rows >= n and columns >= d arrive as zeros from the TMA.
+template <int MA>
+__global__ void __launch_bounds__(kQ5T, 2)
+k_srht_q512(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t m_total, int64_t row_off,
+            int64_t P5, int PG, const int32_t* __restrict__ rows, uint32_t level, uint32_t k0, uint32_t k1,
+            unsigned* status, float* __restrict__ out /* PG x m_total x d partials */) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float* stage = reinterpret_cast<float*>(smraw);                                   // 3 x 512 x 16
+    uint32_t* sbits = reinterpret_cast<uint32_t*>(smraw + kQ5S * kQ5Stage);           // 32 sign words
+    uint64_t* full = reinterpret_cast<uint64_t*>(sbits + 32);                        // 3 mbarriers
+    int2* sel = reinterpret_cast<int2*>(full + kQ5S);                                // 16 MA slots
+    const int tid = threadIdx.x;
+    const int c = tid & 15, ql = tid >> 4;
+    const int col0 = blockIdx.x * kQ5C;
+    const int pg = blockIdx.y;
+    const int64_t q0 = (int64_t)pg * P5 / PG, q1 = (int64_t)(pg + 1) * P5 / PG;
+    const int64_t nblk = q1 - q0;
+
+    if (tid == 0) {
+        for (int i = 0; i < kQ5S; ++i) mbar_init(&full[i], 1);
+        fence_mbar_init();
+    }
+    for (int j = tid; j < 16 * MA; j += kQ5T) {
+        int2 e = make_int2(0, 0);
+        if (j < m) {
+            const uint32_t r = (uint32_t)rows[j];
+            const int lo = (int)(r & 511u);
+            e.x = q5_pos(lo >> 4, lo & 15) * (int)sizeof(float);
+            e.y = (int)(r >> 9);
+        }
+        sel[j] = e;
+    }
+    __syncthreads();
+    auto issue = [&](int64_t bb) {   // block q0 + bb into stage bb % 3
+        const int sidx = (int)(bb % kQ5S);
+        float* dst = stage + (size_t)sidx * (512 * kQ5C);
+        mbar_arrive_expect_tx(&full[sidx], (uint32_t)kQ5Stage);
+        const int y0 = (int)((q0 + bb) * 512);
+        tma_load_2d(dst, &amap, col0, y0, &full[sidx]);
+        tma_load_2d(dst + 256 * kQ5C, &amap, col0, y0 + 256, &full[sidx]);
+    };
+    int64_t issued = 0;
+    if (tid == 0) {
+        for (; issued < kQ5S && issued < nblk; ++issued) issue(issued);
+    }
+    float acc[MA];
+#pragma unroll
+    for (int i = 0; i < MA; ++i) acc[i] = 0.f;
+    // this thread's transposed offsets: writes of Z[K][ql] (even / odd K), and
+    // the two K = ql, ql + 16 it transforms next (even / odd L)
+    const int wE = ql * 16 + c, wO = (ql ^ 1) * 16 + c;
+    const int sw = (ql & 1) * 16;
+    const int rE = ql * 256 + c + sw, rO = ql * 256 + c - sw;
+    int64_t b = 0;
+    int sidx = 0;
+    uint32_t ph = 0;
+    for (; b < nblk; ++b) {
+        const int64_t q = q0 + b;
+        if (tid < 8) {
+            const uint4 w = srht_sign_words((uint64_t)(q >> 1) * 8 + tid, level, k0, k1);
+            sbits[4 * tid + 0] = w.x;
+            sbits[4 * tid + 1] = w.y;
+            sbits[4 * tid + 2] = w.z;
+            sbits[4 * tid + 3] = w.w;
+        }
+        const bool ok = mbar_wait_bounded(&full[sidx], ph, status);
+        if (__syncthreads_or(!ok)) break;   // also: sign words ready, block b - 1 fully gathered
+        if (tid == 0 && b >= 1 && issued < nblk) issue(issued++);   // into the stage of block b - 1
+        float* st = stage + (size_t)sidx * (512 * kQ5C);
+        float v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = st[(16 * k + ql) * kQ5C + c];
+        const int hsh = (int)(q & 1) * 16;
+        const uint32_t w0 = sbits[ql] >> hsh, w1 = sbits[16 + ql] >> hsh;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t w = (k & 1) ? w1 : w0;
+            v[k] = __int_as_float(__float_as_int(v[k]) ^ (int)((w << (31 - (k >> 1))) & 0x80000000u));
+        }
+        wht32(v);   // over k: v[K] = Z[K][ql]
+        __syncthreads();   // the stage is fully read: overwrite it with Z
+#pragma unroll
+        for (int K = 0; K < 32; ++K) st[K * 256 + ((K & 1) ? wO : wE)] = v[K];
+        __syncthreads();
+        float a[16], bb[16];
+#pragma unroll
+        for (int L = 0; L < 16; ++L) {
+            const int o = L * 16 + ((L & 1) ? rO : rE);
+            a[L] = st[o];
+            bb[L] = st[o + 16 * 256];
+        }
+        wht16_pair(a, bb);   // over ql: Y[16 K + L] for K = ql and ql + 16
+#pragma unroll
+        for (int L = 0; L < 16; ++L) {   // back to the positions this thread read
+            const int o = L * 16 + ((L & 1) ? rO : rE);
+            st[o] = a[L];
+            st[o + 16 * 256] = bb[L];
+        }
+        // order these generic writes before the TMA load that will refill the stage
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        const int qb = (int)q;
+        const unsigned char* Tc = reinterpret_cast<const unsigned char*>(st + c);
+#pragma unroll
+        for (int i = 0; i < MA; ++i) {
+            const int2 e = sel[ql + 16 * i];
+            const float val = *reinterpret_cast<const float*>(Tc + e.x);
+            acc[i] += __int_as_float(__float_as_int(val) ^ (int)((unsigned)__popc(e.y & qb) << 31));
+        }
+        if (++sidx == kQ5S) {
+            sidx = 0;
+            ph ^= 1u;
+        }
+    }
+    if (b < nblk) {
+        // a wait gave up: let the copies in flight land before exiting
+        if (tid == 0) {
+            for (int64_t t = b; t < issued; ++t)
+                mbar_wait_bounded(&full[t % kQ5S], (uint32_t)((t / kQ5S) & 1), status);
+        }
+        __syncthreads();
+        return;
+    }
+    const int col = col0 + c;
+    if (col < d) {
+        float* outp = out + ((size_t)pg * m_total + row_off) * d + col;
+#pragma unroll
+        for (int i = 0; i < MA; ++i) {
+            const int64_t j = ql + 16 * i;
+            if (j < m) outp[j * d] = acc[i];
+        }
+    }
+}
+
+template <int MA>
+int launch_q512(ihs_ctx* ctx, const CUtensorMap& amap, int d, int64_t mc, int64_t m, int64_t c0, int64_t P5, int PG,
+                const int32_t* rows, int32_t level, uint64_t seed, float* part) {
+    const size_t smem = q5_smem_bytes(MA);
+    auto kern = k_srht_q512<MA>;
+    IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
+    // two CTAs per SM need the largest shared-memory carveout
+    IHS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    dim3 grid((unsigned)ceil_div64(d, kQ5C), (unsigned)PG);
+    kern<<<grid, kQ5T, smem, ctx->stream>>>(amap, d, mc, m, c0, P5, PG, rows, (uint32_t)level, (uint32_t)seed,
+                                           (uint32_t)(seed >> 32), ctx->d_status, part);
+    IHS_LAUNCH_CHECK();
+    return IHS_OK;
+}
+
 template <int MA>
 int launch_r32(ihs_ctx* ctx, const CUtensorMap& amap, int d, int64_t mc, int64_t m, int64_t c0, int64_t P, int PG,
                const int32_t* rows, int32_t level, uint64_t seed, float* part) {
-    const size_t smem = r32_smem_bytes(mc);
+    const size_t smem = r32_smem_bytes(MA);
     auto kern = k_srht_r32<MA>;
     IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
     dim3 grid((unsigned)ceil_div64(d, kR32C), (unsigned)PG);
@@ -371,19 +581,23 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
     const bool tma = Q == 1024 && ihs_tensor_map_f32(&amap, A, n, d, d, kR32C, 256) == IHS_OK;
     if (tma) {
         // Selected rows go in chunks of at most 1024 (32 register accumulators
-        // per thread); each chunk re-reads A.
+        // per thread); each chunk re-reads A.  Chunks of <= 256 rows run the
+        // 512-row-block kernel at two CTAs per SM, larger ones the 1024-row one.
         const int64_t chunk = std::min<int64_t>(m, 1024);
         const int64_t CT32 = ceil_div64(d, kR32C);
-        // one CTA per SM: a grid of CT32 x PG32 CTAs in whole waves when the
-        // block ranges allow it (PG32 = SMs / gcd(CT32, SMs)), else >= 1 wave
-        int64_t g = CT32, h = ctx->sm_count;
+        const bool small = m <= 256;
+        // a grid of CT32 x PG32 CTAs in whole waves when the block ranges allow
+        // it (PG32 = slots / gcd(CT32, slots), slots = SMs x CTAs per SM), else
+        // >= 1 wave
+        const int64_t slots = (int64_t)ctx->sm_count * (small ? 2 : 1);
+        int64_t g = CT32, h = slots;
         while (h) {
             const int64_t t = g % h;
             g = h;
             h = t;
         }
-        int64_t PG32 = ctx->sm_count / g;
-        if (PG32 > P || PG32 * m * d * 4 > ((int64_t)1 << 30)) PG32 = std::max<int64_t>(1, ceil_div64((int64_t)ctx->sm_count, CT32));
+        int64_t PG32 = slots / g;
+        if (PG32 > P || PG32 * m * d * 4 > ((int64_t)1 << 30)) PG32 = std::max<int64_t>(1, ceil_div64(slots, CT32));
         PG32 = std::min<int64_t>(PG32, P);
         if (PG32 > PG) {
             IHS_TRY(ihs_scratch(ctx, SLOT_SKETCH_PART, (size_t)PG32 * m * d * sizeof(float), &pws));
@@ -393,7 +607,10 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
         for (int64_t c0 = 0; c0 < m; c0 += chunk) {
             const int64_t mc = std::min<int64_t>(chunk, m - c0);
             int st;
-            if (mc <= 32 * 4) st = launch_r32<4>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, part);
+            if (mc <= 16) st = launch_q512<1>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, part);
+            else if (mc <= 64) st = launch_q512<4>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, part);
+            else if (mc <= 128) st = launch_q512<8>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, part);
+            else if (mc <= 256) st = launch_q512<16>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, part);
             else if (mc <= 32 * 16) st = launch_r32<16>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, part);
             else st = launch_r32<32>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, part);
             IHS_TRY(st);

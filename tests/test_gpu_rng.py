@@ -17,13 +17,26 @@ def test_signs_bit_exact(ctx, torch_cuda, n_pad, seed, level):
 
 
 @pytest.mark.parametrize("n_pad,m", [(64, 1), (64, 64), (1000, 37), (4096, 300), (4096, 4095),
-                                     (131072, 1024), (1 << 20, 5000)])
+                                     (131072, 1024), (1 << 20, 5000), (131072, 1), (131072, 16),
+                                     (1 << 20, 6144), (1 << 20, 6145), (9000, 8000), (1 << 22, 3000),
+                                     (8193, 2)])
 @pytest.mark.parametrize("seed,level", [(0, 0), (99, 7)])
 def test_rows_bit_exact(ctx, torch_cuda, n_pad, m, seed, level):
     torch = torch_cuda
     rows = torch.full((m,), -1, dtype=torch.int32, device="cuda")
     ctx.srht_rows(n_pad, m, seed, level, rows)
     assert np.array_equal(rows.cpu().numpy().astype(np.int64), rng.select_rows(n_pad, m, seed, level))
+
+
+@pytest.mark.parametrize("n_pad,m", [(64, 64), (4096, 300), (131072, 1), (131072, 1000), (20000, 6144)])
+def test_rows_exact_fallback(ctx, torch_cuda, monkeypatch, n_pad, m):
+    """The single-CTA fallback of the threshold selection (bisection for the
+    m-th smallest key, then a direct compaction) gives the same rows."""
+    torch = torch_cuda
+    monkeypatch.setenv("IHS_SELECT_FORCE_FALLBACK", "1")
+    rows = torch.full((m,), -1, dtype=torch.int32, device="cuda")
+    ctx.srht_rows(n_pad, m, 5, 2, rows)
+    assert np.array_equal(rows.cpu().numpy().astype(np.int64), rng.select_rows(n_pad, m, 5, 2))
 
 
 def test_rows_rejects_bad_sizes(ctx, torch_cuda):

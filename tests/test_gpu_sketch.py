@@ -24,7 +24,8 @@ def _relfro(a, b):
 
 @pytest.mark.parametrize("n,d,m", [(4096, 256, 1), (4096, 256, 7), (4096, 256, 64), (4096, 256, 300),
                                    (3000, 100, 512), (100, 37, 16), (4096, 256, 2048), (4096, 64, 4096),
-                                   (5000, 48, 33), (1, 8, 1)])
+                                   (5000, 48, 33), (1, 8, 1), (3000, 100, 200), (4096, 64, 1100),
+                                   (2048, 80, 256), (1025, 32, 17)])
 @pytest.mark.parametrize("seed,level", [(0, 3), (77, 0)])
 def test_srht_parity(ctx, torch_cuda, n, d, m, seed, level):
     A = problems.random_matrix(n, d, seed=n * 7 + d)
@@ -51,6 +52,17 @@ def test_srht_full_size_sampled_rows(ctx, torch_cuda):
     got = _sketch(torch_cuda, ctx, A, m, "srht", 0, 10)
     which = [0, 1, 255, 511, 700, 1023]
     ref = sketch.srht_rows_explicit(A, m, 0, 10, which=which)
+    for k, j in enumerate(which):
+        assert _relfro(got[j], ref[k]) <= TOL
+
+
+@pytest.mark.parametrize("m,which", [(16, [0, 7, 15]), (200, [0, 99, 199])])
+def test_srht_full_size_small_m_sampled_rows(ctx, torch_cuda, m, which):
+    """131072 x 2048 at the small sketch sizes of the first levels (512-row
+    block kernel): sampled rows against explicit +-1 sums."""
+    A = problems.random_matrix(131072, 2048, seed=14, scale=1.0 / 45.0)
+    got = _sketch(torch_cuda, ctx, A, m, "srht", 0, 4)
+    ref = sketch.srht_rows_explicit(A, m, 0, 4, which=which)
     for k, j in enumerate(which):
         assert _relfro(got[j], ref[k]) <= TOL
 
