@@ -145,73 +145,128 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ 
 constexpr int CB = 32;
 
 // Diagonal block [j0, j0+nb) of the FP64 Cholesky, in place, and its inverse
-// W = L_jj^{-1} (CB x CB, lower, at Wd) for the panel.  Per column: thread 0
-// forms the reciprocal pivot with one rsqrt (FP64 division and square root
-// are long dependent sequences); then every thread updates its trailing
-// entries with the unscaled column and 1/pivot, while column j is scaled in
-// the next column's first phase.  Non-positive or non-finite pivots set
-// IHS_DEV_NOTPD (the pivot is replaced by 1 so that the kernel finishes).
-__global__ void __launch_bounds__(256) k_potrf32(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
-                                                 double* __restrict__ Wd, unsigned* status) {
-    __shared__ double a[CB][CB + 1];
-    __shared__ double w[CB][CB + 1];
-    __shared__ double dinv[CB];
-    __shared__ int bad;
+// W = L_jj^{-1} (CB x CB, lower, at Wd) for the panel; one CTA of 256 threads.
+// The pivots form a dependent chain of CB reciprocal square roots (a long
+// FP64 latency each), so thread 0 runs that chain alone: at step j it applies
+// column j to the next pivot itself, p_{j+1} = a_{j+1,j+1} - (a_{j+1,j} / sqrt(p_j))^2,
+// and starts its rsqrt at once, while warps 1..7 apply column j to the rest
+// of the trailing triangle (entries packed by descending column, so that the
+// warps with no entries left skip the step).  Columns stay unscaled (a_rc with
+// the pivot p_c on the diagonal) until one final pass forms L_rc = a_rc / sqrt(p_c).
+// W follows by forward substitution row by row, one trailing entry per
+// thread per row.  Rows and columns >= nb are padded with the identity.
+// Non-positive or non-finite pivots set IHS_DEV_NOTPD (the pivot is replaced
+// by 1 so that the kernel finishes).
+struct CholSmem {
+    double a[CB][CB + 1];
+    double w[CB][CB + 1];
+    double dinv[CB];
+    int bad;
+};
+
+__device__ void chol_potrf(CholSmem& S, double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
+                           double* __restrict__ Wd, unsigned* status) {
+    static_assert(CB == 32, "the packed entry mapping assumes CB = 32 and 256 threads");
     const int tid = threadIdx.x;
-    if (tid == 0) bad = 0;
+    if (tid == 0) S.bad = 0;
     for (int e = tid; e < CB * CB; e += 256) {
         const int r = e / CB, c = e % CB;
-        a[r][c] = (r < nb && c < nb && c <= r) ? Kmat[(j0 + r) * k + j0 + c] : 0.0;
-        w[r][c] = (r == c) ? 1.0 : 0.0;
+        double v = 0.0;
+        if (c <= r) v = (r < nb) ? (c < nb ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : 0.0) : (r == c ? 1.0 : 0.0);
+        S.a[r][c] = v;
+        S.w[r][c] = 0.0;
+    }
+    // this thread's trailing entries (bulk threads 32..255): lower-triangle
+    // entries ordered by descending column, e -> group g = 31 - c of g + 1 rows
+    int er[3], ec[3], ei[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int e = tid - 32 + 224 * q;
+        ei[q] = e;
+        int g = 0;
+        if (e >= 0 && e < CB * (CB + 1) / 2) {
+            g = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+            while (g * (g + 1) / 2 > e) --g;
+            while ((g + 1) * (g + 2) / 2 <= e) ++g;
+        } else {
+            ei[q] = 1 << 20;   // never active
+        }
+        ec[q] = CB - 1 - g;
+        er[q] = ec[q] + (e - g * (g + 1) / 2);
     }
     __syncthreads();
-    // thread -> (row r, two columns c, c + 16) of the lower triangle
-    const int tr = tid >> 3, tc = tid & 7;
-    for (int j = 0; j < nb; ++j) {
+    double ri = 0.0;   // thread 0: 1 / sqrt(p_j) of the current step
+    if (tid == 0) {
+        double p = S.a[0][0];
+        if (!(p > 0.0) || !isfinite(p)) {
+            S.bad = 1;
+            p = 1.0;
+            S.a[0][0] = p;
+        }
+        ri = rsqrt(p);
+        S.dinv[0] = ri;
+    }
+    __syncthreads();
+    for (int j = 0; j < CB - 1; ++j) {
         if (tid == 0) {
-            double p = a[j][j];
+            const double l = S.a[j + 1][j] * ri;
+            double p = fma(-l, l, S.a[j + 1][j + 1]);
             if (!(p > 0.0) || !isfinite(p)) {
-                bad = 1;
+                S.bad = 1;
                 p = 1.0;
             }
-            const double ri = rsqrt(p);
-            a[j][j] = p * ri;
-            dinv[j] = ri;
-        }
-        if (j > 0 && tid >= j && tid < nb) a[tid][j - 1] *= dinv[j - 1];   // scale column j-1
-        __syncthreads();
-        const double ip = dinv[j];
-        const double ip2 = ip * ip;
-        if (tr > j && tr < nb) {
-            const double arj = a[tr][j] * ip2;
+            S.a[j + 1][j + 1] = p;
+            ri = rsqrt(p);
+            S.dinv[j + 1] = ri;
+        } else if (tid >= 32) {
+            // entries with column > j lead the order: e < (31 - j)(32 - j) / 2
+            const int active = (CB - 1 - j) * (CB - j) / 2;
+            const int diag_next = (CB - 2 - j) * (CB - 1 - j) / 2;   // entry (j+1, j+1): thread 0's
+            if (tid - 32 < active) {
+                const double rj = S.dinv[j];
+                const double ip2 = rj * rj;
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int c = tc + 8 * h;
-                if (c > j && c <= tr) a[tr][c] = fma(-arj, a[c][j], a[tr][c]);
+                for (int q = 0; q < 3; ++q) {
+                    if (ei[q] < active && ei[q] != diag_next) {
+                        const int r = er[q], c = ec[q];
+                        S.a[r][c] = fma(-S.a[r][j] * ip2, S.a[c][j], S.a[r][c]);
+                    }
+                }
             }
         }
         __syncthreads();
     }
-    // W = L^{-1} by right-looking forward substitution on the identity.
-    for (int l = 0; l < nb; ++l) {
-        if (tid <= l) w[l][tid] *= dinv[l];
-        __syncthreads();
-        if (tr > l && tr < nb) {
-            const double arl = a[tr][l];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int c = tc + 8 * h;
-                if (c <= l) w[tr][c] = fma(-arl, w[l][c], w[tr][c]);
-            }
+    // L_rc = a_rc / sqrt(p_c) (on the diagonal p_c / sqrt(p_c))
+    for (int e = tid; e < CB * CB; e += 256) {
+        const int r = e / CB, c = e % CB;
+        if (c <= r) S.a[r][c] *= S.dinv[c];
+    }
+    if (tid == 0) S.w[0][0] = S.dinv[0];
+    __syncthreads();
+    // W = L^{-1}: after step l, row l + 1 is final
+    for (int l = 0; l < CB - 1; ++l) {
+        const int width = l + 1;
+        if (tid < (CB - 1 - l) * width) {
+            const int r = l + 1 + tid / width, c = tid % width;
+            double v = fma(-S.a[r][l], S.w[l][c], S.w[r][c]);
+            if (r == l + 1) v *= S.dinv[l + 1];
+            S.w[r][c] = v;
         }
+        if (tid == 0) S.w[l + 1][l + 1] = S.dinv[l + 1];
         __syncthreads();
     }
     for (int e = tid; e < CB * CB; e += 256) {
         const int r = e / CB, c = e % CB;
-        if (r < nb && c < nb && c <= r) Kmat[(j0 + r) * k + j0 + c] = a[r][c];
-        Wd[e] = (r < nb && c < nb && c <= r) ? w[r][c] : 0.0;
+        if (r < nb && c < nb && c <= r) Kmat[(j0 + r) * k + j0 + c] = S.a[r][c];
+        Wd[e] = (r < nb && c < nb && c <= r) ? S.w[r][c] : 0.0;
     }
-    if (tid == 0 && bad) atomicOr(status, IHS_DEV_NOTPD);
+    if (tid == 0 && S.bad) atomicOr(status, IHS_DEV_NOTPD);
+}
+
+__global__ void __launch_bounds__(256) k_potrf32(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
+                                                 double* __restrict__ Wd, unsigned* status) {
+    __shared__ CholSmem S;
+    chol_potrf(S, Kmat, k, j0, nb, Wd, status);
 }
 
 // Panel: rows i in [j0+nb, k): L[i][j0:j0+nb] = K[i][j0:j0+nb] W^T with
@@ -341,70 +396,6 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, unsigned* statu
     }
     __syncthreads();
     return gs_ok != 0;
-}
-
-struct CholSmem {
-    double a[CB][CB + 1];
-    double w[CB][CB + 1];
-    double dinv[CB];
-    int bad;
-};
-
-__device__ void chol_potrf(CholSmem& S, double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
-                           double* __restrict__ Wd, unsigned* status) {
-    const int tid = threadIdx.x;
-    if (tid == 0) S.bad = 0;
-    for (int e = tid; e < CB * CB; e += 256) {
-        const int r = e / CB, c = e % CB;
-        S.a[r][c] = (r < nb && c < nb && c <= r) ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : 0.0;
-        S.w[r][c] = (r == c) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    const int tr = tid >> 3, tc = tid & 7;
-    for (int j = 0; j < nb; ++j) {
-        if (tid == 0) {
-            double p = S.a[j][j];
-            if (!(p > 0.0) || !isfinite(p)) {
-                S.bad = 1;
-                p = 1.0;
-            }
-            const double ri = rsqrt(p);
-            S.a[j][j] = p * ri;
-            S.dinv[j] = ri;
-        }
-        if (j > 0 && tid >= j && tid < nb) S.a[tid][j - 1] *= S.dinv[j - 1];
-        __syncthreads();
-        const double ip = S.dinv[j];
-        const double ip2 = ip * ip;
-        if (tr > j && tr < nb) {
-            const double arj = S.a[tr][j] * ip2;
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int c = tc + 8 * h;
-                if (c > j && c <= tr) S.a[tr][c] = fma(-arj, S.a[c][j], S.a[tr][c]);
-            }
-        }
-        __syncthreads();
-    }
-    for (int l = 0; l < nb; ++l) {
-        if (tid <= l) S.w[l][tid] *= S.dinv[l];
-        __syncthreads();
-        if (tr > l && tr < nb) {
-            const double arl = S.a[tr][l];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int c = tc + 8 * h;
-                if (c <= l) S.w[tr][c] = fma(-arl, S.w[l][c], S.w[tr][c]);
-            }
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < CB * CB; e += 256) {
-        const int r = e / CB, c = e % CB;
-        if (r < nb && c < nb && c <= r) Kmat[(j0 + r) * k + j0 + c] = S.a[r][c];
-        Wd[e] = (r < nb && c < nb && c <= r) ? S.w[r][c] : 0.0;
-    }
-    if (tid == 0 && S.bad) atomicOr(status, IHS_DEV_NOTPD);
 }
 
 __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Kmat, int64_t k,
