@@ -368,23 +368,29 @@ __global__ void __launch_bounds__(256) k_syrk_rest(double* __restrict__ Kmat, in
 // barrier.  Every barrier wait is bounded; a wait that gives up sets
 // IHS_DEV_TIMEOUT and the CTAs leave.
 
-// Grid barrier over gridDim.x CTAs: bar[0] arrivals, bar[1] generation.
-__device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, unsigned* status) {
+// Grid barrier over gridDim.x CTAs on a monotonic arrival counter (zeroed
+// before the launch): barrier number t (1, 2, ...) is passed when the counter
+// reaches t * gridDim.x.  Arrival is a release reduction after the CTA's
+// writes, the wait an acquire load; a wait that exceeds one second sets
+// IHS_DEV_TIMEOUT and returns false.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* cnt, unsigned& nbar, unsigned* status) {
     __shared__ int gs_ok;
     __syncthreads();
+    ++nbar;
     if (threadIdx.x == 0) {
         gs_ok = 1;
-        volatile unsigned* vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        const unsigned target = nbar * gridDim.x;
+        __threadfence();   // the whole CTA's writes (ordered by the barrier above) before the arrival
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(cnt) : "memory");
+        if (ld_acquire_gpu(cnt) < target) {
             const uint64_t t0 = global_timer_ns();
-            while (*vgen == gen) {
+            while (ld_acquire_gpu(cnt) < target) {
                 if (global_timer_ns() - t0 > 1000000000ull) {
                     atomicOr(status, IHS_DEV_TIMEOUT);
                     gs_ok = 0;
@@ -392,7 +398,6 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, unsigned* statu
                 }
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return gs_ok != 0;
@@ -407,6 +412,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
     const int tid = threadIdx.x;
     const int G = gridDim.x, cta = blockIdx.x;
     const int64_t T = ceil_div64(k, CB);
+    unsigned nbar = 0;   // grid barriers passed
     for (int64_t jb = 0; jb < T; ++jb) {
         const int64_t j0 = jb * CB;
         const int nb = (int)min((int64_t)CB, k - j0);
@@ -418,7 +424,13 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
             const int64_t Tr = ceil_div64(k - j1, CB);
             const int64_t ntile = Tr * (Tr + 1) / 2;
             const int workers = G > 1 ? G - 1 : 1, me = G > 1 ? cta - 1 : 0;
-            for (int64_t t = me; t < ntile; t += workers) {
+            // tiles of column blocks >= 1 of the trailing region: Tr (Tr - 1) / 2;
+            // when they are fewer than two per worker, split each into two
+            // 16-row halves so that the short last steps spread wider
+            const int H = (Tr * (Tr - 1) / 2 < 2 * (int64_t)workers) ? 2 : 1;
+            for (int64_t it = me; it < ntile * H; it += workers) {
+                const int64_t t = it / H;
+                const int hsel = (int)(it % H);
                 int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
                 while (I * (I + 1) / 2 > t) --I;
                 while ((I + 1) * (I + 2) / 2 <= t) ++I;
@@ -433,26 +445,45 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 }
                 __syncthreads();
                 const int tx = tid % 16, ty = tid / 16;
-                double acc[2][2] = {};
+                if (H == 1) {
+                    double acc[2][2] = {};
 #pragma unroll 8
-                for (int q = 0; q < CB; ++q) {
-                    const double a0 = pa[ty][q], a1 = pa[ty + 16][q];
-                    const double b0 = pb[tx][q], b1 = pb[tx + 16][q];
-                    acc[0][0] = fma(a0, b0, acc[0][0]);
-                    acc[0][1] = fma(a0, b1, acc[0][1]);
-                    acc[1][0] = fma(a1, b0, acc[1][0]);
-                    acc[1][1] = fma(a1, b1, acc[1][1]);
-                }
+                    for (int q = 0; q < CB; ++q) {
+                        const double a0 = pa[ty][q], a1 = pa[ty + 16][q];
+                        const double b0 = pb[tx][q], b1 = pb[tx + 16][q];
+                        acc[0][0] = fma(a0, b0, acc[0][0]);
+                        acc[0][1] = fma(a0, b1, acc[0][1]);
+                        acc[1][0] = fma(a1, b0, acc[1][0]);
+                        acc[1][1] = fma(a1, b1, acc[1][1]);
+                    }
 #pragma unroll
-                for (int a = 0; a < 2; ++a)
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) {
+                            const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
+                            if (r < k && c <= r) Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - acc[a][b];
+                        }
+                } else {
+                    // rows ty + 16 hsel only; two chains per output (even / odd q)
+                    double acc[2][2] = {};
+                    const int ra = ty + 16 * hsel;
+#pragma unroll 8
+                    for (int q = 0; q < CB; q += 2) {
+                        const double a0 = pa[ra][q], a1 = pa[ra][q + 1];
+                        acc[0][0] = fma(a0, pb[tx][q], acc[0][0]);
+                        acc[0][1] = fma(a0, pb[tx + 16][q], acc[0][1]);
+                        acc[1][0] = fma(a1, pb[tx][q + 1], acc[1][0]);
+                        acc[1][1] = fma(a1, pb[tx + 16][q + 1], acc[1][1]);
+                    }
 #pragma unroll
                     for (int b = 0; b < 2; ++b) {
-                        const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
-                        if (r < k && c <= r) Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - acc[a][b];
+                        const int64_t r = j1 + I * CB + ra, c = j1 + J * CB + tx + 16 * b;
+                        if (r < k && c <= r) Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - (acc[0][b] + acc[1][b]);
                     }
+                }
             }
         }
-        if (!grid_sync_bounded(bar, status)) return;
+        if (!grid_sync_bounded(bar, nbar, status)) return;
         const int64_t rest = k - j0 - nb;
         if (rest <= 0) break;
         // ---- phase N: panel jb, 8 rows per work item
@@ -469,13 +500,14 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 }
                 __syncthreads();
                 const int tx = tid % CB, ty = tid / CB;
-                double acc = 0.0;
-                for (int q = 0; q < nb; ++q) acc = fma(pa[ty][q], pb[q][tx], acc);
+                double acc[4] = {0.0, 0.0, 0.0, 0.0};   // four chains: FP64 latency, not throughput, bounds this
+#pragma unroll
+                for (int q = 0; q < CB; ++q) acc[q & 3] = fma(pa[ty][q], pb[q][tx], acc[q & 3]);
                 const int64_t r = r0 + ty;
-                if (r < k && tx < nb) Kmat[r * k + j0 + tx] = acc;
+                if (r < k && tx < nb) Kmat[r * k + j0 + tx] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
             }
         }
-        if (!grid_sync_bounded(bar, status)) return;
+        if (!grid_sync_bounded(bar, nbar, status)) return;
         // ---- phase S: column block jb+1 updated by panel jb
         {
             const int64_t j1 = j0 + nb;
@@ -494,13 +526,15 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 }
                 __syncthreads();
                 const int tx = tid % CB, ty = tid / CB;
-                double acc = 0.0;
-                for (int q = 0; q < nb; ++q) acc = fma(pa[ty][q], pb[tx][q], acc);
+                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+                for (int q = 0; q < CB; ++q) acc[q & 3] = fma(pa[ty][q], pb[tx][q], acc[q & 3]);
                 const int64_t r = r0 + ty, c = j1 + tx;
-                if (r < k && tx < ncol && c <= r) Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - acc;
+                if (r < k && tx < ncol && c <= r)
+                    Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - ((acc[0] + acc[1]) + (acc[2] + acc[3]));
             }
         }
-        if (!grid_sync_bounded(bar, status)) return;
+        if (!grid_sync_bounded(bar, nbar, status)) return;
     }
 }
 
@@ -656,12 +690,33 @@ __global__ void k_rowdot(const float* __restrict__ M, int64_t rows, int64_t cols
     if (i >= rows) return;
     const int64_t l0 = tri == 2 ? i : 0, l1 = tri == 1 ? i + 1 : cols;
     const float* row = M + i * ld;
-    Acc2 acc{0.f, 0.f};
+    // four independent accumulators per lane (loads of four strides in flight)
+    Acc2 acc{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+    int64_t l = l0 + lane;
     if (xf) {
-        for (int64_t l = l0 + lane; l < l1; l += 32) acc_mul(acc, row[l], make_float2(xf[l], 0.f));
+        for (; l + 96 < l1; l += 128) {
+            const float m0 = row[l], m1 = row[l + 32], m2 = row[l + 64], m3 = row[l + 96];
+            const float x0 = xf[l], x1 = xf[l + 32], x2 = xf[l + 64], x3 = xf[l + 96];
+            acc_mul(acc, m0, make_float2(x0, 0.f));
+            acc_mul(a1, m1, make_float2(x1, 0.f));
+            acc_mul(a2, m2, make_float2(x2, 0.f));
+            acc_mul(a3, m3, make_float2(x3, 0.f));
+        }
+        for (; l < l1; l += 32) acc_mul(acc, row[l], make_float2(xf[l], 0.f));
     } else {
-        for (int64_t l = l0 + lane; l < l1; l += 32) acc_mul(acc, row[l], x[l]);
+        for (; l + 96 < l1; l += 128) {
+            const float m0 = row[l], m1 = row[l + 32], m2 = row[l + 64], m3 = row[l + 96];
+            const float2 x0 = x[l], x1 = x[l + 32], x2 = x[l + 64], x3 = x[l + 96];
+            acc_mul(acc, m0, x0);
+            acc_mul(a1, m1, x1);
+            acc_mul(a2, m2, x2);
+            acc_mul(a3, m3, x3);
+        }
+        for (; l < l1; l += 32) acc_mul(acc, row[l], x[l]);
     }
+    acc.add_pair(a1.hi, a1.lo);
+    a2.add_pair(a3.hi, a3.lo);
+    acc.add_pair(a2.hi, a2.lo);
     acc = warp_sum_acc2(acc);
     if (lane == 0) {
         float2 r = df_norm(acc.hi, acc.lo);
@@ -678,8 +733,15 @@ __global__ void k_coldot_part(const float* __restrict__ M, int64_t rows, int64_t
     const int64_t j0 = (int64_t)blockIdx.y * rows_per_chunk;
     const int64_t j1 = rows < j0 + rows_per_chunk ? rows : j0 + rows_per_chunk;
     if (c >= cols) return;
-    Acc2 acc{0.f, 0.f};
-    for (int64_t j = j0; j < j1; ++j) acc_mul(acc, M[j * cols + c], x[j]);
+    Acc2 acc{0.f, 0.f}, a1{0.f, 0.f};
+    int64_t j = j0;
+    for (; j + 1 < j1; j += 2) {
+        const float m0 = M[j * cols + c], m1 = M[(j + 1) * cols + c];
+        acc_mul(acc, m0, x[j]);
+        acc_mul(a1, m1, x[j + 1]);
+    }
+    if (j < j1) acc_mul(acc, M[j * cols + c], x[j]);
+    acc.add_pair(a1.hi, a1.lo);
     part[blockIdx.y * cols + c] = df_norm(acc.hi, acc.lo);
 }
 
@@ -799,7 +861,7 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
         G = std::min(G, per_sm * ctx->sm_count);
         if (G >= 1) {
             unsigned* bar = ctx->d_status + 16;
-            IHS_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+            IHS_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
             int64_t kk = k;
             void* args[] = {&Kmat, &kk, &Wall, &bar, &ctx->d_status};
             IHS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_chol_persistent, dim3((unsigned)G), dim3(256),
