@@ -52,8 +52,8 @@ def profiled_traffic():
         return None
     fields = {}
     for line in open(GRAD_PROFILE):
-        if ":" in line:
-            k, v = line.split(":", 1)
+        if ": " in line:
+            k, v = line.split(": ", 1)
             fields[k.strip()] = v.strip()
     if fields.get("grad.cu sha256[:16]") != grad_source_hash():
         return None
