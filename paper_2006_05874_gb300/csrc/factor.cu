@@ -403,12 +403,39 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned* cnt, unsigned& nbar,
     return gs_ok != 0;
 }
 
+// acc += (a.x + a.y)(b.x + b.y) for double-float operands (pairs of binary32
+// whose sum carries about 48 bits): the high product exactly (TwoProduct), the
+// cross terms rounded once, a.y b.y dropped (2^-48 relative), the sum
+// compensated (TwoSum).  Thirteen FP32 operations in place of one FP64 FMA,
+// whose rate on this part is 1/64 of FP32.
+__device__ __forceinline__ void df_fma_acc(Acc2& acc, float2 a, float2 b) {
+    float p, e, s, es;
+    two_prod(a.x, b.x, p, e);
+    const float cross = __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x));
+    two_sum(acc.hi, p, s, es);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(__fadd_rn(e, cross), es));
+}
+
+__device__ __forceinline__ float2 df_split(double v) {
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
 __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Kmat, int64_t k,
                                                          double* __restrict__ Wall, unsigned* bar,
                                                          unsigned* status) {
     __shared__ CholSmem S;
-    __shared__ double pa[CB][CB + 1];
-    __shared__ double pb[CB][CB + 1];
+    // panel operands: FP64 for the panel and column phases, double-float pairs
+    // for the trailing tiles
+    __shared__ union {
+        double d[2][CB][CB + 1];
+        float2 f[2][CB][CB + 1];
+    } P;
+    double (*pa)[CB + 1] = P.d[0];
+    double (*pb)[CB + 1] = P.d[1];
+    float2 (*fa)[CB + 1] = P.f[0];
+    float2 (*fb)[CB + 1] = P.f[1];
     const int tid = threadIdx.x;
     const int G = gridDim.x, cta = blockIdx.x;
     const int64_t T = ceil_div64(k, CB);
@@ -440,45 +467,48 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 for (int e = tid; e < CB * CB; e += 256) {
                     const int rr = e / CB, q = e % CB;
                     const int64_t ra = j1 + I * CB + rr, rb = j1 + J * CB + rr;
-                    pa[rr][q] = ra < k ? __ldcg(Kmat + ra * k + jp0 + q) : 0.0;
-                    pb[rr][q] = rb < k ? __ldcg(Kmat + rb * k + jp0 + q) : 0.0;
+                    fa[rr][q] = df_split(ra < k ? __ldcg(Kmat + ra * k + jp0 + q) : 0.0);
+                    fb[rr][q] = df_split(rb < k ? __ldcg(Kmat + rb * k + jp0 + q) : 0.0);
                 }
                 __syncthreads();
+                // the rank-32 product in double-float on the FP32 pipes, the
+                // subtraction from K in FP64
                 const int tx = tid % 16, ty = tid / 16;
                 if (H == 1) {
-                    double acc[2][2] = {};
-#pragma unroll 8
+                    Acc2 acc[2][2] = {};
+#pragma unroll 4
                     for (int q = 0; q < CB; ++q) {
-                        const double a0 = pa[ty][q], a1 = pa[ty + 16][q];
-                        const double b0 = pb[tx][q], b1 = pb[tx + 16][q];
-                        acc[0][0] = fma(a0, b0, acc[0][0]);
-                        acc[0][1] = fma(a0, b1, acc[0][1]);
-                        acc[1][0] = fma(a1, b0, acc[1][0]);
-                        acc[1][1] = fma(a1, b1, acc[1][1]);
+                        const float2 a0 = fa[ty][q], a1 = fa[ty + 16][q];
+                        const float2 b0 = fb[tx][q], b1 = fb[tx + 16][q];
+                        df_fma_acc(acc[0][0], a0, b0);
+                        df_fma_acc(acc[0][1], a0, b1);
+                        df_fma_acc(acc[1][0], a1, b0);
+                        df_fma_acc(acc[1][1], a1, b1);
                     }
 #pragma unroll
                     for (int a = 0; a < 2; ++a)
 #pragma unroll
                         for (int b = 0; b < 2; ++b) {
                             const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
-                            if (r < k && c <= r) Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - acc[a][b];
+                            if (r < k && c <= r)
+                                Kmat[r * k + c] = __ldcg(Kmat + r * k + c) -
+                                                  ((double)acc[a][b].hi + (double)acc[a][b].lo);
                         }
                 } else {
-                    // rows ty + 16 hsel only; two chains per output (even / odd q)
-                    double acc[2][2] = {};
+                    // rows ty + 16 hsel only
+                    Acc2 acc[2] = {};
                     const int ra = ty + 16 * hsel;
-#pragma unroll 8
-                    for (int q = 0; q < CB; q += 2) {
-                        const double a0 = pa[ra][q], a1 = pa[ra][q + 1];
-                        acc[0][0] = fma(a0, pb[tx][q], acc[0][0]);
-                        acc[0][1] = fma(a0, pb[tx + 16][q], acc[0][1]);
-                        acc[1][0] = fma(a1, pb[tx][q + 1], acc[1][0]);
-                        acc[1][1] = fma(a1, pb[tx + 16][q + 1], acc[1][1]);
+#pragma unroll 4
+                    for (int q = 0; q < CB; ++q) {
+                        const float2 a0 = fa[ra][q];
+                        df_fma_acc(acc[0], a0, fb[tx][q]);
+                        df_fma_acc(acc[1], a0, fb[tx + 16][q]);
                     }
 #pragma unroll
                     for (int b = 0; b < 2; ++b) {
                         const int64_t r = j1 + I * CB + ra, c = j1 + J * CB + tx + 16 * b;
-                        if (r < k && c <= r) Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - (acc[0][b] + acc[1][b]);
+                        if (r < k && c <= r)
+                            Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - ((double)acc[b].hi + (double)acc[b].lo);
                     }
                 }
             }
