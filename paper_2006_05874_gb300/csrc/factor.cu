@@ -144,8 +144,9 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ 
 // on the critical path, and its cost grows as CB^3 per block step.
 constexpr int CB = 32;
 
-// Diagonal block [j0, j0+nb) of the FP64 Cholesky, in place, and its inverse
-// W = L_jj^{-1} (CB x CB, lower, at Wd) for the panel; one CTA of 256 threads.
+// Diagonal block [j0, j0+nb) of the FP64 Cholesky, in place, and (WANT_W) its
+// inverse W = L_jj^{-1} (CB x CB, lower, at Wd) for the panel; one CTA of 256
+// threads.
 // The pivots form a dependent chain of CB reciprocal square roots (a long
 // FP64 latency each), so thread 0 runs that chain alone: at step j it applies
 // column j to the next pivot itself, p_{j+1} = a_{j+1,j+1} - (a_{j+1,j} / sqrt(p_j))^2,
@@ -153,8 +154,9 @@ constexpr int CB = 32;
 // of the trailing triangle (entries packed by descending column, so that the
 // warps with no entries left skip the step).  Columns stay unscaled (a_rc with
 // the pivot p_c on the diagonal) until one final pass forms L_rc = a_rc / sqrt(p_c).
-// W follows by forward substitution row by row, one trailing entry per
-// thread per row.  Rows and columns >= nb are padded with the identity.
+// With WANT_W, W = L^{-1} follows by forward substitution row by row, one
+// trailing entry per thread per row; without it the reciprocal diagonal
+// 1 / L_cc goes to Wd[0..CB) for a panel formed by substitution.  Rows and columns >= nb are padded with the identity.
 // Non-positive or non-finite pivots set IHS_DEV_NOTPD (the pivot is replaced
 // by 1 so that the kernel finishes).
 struct CholSmem {
@@ -164,6 +166,7 @@ struct CholSmem {
     int bad;
 };
 
+template <bool WANT_W>
 __device__ void chol_potrf(CholSmem& S, double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
                            double* __restrict__ Wd, unsigned* status) {
     static_assert(CB == 32, "the packed entry mapping assumes CB = 32 and 256 threads");
@@ -241,32 +244,37 @@ __device__ void chol_potrf(CholSmem& S, double* __restrict__ Kmat, int64_t k, in
         const int r = e / CB, c = e % CB;
         if (c <= r) S.a[r][c] *= S.dinv[c];
     }
-    if (tid == 0) S.w[0][0] = S.dinv[0];
-    __syncthreads();
-    // W = L^{-1}: after step l, row l + 1 is final
-    for (int l = 0; l < CB - 1; ++l) {
-        const int width = l + 1;
-        if (tid < (CB - 1 - l) * width) {
-            const int r = l + 1 + tid / width, c = tid % width;
-            double v = fma(-S.a[r][l], S.w[l][c], S.w[r][c]);
-            if (r == l + 1) v *= S.dinv[l + 1];
-            S.w[r][c] = v;
+    if (WANT_W) {
+        if (tid == 0) S.w[0][0] = S.dinv[0];
+        __syncthreads();
+        // W = L^{-1}: after step l, row l + 1 is final
+        for (int l = 0; l < CB - 1; ++l) {
+            const int width = l + 1;
+            if (tid < (CB - 1 - l) * width) {
+                const int r = l + 1 + tid / width, c = tid % width;
+                double v = fma(-S.a[r][l], S.w[l][c], S.w[r][c]);
+                if (r == l + 1) v *= S.dinv[l + 1];
+                S.w[r][c] = v;
+            }
+            if (tid == 0) S.w[l + 1][l + 1] = S.dinv[l + 1];
+            __syncthreads();
         }
-        if (tid == 0) S.w[l + 1][l + 1] = S.dinv[l + 1];
+    } else {
         __syncthreads();
     }
     for (int e = tid; e < CB * CB; e += 256) {
         const int r = e / CB, c = e % CB;
         if (r < nb && c < nb && c <= r) Kmat[(j0 + r) * k + j0 + c] = S.a[r][c];
-        Wd[e] = (r < nb && c < nb && c <= r) ? S.w[r][c] : 0.0;
+        if (WANT_W) Wd[e] = (r < nb && c < nb && c <= r) ? S.w[r][c] : 0.0;
     }
+    if (!WANT_W && tid < CB) Wd[tid] = tid < nb ? S.dinv[tid] : 0.0;   // 1 / L_cc
     if (tid == 0 && S.bad) atomicOr(status, IHS_DEV_NOTPD);
 }
 
 __global__ void __launch_bounds__(256) k_potrf32(double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
                                                  double* __restrict__ Wd, unsigned* status) {
     __shared__ CholSmem S;
-    chol_potrf(S, Kmat, k, j0, nb, Wd, status);
+    chol_potrf<true>(S, Kmat, k, j0, nb, Wd, status);
 }
 
 // Panel: rows i in [j0+nb, k): L[i][j0:j0+nb] = K[i][j0:j0+nb] W^T with
@@ -426,16 +434,9 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                                                          double* __restrict__ Wall, unsigned* bar,
                                                          unsigned* status) {
     __shared__ CholSmem S;
-    // panel operands: FP64 for the panel and column phases, double-float pairs
-    // for the trailing tiles
-    __shared__ union {
-        double d[2][CB][CB + 1];
-        float2 f[2][CB][CB + 1];
-    } P;
-    double (*pa)[CB + 1] = P.d[0];
-    double (*pb)[CB + 1] = P.d[1];
-    float2 (*fa)[CB + 1] = P.f[0];
-    float2 (*fb)[CB + 1] = P.f[1];
+    // operands of the panel, column and trailing products as double-float pairs
+    __shared__ float2 fa[CB][CB + 1];
+    __shared__ float2 fb[CB][CB + 1];
     const int tid = threadIdx.x;
     const int G = gridDim.x, cta = blockIdx.x;
     const int64_t T = ceil_div64(k, CB);
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
         const int64_t j0 = jb * CB;
         const int nb = (int)min((int64_t)CB, k - j0);
         // ---- phase P: diagonal block jb | rest of the update by panel jb-1
-        if (cta == 0) chol_potrf(S, Kmat, k, j0, nb, Wall + jb * CB * CB, status);
+        if (cta == 0) chol_potrf<false>(S, Kmat, k, j0, nb, Wall + jb * CB * CB, status);
         if (jb > 0 && (cta > 0 || G == 1)) {
             const int64_t jp0 = j0 - CB;          // panel jb-1 columns [jp0, jp0 + CB)
             const int64_t j1 = j0;                 // trailing region starts at block jb
@@ -455,26 +456,66 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
             // when they are fewer than two per worker, split each into two
             // 16-row halves so that the short last steps spread wider
             const int H = (Tr * (Tr - 1) / 2 < 2 * (int64_t)workers) ? 2 : 1;
-            for (int64_t it = me; it < ntile * H; it += workers) {
+            const int64_t total = ntile * H;
+            auto tile_of = [&](int64_t it, int64_t& I, int64_t& J) {
                 const int64_t t = it / H;
-                const int hsel = (int)(it % H);
-                int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+                I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
                 while (I * (I + 1) / 2 > t) --I;
                 while ((I + 1) * (I + 2) / 2 <= t) ++I;
-                const int64_t J = t - I * (I + 1) / 2;
-                if (J < 1) continue;   // column block jb: done in phase S of step jb-1
-                __syncthreads();
-                for (int e = tid; e < CB * CB; e += 256) {
+                J = t - I * (I + 1) / 2;
+            };
+            // column block jb (J = 0) was done in phase S of step jb-1
+            auto next_item = [&](int64_t it) -> int64_t {
+                for (; it < total; it += workers) {
+                    int64_t I, J;
+                    tile_of(it, I, J);
+                    if (J >= 1) return it;
+                }
+                return total;
+            };
+            // operands of the next item are loaded into registers while the
+            // current one computes
+            double va[4], vb[4];
+            auto fetch = [&](int64_t it) {
+                int64_t I, J;
+                tile_of(it, I, J);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int e = tid + 256 * i;
                     const int rr = e / CB, q = e % CB;
                     const int64_t ra = j1 + I * CB + rr, rb = j1 + J * CB + rr;
-                    fa[rr][q] = df_split(ra < k ? __ldcg(Kmat + ra * k + jp0 + q) : 0.0);
-                    fb[rr][q] = df_split(rb < k ? __ldcg(Kmat + rb * k + jp0 + q) : 0.0);
+                    va[i] = ra < k ? __ldcg(Kmat + ra * k + jp0 + q) : 0.0;
+                    vb[i] = rb < k ? __ldcg(Kmat + rb * k + jp0 + q) : 0.0;
+                }
+            };
+            int64_t it = next_item(me);
+            if (it < total) fetch(it);
+            const int tx = tid % 16, ty = tid / 16;
+            while (it < total) {
+                int64_t I, J;
+                tile_of(it, I, J);
+                const int hsel = (int)(it % H);
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int e = tid + 256 * i;
+                    fa[e / CB][e % CB] = df_split(va[i]);
+                    fb[e / CB][e % CB] = df_split(vb[i]);
                 }
                 __syncthreads();
+                const int64_t nx = next_item(it + workers);
+                if (nx < total) fetch(nx);
                 // the rank-32 product in double-float on the FP32 pipes, the
                 // subtraction from K in FP64
-                const int tx = tid % 16, ty = tid / 16;
                 if (H == 1) {
+                    double kold[2][2];
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) {
+                            const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
+                            kold[a][b] = (r < k && c <= r) ? __ldcg(Kmat + r * k + c) : 0.0;
+                        }
                     Acc2 acc[2][2] = {};
 #pragma unroll 4
                     for (int q = 0; q < CB; ++q) {
@@ -491,13 +532,18 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                         for (int b = 0; b < 2; ++b) {
                             const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
                             if (r < k && c <= r)
-                                Kmat[r * k + c] = __ldcg(Kmat + r * k + c) -
-                                                  ((double)acc[a][b].hi + (double)acc[a][b].lo);
+                                Kmat[r * k + c] = kold[a][b] - ((double)acc[a][b].hi + (double)acc[a][b].lo);
                         }
                 } else {
                     // rows ty + 16 hsel only
-                    Acc2 acc[2] = {};
                     const int ra = ty + 16 * hsel;
+                    double kold[2];
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int64_t r = j1 + I * CB + ra, c = j1 + J * CB + tx + 16 * b;
+                        kold[b] = (r < k && c <= r) ? __ldcg(Kmat + r * k + c) : 0.0;
+                    }
+                    Acc2 acc[2] = {};
 #pragma unroll 4
                     for (int q = 0; q < CB; ++q) {
                         const float2 a0 = fa[ra][q];
@@ -507,34 +553,42 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
 #pragma unroll
                     for (int b = 0; b < 2; ++b) {
                         const int64_t r = j1 + I * CB + ra, c = j1 + J * CB + tx + 16 * b;
-                        if (r < k && c <= r)
-                            Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - ((double)acc[b].hi + (double)acc[b].lo);
+                        if (r < k && c <= r) Kmat[r * k + c] = kold[b] - ((double)acc[b].hi + (double)acc[b].lo);
                     }
                 }
+                it = nx;
             }
         }
         if (!grid_sync_bounded(bar, nbar, status)) return;
         const int64_t rest = k - j0 - nb;
         if (rest <= 0) break;
-        // ---- phase N: panel jb, 8 rows per work item
+        // ---- phase N: panel jb = K L_jj^{-T} by forward substitution, 8 rows per
+        // work item: warp w solves row r0 + w, lane c holds column c
         {
-            const double* Wd = Wall + jb * CB * CB;
+            const double* dinv = Wall + jb * CB * CB;   // 1 / L_cc
+            double (*Ls)[CB + 1] = reinterpret_cast<double (*)[CB + 1]>(&fa[0][0]);
+            double* dl = reinterpret_cast<double*>(&fb[0][0]);
             const int64_t items = ceil_div64(rest, 8);
+            const int lane = tid & 31, wq = tid >> 5;
             for (int64_t it = cta; it < items; it += G) {
                 const int64_t r0 = j0 + nb + it * 8;
                 __syncthreads();
-                for (int e = tid; e < CB * CB; e += 256) pb[e % CB][e / CB] = __ldcg(Wd + e);   // pb[c][r] = W[r][c]
-                {
-                    const int r = tid / CB, c = tid % CB;
-                    pa[r][c] = (r0 + r < k && c < nb) ? __ldcg(Kmat + (r0 + r) * k + j0 + c) : 0.0;
+                for (int e = tid; e < CB * CB; e += 256) {
+                    const int r = e / CB, c = e % CB;
+                    Ls[r][c] = (c <= r && r < nb) ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : 0.0;
                 }
+                if (tid < CB) dl[tid] = __ldcg(dinv + tid);
                 __syncthreads();
-                const int tx = tid % CB, ty = tid / CB;
-                double acc[4] = {0.0, 0.0, 0.0, 0.0};   // four chains: FP64 latency, not throughput, bounds this
+                const int64_t r = r0 + wq;
+                double kv = (r < k && lane < nb) ? __ldcg(Kmat + r * k + j0 + lane) : 0.0;
+                double x = 0.0;
 #pragma unroll
-                for (int q = 0; q < CB; ++q) acc[q & 3] = fma(pa[ty][q], pb[q][tx], acc[q & 3]);
-                const int64_t r = r0 + ty;
-                if (r < k && tx < nb) Kmat[r * k + j0 + tx] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+                for (int c = 0; c < CB; ++c) {
+                    const double xc = __shfl_sync(0xffffffffu, kv, c) * dl[c];
+                    if (lane == c) x = xc;
+                    else if (lane > c) kv = fma(-xc, Ls[lane][c], kv);
+                }
+                if (r < k && lane < nb) Kmat[r * k + j0 + lane] = x;
             }
         }
         if (!grid_sync_bounded(bar, nbar, status)) return;
@@ -548,20 +602,24 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 __syncthreads();
                 for (int e = tid; e < CB * CB; e += 256) {
                     const int c = e / CB, q = e % CB;
-                    pb[c][q] = (c < ncol && q < nb) ? __ldcg(Kmat + (j1 + c) * k + j0 + q) : 0.0;
+                    fb[c][q] = df_split((c < ncol && q < nb) ? __ldcg(Kmat + (j1 + c) * k + j0 + q) : 0.0);
                 }
                 {
                     const int r = tid / CB, q = tid % CB;
-                    pa[r][q] = (r0 + r < k && q < nb) ? __ldcg(Kmat + (r0 + r) * k + j0 + q) : 0.0;
+                    fa[r][q] = df_split((r0 + r < k && q < nb) ? __ldcg(Kmat + (r0 + r) * k + j0 + q) : 0.0);
                 }
                 __syncthreads();
                 const int tx = tid % CB, ty = tid / CB;
-                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                Acc2 acc0{0.f, 0.f}, acc1{0.f, 0.f};
 #pragma unroll
-                for (int q = 0; q < CB; ++q) acc[q & 3] = fma(pa[ty][q], pb[tx][q], acc[q & 3]);
+                for (int q = 0; q < CB; q += 2) {
+                    df_fma_acc(acc0, fa[ty][q], fb[tx][q]);
+                    df_fma_acc(acc1, fa[ty][q + 1], fb[tx][q + 1]);
+                }
                 const int64_t r = r0 + ty, c = j1 + tx;
                 if (r < k && tx < ncol && c <= r)
-                    Kmat[r * k + c] = __ldcg(Kmat + r * k + c) - ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+                    Kmat[r * k + c] = __ldcg(Kmat + r * k + c) -
+                                      (((double)acc0.hi + (double)acc0.lo) + ((double)acc1.hi + (double)acc1.lo));
             }
         }
         if (!grid_sync_bounded(bar, nbar, status)) return;
