@@ -377,9 +377,10 @@ struct Acc2x2 {
 
 struct V3Layout {
     size_t pdot, bsh, rsh, bars, total;
-    __host__ __device__ V3Layout(int S, int R, int d) {
+    // np: lane partials per tile (consumer lanes x rows per lane)
+    __host__ __device__ V3Layout(int S, int R, int d, int np) {
         pdot = align16((size_t)S * R * d * sizeof(float));
-        bsh = pdot + (size_t)S * kV3Consumers * 32 * sizeof(Acc2);
+        bsh = pdot + (size_t)S * np * sizeof(Acc2);
         rsh = align16(bsh + (size_t)S * R * sizeof(float));
         bars = align16(rsh + (size_t)S * R * 2 * sizeof(float));
         total = bars + 4 * (size_t)S * sizeof(uint64_t);
@@ -395,17 +396,19 @@ __device__ __forceinline__ f2 lds_f2(uint32_t addr) {
     return a;
 }
 
-template <int NSEG, int CPT, bool FULL>
+template <int NSEG, int CPT, bool FULL, int RPW>
 __global__ void __launch_bounds__(kV3Threads, 1)
 k_grad_v3(const float* __restrict__ A, const float* __restrict__ b, const float* __restrict__ x, int64_t n,
           int d, int64_t ntiles, int S, float2* __restrict__ part, double* __restrict__ part_ax2,
           unsigned* status) {
-    constexpr int R = kV3Consumers / NSEG;   // rows per tile
-    constexpr int XC = 4;                    // float4 chunks per lane per row
-    constexpr int LPR = 32 / R;              // finaliser lanes per row
-    constexpr int NP = kV3Consumers * 32;    // lane partials per tile
+    constexpr int G16 = kV3Consumers / NSEG;   // row groups of NSEG warps
+    constexpr int R = G16 * RPW;               // rows per tile (RPW per row group)
+    constexpr int XC = 4;                      // float4 chunks per lane per row
+    constexpr int LPR = 32 / R;                // finaliser lanes per row
+    constexpr int NP = kV3Consumers * 32 * RPW;   // lane partials per tile
+    static_assert(R <= 32, "one finaliser lane per row at least");
     extern __shared__ __align__(128) unsigned char smem[];
-    const V3Layout lay(S, R, d);
+    const V3Layout lay(S, R, d, NP);
     float* stage_base = reinterpret_cast<float*>(smem);
     Acc2* pdot = reinterpret_cast<Acc2*>(smem + lay.pdot);   // [S][R][NP / R]
     float* bsh = reinterpret_cast<float*>(smem + lay.bsh);   // [S][R]
@@ -561,28 +564,33 @@ k_grad_v3(const float* __restrict__ A, const float* __restrict__ b, const float*
             const int rows = (int)min((int64_t)R, n - row0);
             ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s1], ph1, status));
             if (!ok) break;
-            Acc2x2 pa{zero2, zero2}, pb{zero2, zero2};
-            if (prow < rows) {
-                const uint32_t base = sm0 + (uint32_t)s1 * sbytes + p1_off;
 #pragma unroll
-                for (int k = 0; k < XC; ++k) {
-                    if (cv[k]) {
-                        f2 a01, a23;
-                        lds_f2x2(base + (uint32_t)(k * NSEG * 32 * 16), a01, a23);
-                        pa.add_prod(a01, xa[k], xan[k]);
-                        pb.add_prod(a23, xb[k], xbn[k]);
+            for (int u = 0; u < RPW; ++u) {
+                const int row = prow + G16 * u;
+                Acc2x2 pa{zero2, zero2}, pb{zero2, zero2};
+                if (row < rows) {
+                    const uint32_t base = sm0 + (uint32_t)s1 * sbytes + p1_off + (uint32_t)(u * G16) * row_bytes;
+#pragma unroll
+                    for (int k = 0; k < XC; ++k) {
+                        if (cv[k]) {
+                            f2 a01, a23;
+                            lds_f2x2(base + (uint32_t)(k * NSEG * 32 * 16), a01, a23);
+                            pa.add_prod(a01, xa[k], xan[k]);
+                            pb.add_prod(a23, xb[k], xbn[k]);
+                        }
                     }
                 }
+                pa.add_pair(pb.hi, pb.lo);
+                float h0, h1, l0, l1;
+                f2_unpack(pa.hi, h0, h1);
+                f2_unpack(pa.lo, l0, l1);
+                Acc2 a0{h0, l0};
+                a0.add_pair(h1, l1);
+                asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(pd0 + (uint32_t)s1 * pd_stage +
+                                                                     (uint32_t)(u * G16 * (NP / R) * sizeof(Acc2))),
+                             "f"(a0.hi), "f"(a0.lo)
+                             : "memory");
             }
-            pa.add_pair(pb.hi, pb.lo);
-            float h0, h1, l0, l1;
-            f2_unpack(pa.hi, h0, h1);
-            f2_unpack(pa.lo, l0, l1);
-            Acc2 a0{h0, l0};
-            a0.add_pair(h1, l1);
-            asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(pd0 + (uint32_t)s1 * pd_stage), "f"(a0.hi),
-                         "f"(a0.lo)
-                         : "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&rready[s1]);
             if (++s1 == S) {
@@ -789,15 +797,18 @@ int launch_fast(ihs_ctx* ctx, const float* A, const float* b, const float* x, in
 template <int NSEG, int CPT, bool FULL>
 int launch_v3(ihs_ctx* ctx, const float* A, const float* b, const float* x, int64_t n, int d, float2* part,
               double* part_ax2, int* G_out) {
-    constexpr int R = kV3Consumers / NSEG;
+    // two rows per row group: a tile is 64 KB at d = 1024 ... 8192, so the
+    // per-tile hand-offs are spread over twice the elements
+    constexpr int RPW = 2;
+    constexpr int R = RPW * kV3Consumers / NSEG;
     const size_t stage_bytes = (size_t)R * d * sizeof(float);
     int S = (int)std::min<size_t>(8, (192 * 1024) / stage_bytes);
     if (S < 3) return IHS_EINVAL;
-    const size_t smem = V3Layout(S, R, d).total;
+    const size_t smem = V3Layout(S, R, d, kV3Consumers * 32 * RPW).total;
     const int64_t ntiles = ceil_div64(n, R);
     int64_t G = ctx->sm_count;
     if (G > ntiles) G = ntiles;
-    auto kern = k_grad_v3<NSEG, CPT, FULL>;
+    auto kern = k_grad_v3<NSEG, CPT, FULL, RPW>;
     IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
     kern<<<(unsigned)G, kV3Threads, smem, ctx->stream>>>(A, b, x, n, d, ntiles, S, part, part_ax2, ctx->d_status);
     IHS_LAUNCH_CHECK();
