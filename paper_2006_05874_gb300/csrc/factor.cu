@@ -440,14 +440,17 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
     const int tid = threadIdx.x;
     const int G = gridDim.x, cta = blockIdx.x;
     const int64_t T = ceil_div64(k, CB);
+    // Wall: 1 / L_cc of every block step (T x CB), then the current panel as
+    // double-float pairs, row r at Pdf + r * CB (written once per element in
+    // phase N, read by phase S and by the next step's trailing tiles)
+    float2* Pdf = reinterpret_cast<float2*>(Wall + T * CB);
     unsigned nbar = 0;   // grid barriers passed
     for (int64_t jb = 0; jb < T; ++jb) {
         const int64_t j0 = jb * CB;
         const int nb = (int)min((int64_t)CB, k - j0);
         // ---- phase P: diagonal block jb | rest of the update by panel jb-1
-        if (cta == 0) chol_potrf<false>(S, Kmat, k, j0, nb, Wall + jb * CB * CB, status);
+        if (cta == 0) chol_potrf<false>(S, Kmat, k, j0, nb, Wall + jb * CB, status);
         if (jb > 0 && (cta > 0 || G == 1)) {
-            const int64_t jp0 = j0 - CB;          // panel jb-1 columns [jp0, jp0 + CB)
             const int64_t j1 = j0;                 // trailing region starts at block jb
             const int64_t Tr = ceil_div64(k - j1, CB);
             const int64_t ntile = Tr * (Tr + 1) / 2;
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
             };
             // operands of the next item are loaded into registers while the
             // current one computes
-            double va[4], vb[4];
+            float2 va[4], vb[4];
             auto fetch = [&](int64_t it) {
                 int64_t I, J;
                 tile_of(it, I, J);
@@ -484,8 +487,8 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                     const int e = tid + 256 * i;
                     const int rr = e / CB, q = e % CB;
                     const int64_t ra = j1 + I * CB + rr, rb = j1 + J * CB + rr;
-                    va[i] = ra < k ? __ldcg(Kmat + ra * k + jp0 + q) : 0.0;
-                    vb[i] = rb < k ? __ldcg(Kmat + rb * k + jp0 + q) : 0.0;
+                    va[i] = ra < k ? __ldcg(Pdf + ra * CB + q) : make_float2(0.f, 0.f);
+                    vb[i] = rb < k ? __ldcg(Pdf + rb * CB + q) : make_float2(0.f, 0.f);
                 }
             };
             int64_t it = next_item(me);
@@ -499,8 +502,8 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int e = tid + 256 * i;
-                    fa[e / CB][e % CB] = df_split(va[i]);
-                    fb[e / CB][e % CB] = df_split(vb[i]);
+                    fa[e / CB][e % CB] = va[i];
+                    fb[e / CB][e % CB] = vb[i];
                 }
                 __syncthreads();
                 const int64_t nx = next_item(it + workers);
@@ -565,7 +568,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
         // ---- phase N: panel jb = K L_jj^{-T} by forward substitution, 8 rows per
         // work item: warp w solves row r0 + w, lane c holds column c
         {
-            const double* dinv = Wall + jb * CB * CB;   // 1 / L_cc
+            const double* dinv = Wall + jb * CB;   // 1 / L_cc
             double (*Ls)[CB + 1] = reinterpret_cast<double (*)[CB + 1]>(&fa[0][0]);
             double* dl = reinterpret_cast<double*>(&fb[0][0]);
             const int64_t items = ceil_div64(rest, 8);
@@ -589,6 +592,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                     else if (lane > c) kv = fma(-xc, Ls[lane][c], kv);
                 }
                 if (r < k && lane < nb) Kmat[r * k + j0 + lane] = x;
+                if (r < k) Pdf[r * CB + lane] = df_split(x);   // 0 for lanes >= nb
             }
         }
         if (!grid_sync_bounded(bar, nbar, status)) return;
@@ -602,11 +606,11 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 __syncthreads();
                 for (int e = tid; e < CB * CB; e += 256) {
                     const int c = e / CB, q = e % CB;
-                    fb[c][q] = df_split((c < ncol && q < nb) ? __ldcg(Kmat + (j1 + c) * k + j0 + q) : 0.0);
+                    fb[c][q] = c < ncol ? __ldcg(Pdf + (j1 + c) * CB + q) : make_float2(0.f, 0.f);
                 }
                 {
                     const int r = tid / CB, q = tid % CB;
-                    fa[r][q] = df_split((r0 + r < k && q < nb) ? __ldcg(Kmat + (r0 + r) * k + j0 + q) : 0.0);
+                    fa[r][q] = r0 + r < k ? __ldcg(Pdf + (r0 + r) * CB + q) : make_float2(0.f, 0.f);
                 }
                 __syncthreads();
                 const int tx = tid % CB, ty = tid / CB;
