@@ -425,9 +425,43 @@ __device__ __forceinline__ void df_fma_acc(Acc2& acc, float2 a, float2 b) {
     acc.lo = __fadd_rn(acc.lo, __fadd_rn(__fadd_rn(e, cross), es));
 }
 
+// v as hi + lo with integer operations (no FP64 instruction: conversions from
+// double run at the FP64 rate): hi keeps the sign, the exponent and the top 23
+// stored mantissa bits (truncated), lo the remaining 29 bits rounded to 24,
+// 48 bits in all.  Magnitudes outside [2^-74, 2^127] take the FP64 conversion.
 __device__ __forceinline__ float2 df_split(double v) {
-    const float hi = __double2float_rn(v);
-    return make_float2(hi, __double2float_rn(v - (double)hi));
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const unsigned h32 = (unsigned)(bits >> 32), l32 = (unsigned)bits;
+    const int e32 = (int)((h32 >> 20) & 0x7FFu) - 1023 + 127;   // binary32 biased exponent of v
+    if (e32 < 53 || e32 > 254) {
+        if (v == 0.0) return make_float2(0.f, 0.f);
+        const float hi = __double2float_rn(v);
+        return make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+    const unsigned sign = h32 & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((unsigned)e32 << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
+    const float scale = __uint_as_float((unsigned)(e32 - 52) << 23);   // 2^(exponent of v - 52)
+    const float lo = __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale);
+    return make_float2(hi, sign ? -lo : lo);
+}
+
+// x y for double-float operands, renormalised: about 2^-47 relative
+__device__ __forceinline__ float2 df_mul2(float2 x, float2 y) {
+    float p, e;
+    two_prod(x.x, y.x, p, e);
+    e = __fmaf_rn(x.x, y.y, __fmaf_rn(x.y, y.x, e));
+    const float s = __fadd_rn(p, e);
+    return make_float2(s, __fsub_rn(e, __fsub_rn(s, p)));
+}
+
+// k - x y for double-float operands
+__device__ __forceinline__ float2 df_fnms(float2 k, float2 x, float2 y) {
+    const float2 q = df_mul2(x, y);
+    float s, e;
+    two_sum(k.x, -q.x, s, e);
+    e = __fadd_rn(e, __fsub_rn(k.y, q.y));
+    const float t = __fadd_rn(s, e);
+    return make_float2(t, __fsub_rn(e, __fsub_rn(t, s)));
 }
 
 __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Kmat, int64_t k,
@@ -569,30 +603,34 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
         // work item: warp w solves row r0 + w, lane c holds column c
         {
             const double* dinv = Wall + jb * CB;   // 1 / L_cc
-            double (*Ls)[CB + 1] = reinterpret_cast<double (*)[CB + 1]>(&fa[0][0]);
-            double* dl = reinterpret_cast<double*>(&fb[0][0]);
             const int64_t items = ceil_div64(rest, 8);
             const int lane = tid & 31, wq = tid >> 5;
+            bool loaded = false;
             for (int64_t it = cta; it < items; it += G) {
                 const int64_t r0 = j0 + nb + it * 8;
-                __syncthreads();
-                for (int e = tid; e < CB * CB; e += 256) {
-                    const int r = e / CB, c = e % CB;
-                    Ls[r][c] = (c <= r && r < nb) ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : 0.0;
+                if (!loaded) {
+                    // L_jj and 1 / L_cc as double-float pairs, once per step
+                    for (int e = tid; e < CB * CB; e += 256) {
+                        const int r = e / CB, c = e % CB;
+                        fa[r][c] = df_split((c <= r && r < nb) ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : 0.0);
+                    }
+                    if (tid < CB) fb[0][tid] = df_split(__ldcg(dinv + tid));
+                    __syncthreads();
+                    loaded = true;
                 }
-                if (tid < CB) dl[tid] = __ldcg(dinv + tid);
-                __syncthreads();
+                // substitution in double-float (FP32 latencies on the dependent chain)
                 const int64_t r = r0 + wq;
-                double kv = (r < k && lane < nb) ? __ldcg(Kmat + r * k + j0 + lane) : 0.0;
-                double x = 0.0;
+                float2 kv = df_split((r < k && lane < nb) ? __ldcg(Kmat + r * k + j0 + lane) : 0.0);
+                float2 x = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < CB; ++c) {
-                    const double xc = __shfl_sync(0xffffffffu, kv, c) * dl[c];
+                    const float2 kc = make_float2(__shfl_sync(0xffffffffu, kv.x, c), __shfl_sync(0xffffffffu, kv.y, c));
+                    const float2 xc = df_mul2(kc, fb[0][c]);
                     if (lane == c) x = xc;
-                    else if (lane > c) kv = fma(-xc, Ls[lane][c], kv);
+                    else if (lane > c) kv = df_fnms(kv, xc, fa[lane][c]);
                 }
-                if (r < k && lane < nb) Kmat[r * k + j0 + lane] = x;
-                if (r < k) Pdf[r * CB + lane] = df_split(x);   // 0 for lanes >= nb
+                if (r < k && lane < nb) Kmat[r * k + j0 + lane] = (double)x.x + (double)x.y;
+                if (r < k) Pdf[r * CB + lane] = x;   // 0 for lanes >= nb
             }
         }
         if (!grid_sync_bounded(bar, nbar, status)) return;
