@@ -48,15 +48,21 @@ class IHSResult:
 
 def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
                  m_init=1, x0=None, x1=None, tol=1e-5, max_iter=200, floor=0.0,
-                 sketch_fn=None, keep_history=False):
+                 sketch_fn=None, keep_history=False, dual_b=None):
     """Run Algorithm 1 (variant="polyak") or its gradient-only variant
     (variant="gd", Sec. 5) on min 1/2||Ax-b||^2 + nu^2/2 ||x||^2.
 
     sketch_fn(A, m, kind, seed, level) -> SA may replace the oracle's own sketch
     (used to run the method on externally given sketches in tests).
-    keep_history stores (t, x_t, SA in force) for every iterate (small n only)."""
+    keep_history stores (t, x_t, SA in force) for every iterate (small n only).
+    dual_b: run on the dual of App. A.2 instead, with A standing for the dual's
+    data matrix (the transpose of the primal one) and the gradient
+    A^T A z - dual_b + nu^2 z in place of A^T (A z - b) + nu^2 z (b unused)."""
     A = np.asarray(A, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
+    if dual_b is not None:
+        dual_b = np.asarray(dual_b, dtype=np.float64)
+        b = np.zeros(A.shape[0])
     n, d = A.shape
     if m_init < 1 or (m_init & (m_init - 1)):
         raise ValueError("m_init must be a power of two")
@@ -74,7 +80,10 @@ def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
         nonlocal passes
         passes += 1
         Av = A @ v
-        return A.T @ (Av - b) + nu * nu * v, float(Av @ Av)
+        g = A.T @ (Av - b) + nu * nu * v
+        if dual_b is not None:
+            g = g - dual_b
+        return g, float(Av @ Av)
 
     # Draw S, form SA and cache the factor of H_S.
     fac = linalg.WoodburyFactor(sketch_fn(A, m, kind, seed, level), nu)
@@ -135,3 +144,14 @@ def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
             history.append((t, x.copy(), fac.SA))
     return IHSResult(x=x, m=m, level=level, iterations=t, status=status, trace=trace,
                      levels=levels, grad_passes=passes, r=r, r1=r1, history=history)
+
+
+def adaptive_ihs_dual(A, b, nu, **kw):
+    """The underdetermined case (App. A.2): for A of shape (n, d), n <= d, run the
+    method on the dual z* = argmin 1/2 ||A^T z||^2 + nu^2/2 ||z||^2 - b^T z, whose
+    data matrix is A^T (d x n, overdetermined) and whose gradient is
+    A A^T z - b + nu^2 z (App. A.2 drops nu^2 z; the dual objective has it),
+    then map back with x = A^T z.  Returns (x, dual result)."""
+    A = np.asarray(A, dtype=np.float64)
+    res = adaptive_ihs(A.T, np.zeros(A.shape[1]), nu, dual_b=b, **kw)
+    return A.T @ res.x, res
