@@ -202,6 +202,18 @@ int ihs_grad_noalloc(void* stream, const float* A, const float* b, int64_t n, in
 int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
               double nu, double tol, float* x, ihs_report* rep_h);
 
+/* Underdetermined case, n <= d (App. A.2): the same controller on the dual
+ * z* = argmin 1/2 ||A^T z||^2 + nu^2/2 ||z||^2 - b^T z, whose data matrix is A^T
+ * (d x n) and whose gradient is A A^T z - b + nu^2 z; sketches are drawn over
+ * the d rows of A^T with the context's kind, seed and levels.  z starts at 0;
+ * on return x = A^T z (device, d floats; its content on entry is ignored).
+ * A (n x d, row-major FP32) and b (n) are device buffers owned by the caller;
+ * A^T is formed in context scratch (4nd bytes).  tol and rep_h as for
+ * ihs_solve, applied to the dual iteration (rep_h->m_levels are dual sketch
+ * sizes).  IHS_EINVAL when n > d, nu <= 0 or a pointer is NULL. */
+int ihs_solve_dual(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
+                   double nu, double tol, float* x, ihs_report* rep_h);
+
 /* ---- batched solves ------------------------------------------------------- */
 /* One ridge problem of a batch.  A (n x d, row-major FP32), b (n) and x (d)
  * are device buffers owned by the caller; x holds x_1 on entry and x_T on

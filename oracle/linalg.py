@@ -59,6 +59,19 @@ def atb_blocked(A, b, block=16384):
     return out
 
 
+def direct_solve_dual(A, b, nu):
+    """x* = A^T (A A^T + nu^2 I)^{-1} b for n <= d (App. A.2's map x* = A^T z* of
+    the dual optimum; equal to Eq. 1's solution by the push-through identity),
+    by a float64 Cholesky of the n x n matrix and one step of refinement."""
+    A = _f64(A)
+    b = _f64(b)
+    K = A @ A.T + nu * nu * np.eye(A.shape[0])
+    L = np.linalg.cholesky(K)
+    z = _chol_solve(L, b)
+    z = z + _chol_solve(L, b - K @ z)
+    return A.T @ z
+
+
 def direct_solve(A, b, nu):
     """x* = (A^T A + nu^2 I)^{-1} A^T b (Eq. 1's normal equations) by a float64
     Cholesky factorisation, followed by one step of iterative refinement of the

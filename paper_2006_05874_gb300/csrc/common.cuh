@@ -47,6 +47,7 @@ enum ScratchSlot {
     SLOT_SOLVE_SA,        // solver-owned SA (m x d)
     SLOT_MISC,            // small device scalars (status word, reductions)
     SLOT_FACTOR,          // the solver's factor (K/L, block inverses, X, X^T, apply scratch)
+    SLOT_DUAL,            // underdetermined solves: A^T and a zero vector
     SLOT_COUNT
 };
 

@@ -92,10 +92,192 @@ __global__ void k_fold(const double* __restrict__ part, int count, double* __res
     *out = s;
 }
 
+// AT = A^T for row-major A (rows x cols), 32 x 32 tiles through shared memory.
+__global__ void k_transpose_rect(const float* __restrict__ A, int64_t rows, int64_t cols, float* __restrict__ AT) {
+    __shared__ float tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t gr = r0 + r, gc = c0 + tx;
+        tile[r][tx] = (gr < rows && gc < cols) ? A[gr * cols + gc] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t gr = c0 + r, gc = r0 + tx;   // row of AT = column of A
+        if (gr < cols && gc < rows) AT[gr * rows + gc] = tile[tx][r];
+    }
+}
+
+// ---- the underdetermined case (App. A.2) ----------------------------------
+// The dual iterate z is kept as a double-float pair (z + zlo): its gradient
+// A A^T z - b + nu^2 z cancels to a small vector against b, which the FP32
+// iterate of the primal path would not resolve once sigma_1^2 / nu^2 is large.
+// With M = A^T (rows = d, cols = n): r = M (z + zlo) in double-float, then
+// g = M^T r + nu^2 (z + zlo) - b with exact products and FP64 sums.
+
+__device__ __forceinline__ float2 df_two_sum_norm(float a, float b) {   // a + b as a normalised pair
+    float s, e;
+    two_sum(a, b, s, e);
+    return make_float2(s, e);
+}
+
+// r_i = M_i . (z + zlo) (Dot2 on z, FMA on zlo), one warp per row, eight warps
+// per block of 128 rows; block partials of ||r||^2 (FP64).
+__global__ void k_dual_resid(const float* __restrict__ M, int64_t rows, int cols, const float* __restrict__ z,
+                             const float* __restrict__ zlo, float2* __restrict__ r, double* __restrict__ part) {
+    __shared__ double sm[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row_begin = (int64_t)blockIdx.x * 128;
+    double ax2 = 0.0;
+    for (int64_t i = row_begin + warp; i < min(rows, row_begin + 128); i += 8) {
+        Acc2 acc{0.f, 0.f};
+        float l2 = 0.f;
+        const float* mi = M + i * cols;
+        for (int c = lane; c < cols; c += 32) {
+            const float a = mi[c];
+            acc.add_prod(a, z[c]);
+            l2 = __fmaf_rn(a, zlo[c], l2);
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const Acc2 o = acc2_shfl_xor(acc, off);
+            acc.add_pair(o.hi, o.lo);
+            l2 = __fadd_rn(l2, __shfl_xor_sync(0xffffffffu, l2, off));
+        }
+        if (lane == 0) {
+            const float2 v = df_two_sum_norm(acc.hi, __fadd_rn(acc.lo, l2));
+            r[i] = v;
+            const double dv = (double)v.x + (double)v.y;
+            ax2 += dv * dv;
+        }
+    }
+    if (lane == 0) sm[warp] = ax2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sm[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// part[y][c] = sum over the rows of group y of (r_i + r_lo_i) M_ic: exact
+// products of the high parts (TwoProduct), the low parts by FMA.
+__global__ void k_dual_atr(const float* __restrict__ M, int64_t rows, int cols, const float2* __restrict__ r,
+                           int64_t rows_per_group, float2* __restrict__ part) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.y * rows_per_group;
+    const int64_t i1 = min(rows, i0 + rows_per_group);
+    if (c >= cols) return;
+    Acc2 acc{0.f, 0.f};
+    for (int64_t i = i0; i < i1; ++i) {
+        const float a = M[i * cols + c];
+        const float2 ri = r[i];
+        acc.add_prod(ri.x, a);
+        acc.lo = __fmaf_rn(ri.y, a, acc.lo);
+    }
+    part[(size_t)blockIdx.y * cols + c] = make_float2(acc.hi, acc.lo);
+}
+
+// g_c = sum of the partials + nu^2 (z_c + zlo_c) - b_c in FP64, one rounding;
+// block 0 also folds the ||r||^2 partials.
+__global__ void k_dual_reduce(const float2* __restrict__ part, int G, int cols, double nu2,
+                              const float* __restrict__ z, const float* __restrict__ zlo,
+                              const float* __restrict__ b, float* __restrict__ g, const double* __restrict__ rpart,
+                              int nrb, double* __restrict__ ax2) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < cols) {
+        double t = 0.0;
+        for (int y = 0; y < G; ++y) {
+            const float2 v = part[(size_t)y * cols + c];
+            t += (double)v.x + (double)v.y;
+        }
+        t += nu2 * ((double)z[c] + (double)zlo[c]);
+        g[c] = (float)(t - (double)b[c]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ax2) {
+        double t = 0.0;
+        for (int k = 0; k < nrb; ++k) t += rpart[k];
+        *ax2 = t;
+    }
+}
+
+// xc = (x + xlo) - mu gt + beta ((x + xlo) - (xp + xplo)) as a double-float pair;
+// block partials of ||xc||^2 (FP64).
+__global__ void k_candidate_df(const float* __restrict__ x, const float* __restrict__ xlo,
+                               const float* __restrict__ gt, const float* __restrict__ xp,
+                               const float* __restrict__ xplo, int64_t d, float mu, float beta,
+                               float* __restrict__ xc, float* __restrict__ xclo, double* __restrict__ part) {
+    __shared__ double sm[256];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (i < d) {
+        float p, e, s, es;
+        two_prod(-mu, gt[i], p, e);                 // -mu gt exactly
+        two_sum(x[i], p, s, es);
+        float lo = __fadd_rn(xlo[i], __fadd_rn(e, es));
+        if (beta != 0.f) {
+            float dh, de;
+            two_sum(x[i], -xp[i], dh, de);          // x - xp
+            de = __fadd_rn(de, __fsub_rn(xlo[i], xplo[i]));
+            float q, qe, s2, e2;
+            two_prod(beta, dh, q, qe);
+            two_sum(s, q, s2, e2);
+            s = s2;
+            lo = __fadd_rn(lo, __fadd_rn(e2, __fmaf_rn(beta, de, qe)));
+        }
+        const float2 v = df_two_sum_norm(s, lo);
+        xc[i] = v.x;
+        xclo[i] = v.y;
+        sq = ((double)v.x + (double)v.y) * ((double)v.x + (double)v.y);
+    }
+    sm[threadIdx.x] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < 256; ++k) t += sm[k];
+        part[blockIdx.x] = t;
+    }
+}
+
+// x = M (z + zlo) for row-major M (rows x cols): one warp per row, Dot2 on z,
+// FMA on zlo, the fixed-order butterfly over the lanes.
+__global__ void k_rows_dot(const float* __restrict__ M, int64_t rows, int64_t cols, const float* __restrict__ z,
+                           const float* __restrict__ zlo, float* __restrict__ x) {
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= rows) return;
+    const float* row = M + i * cols;
+    Acc2 acc{0.f, 0.f};
+    float l2 = 0.f;
+    for (int64_t l = lane; l < cols; l += 32) {
+        acc.add_prod(row[l], z[l]);
+        l2 = __fmaf_rn(row[l], zlo[l], l2);
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const Acc2 o = acc2_shfl_xor(acc, off);
+        acc.add_pair(o.hi, o.lo);
+        l2 = __fadd_rn(l2, __shfl_xor_sync(0xffffffffu, l2, off));
+    }
+    if (lane == 0) x[i] = __fadd_rn(acc.hi, __fadd_rn(acc.lo, l2));
+}
+
+// Scratch of the dual gradient.
+struct DualScratch {
+    float2* r;        // rows
+    double* rpart;    // ceil(rows / 128)
+    float2* part;     // G x cols
+    int G;
+    int64_t rows_per_group;
+};
+
 struct Solver {
     ihs_ctx* ctx;
     const float* A;
     const float* b;
+    const float* bsub;    // dual mode: the right-hand side b of App. A.2
+    float* vlo[7];        // dual mode: low parts of the double-float iterates
+    DualScratch ds;
     int64_t n, d;
     double nu;
     float* vec[7];        // x, x_prev, g, gt, xc, gc, gtc
@@ -132,7 +314,20 @@ int sketch_level(Solver& S, int64_t m, int level) {
 int evaluate(Solver& S, int ix, int ig, int igt, double* r, double* ax2, double* xx, bool need_xx) {
     ihs_ctx* ctx = S.ctx;
     IHS_CUDA_TRY(cudaEventRecord(ctx->ev[2], ctx->stream));
-    IHS_TRY(ihs_grad_enqueue(ctx, S.A, S.b, S.n, S.d, S.nu, S.vec[ix], S.vec[ig], S.dsc + 1));
+    if (S.bsub) {
+        const unsigned nrb = (unsigned)ceil_div64(S.n, 128);
+        k_dual_resid<<<nrb, 256, 0, ctx->stream>>>(S.A, S.n, (int)S.d, S.vec[ix], S.vlo[ix], S.ds.r, S.ds.rpart);
+        IHS_LAUNCH_CHECK();
+        dim3 grid((unsigned)ceil_div64(S.d, 256), (unsigned)S.ds.G);
+        k_dual_atr<<<grid, 256, 0, ctx->stream>>>(S.A, S.n, (int)S.d, S.ds.r, S.ds.rows_per_group, S.ds.part);
+        IHS_LAUNCH_CHECK();
+        k_dual_reduce<<<(unsigned)ceil_div64(S.d, 256), 256, 0, ctx->stream>>>(
+            S.ds.part, S.ds.G, (int)S.d, S.nu * S.nu, S.vec[ix], S.vlo[ix], S.bsub, S.vec[ig], S.ds.rpart, (int)nrb,
+            S.dsc + 1);
+        IHS_LAUNCH_CHECK();
+    } else {
+        IHS_TRY(ihs_grad_enqueue(ctx, S.A, S.b, S.n, S.d, S.nu, S.vec[ix], S.vec[ig], S.dsc + 1));
+    }
     IHS_CUDA_TRY(cudaEventRecord(ctx->ev[0], ctx->stream));
     IHS_TRY(ihs_apply_enqueue(ctx, S.F, S.vec[ig], S.vec[igt], S.dsc + 0));
     if (need_xx) {
@@ -169,8 +364,13 @@ int reapply(Solver& S, int ig, int igt, double* r) {
 int make_candidate(Solver& S, int ix, int igt, int ixp, double mu, double beta, int ixc, double* xx) {
     ihs_ctx* ctx = S.ctx;
     const unsigned blocks = (unsigned)ceil_div64(S.d, 256);
-    k_candidate<<<blocks, 256, 0, ctx->stream>>>(S.vec[ix], S.vec[igt], S.vec[ixp], S.d, (float)mu, (float)beta,
-                                                S.vec[ixc], S.dsc + 8);
+    if (S.bsub) {
+        k_candidate_df<<<blocks, 256, 0, ctx->stream>>>(S.vec[ix], S.vlo[ix], S.vec[igt], S.vec[ixp], S.vlo[ixp], S.d,
+                                                       (float)mu, (float)beta, S.vec[ixc], S.vlo[ixc], S.dsc + 8);
+    } else {
+        k_candidate<<<blocks, 256, 0, ctx->stream>>>(S.vec[ix], S.vec[igt], S.vec[ixp], S.d, (float)mu, (float)beta,
+                                                    S.vec[ixc], S.dsc + 8);
+    }
     IHS_LAUNCH_CHECK();
     k_fold<<<1, 1, 0, ctx->stream>>>(S.dsc + 8, (int)blocks, S.dsc + 2);
     IHS_LAUNCH_CHECK();
@@ -190,6 +390,7 @@ int solve_impl(Solver& S, double tol, ihs_report* rep) {
     int ix = X, ixp = XP, ig = G, igt = GT, ixc = XC, igc = GC, igtc = GTC;
     const size_t vbytes = (size_t)S.d * sizeof(float);
     IHS_CUDA_TRY(cudaMemcpyAsync(S.vec[XP], S.vec[X], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (S.bsub) IHS_CUDA_TRY(cudaMemcpyAsync(S.vlo[XP], S.vlo[X], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
 
     IHS_TRY(sketch_level(S, m, level));
     rep->m_levels[0] = m;
@@ -271,6 +472,7 @@ int solve_impl(Solver& S, double tol, ihs_report* rep) {
     }
     if (ix != X) {
         IHS_CUDA_TRY(cudaMemcpyAsync(S.vec[X], S.vec[ix], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        if (S.bsub) IHS_CUDA_TRY(cudaMemcpyAsync(S.vlo[X], S.vlo[ix], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
         IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     }
     rep->status = status;
@@ -311,6 +513,67 @@ extern "C" int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n
     const int st = solve_impl(S, tol, &rep);
     if (rep_h) *rep_h = rep;
     if (st == IHS_OK || st == IHS_EMAXITER) {
+        const int s2 = ihs_check_status(ctx);
+        if (s2 != IHS_OK) return s2;
+    }
+    return st;
+}
+
+// Underdetermined case (App. A.2): the controller runs on the dual
+// z* = argmin 1/2 ||A^T z||^2 + nu^2/2 ||z||^2 - b^T z, an overdetermined
+// problem with data matrix A^T (d x n) and gradient A A^T z - b + nu^2 z
+// (double-float iterate and residual, see k_dual_resid); sketches are drawn
+// over the d rows of A^T.  x = A^T z at the end.
+extern "C" int ihs_solve_dual(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
+                              double tol, float* x, ihs_report* rep_h) {
+    if (!ctx || !A || !b || !x) return IHS_EINVAL;
+    if (n < 1 || d < 1 || n > d || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
+    if (!(tol > 0.0)) tol = ctx->p.tol;
+    ihs_report rep;
+    memset(&rep, 0, sizeof(rep));
+    // A^T (d x n), then the dual gradient's scratch: r (d pairs), its ||r||^2
+    // partials, and G x n column partials
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(256, (2 * (int64_t)ctx->sm_count * 256) / n));
+    const size_t at_bytes = ((size_t)n * d * sizeof(float) + 255) & ~(size_t)255;
+    const size_t r_bytes = ((size_t)d * sizeof(float2) + 255) & ~(size_t)255;
+    const size_t rp_bytes = (((size_t)ceil_div64(d, 128)) * sizeof(double) + 255) & ~(size_t)255;
+    const size_t part_bytes = (size_t)G * n * sizeof(float2);
+    void* dws = nullptr;
+    IHS_TRY(ihs_scratch(ctx, SLOT_DUAL, at_bytes + r_bytes + rp_bytes + part_bytes, &dws));
+    char* dp = static_cast<char*>(dws);
+    float* AT = reinterpret_cast<float*>(dp);
+    dim3 tg((unsigned)ceil_div64(d, 32), (unsigned)ceil_div64(n, 32));
+    k_transpose_rect<<<tg, 256, 0, ctx->stream>>>(A, n, d, AT);
+    IHS_LAUNCH_CHECK();
+    Solver S;
+    memset(&S, 0, sizeof(S));
+    S.ctx = ctx;
+    S.A = AT;
+    S.b = nullptr;
+    S.bsub = b;
+    S.n = d;
+    S.d = n;
+    S.nu = nu;
+    S.ds.r = reinterpret_cast<float2*>(dp + at_bytes);
+    S.ds.rpart = reinterpret_cast<double*>(dp + at_bytes + r_bytes);
+    S.ds.part = reinterpret_cast<float2*>(dp + at_bytes + r_bytes + rp_bytes);
+    S.ds.G = (int)G;
+    S.ds.rows_per_group = ceil_div64(d, G);
+    void* ws = nullptr;
+    const size_t vb = ((size_t)n * sizeof(float) + 255) & ~(size_t)255;
+    IHS_TRY(ihs_scratch(ctx, SLOT_SOLVE, 14 * vb + 8192 * sizeof(double), &ws));
+    char* base = static_cast<char*>(ws);
+    for (int i = 0; i < 7; ++i) {
+        S.vec[i] = reinterpret_cast<float*>(base + i * vb);   // vec[0] = z
+        S.vlo[i] = reinterpret_cast<float*>(base + (7 + i) * vb);
+    }
+    S.dsc = reinterpret_cast<double*>(base + 14 * vb);
+    IHS_CUDA_TRY(cudaMemsetAsync(base, 0, 14 * vb, ctx->stream));   // z_0 = 0 (both parts)
+    const int st = solve_impl(S, tol, &rep);
+    if (rep_h) *rep_h = rep;
+    if (st == IHS_OK || st == IHS_EMAXITER) {
+        k_rows_dot<<<(unsigned)ceil_div64(d * 32, 256), 256, 0, ctx->stream>>>(AT, d, n, S.vec[0], S.vlo[0], x);
+        IHS_LAUNCH_CHECK();
         const int s2 = ihs_check_status(ctx);
         if (s2 != IHS_OK) return s2;
     }

@@ -67,6 +67,7 @@ _SIGNATURES = {
     "ihs_apply_hinv": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
     "ihs_grad": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
     "ihs_solve": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
+    "ihs_solve_dual": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_cg": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i32, _i32, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_grad_noalloc": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, _vp], ctypes.c_int),
     "ihs_solve_batched": ([_vp, _vp, _i32, _dbl, _vp], ctypes.c_int),
@@ -237,6 +238,16 @@ class Context:
         st = _lib.ihs_solve(self.handle, _ptr(A), _ptr(b), n, d, float(nu), float(tol), _ptr(x), ctypes.byref(rep))
         if st != IHS_OK and (st != IHS_EMAXITER or raise_on_maxiter):
             _check("ihs_solve", st)
+        return rep
+
+    def solve_dual(self, A, b, nu, x, tol=0.0, raise_on_maxiter=False):
+        """Underdetermined A (n <= d): the dual iteration, x = A^T z on return."""
+        n, d = A.shape
+        rep = Report()
+        st = _lib.ihs_solve_dual(self.handle, _ptr(A), _ptr(b), n, d, float(nu), float(tol), _ptr(x),
+                                 ctypes.byref(rep))
+        if st != IHS_OK and (st != IHS_EMAXITER or raise_on_maxiter):
+            _check("ihs_solve_dual", st)
         return rep
 
     def solve_batched(self, problems, tol=0.0, m_init=None):

@@ -43,6 +43,7 @@ def test_push_through_identity():
     rhs = np.linalg.solve(A.T @ A + nu * nu * np.eye(90), A.T @ b)
     assert np.allclose(lhs, rhs, rtol=1e-10, atol=1e-12)
     assert np.allclose(lhs, linalg.direct_solve(A, b, nu), rtol=1e-10, atol=1e-12)
+    assert np.allclose(linalg.direct_solve_dual(A, b, nu), rhs, rtol=1e-10, atol=1e-12)
 
 
 def test_dual_levels_keyed_like_the_primal():
