@@ -441,6 +441,51 @@ def precision_workload(ihs, stream):
     return {"workload": "precision 1048576x4096 (16 GB), sigma_j=exp(-j/300), gauss gd from m=1", "cases": out}
 
 
+def dual_workload(ihs, stream, p, A):
+    """The underdetermined case (App. A.2) on the spectral workload's matrix
+    transposed: A_u = A^T (2048 x 131072), b_u ~ N(0, I), the same nu; SRHT
+    gradient-IHS on the dual from m = 1, x = A_u^T z.  The dual's tolerance is
+    tightened x0.3 until the FP64 bound ||grad f(x)|| / (nu ||Abar x||) on the
+    primal relative prediction error is <= 1e-5 (as for the precision form)."""
+    import torch
+
+    Au = A.t().contiguous()
+    nu = p.nu
+    bu = torch.from_numpy(np.random.default_rng(11).standard_normal(Au.shape[0]).astype(np.float32)).cuda()
+    bh = bu.cpu().numpy().astype(np.float64)
+    ctx = ihs.Context(kind="srht", variant="gd", tol=TOL, stream=stream)
+    x = torch.zeros(Au.shape[1], device="cuda")
+    ctx.solve_dual(Au, bu, nu, x, tol=1e-7)   # warm-up (scratch)
+    tol = 1e-7
+    for attempt in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rep = ctx.solve_dual(Au, bu, nu, x, tol=tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        xh = x.cpu().numpy().astype(np.float64)
+        # FP64 primal gradient A_u^T (A_u x - b_u) + nu^2 x, with A_u^T = p.A (row blocks)
+        ax = np.zeros(Au.shape[0])
+        for r0 in range(0, p.n, 16384):
+            ax += p.A[r0:r0 + 16384].astype(np.float64).T @ xh[r0:r0 + 16384]
+        res = ax - bh
+        g = nu * nu * xh
+        for r0 in range(0, p.n, 16384):
+            g[r0:r0 + 16384] += p.A[r0:r0 + 16384].astype(np.float64) @ res
+        bound = float(np.linalg.norm(g)) / (nu * math.sqrt(float(ax @ ax) + nu * nu * float(xh @ xh)))
+        if bound <= TOL:
+            break
+        tol *= 0.3
+    ctx.destroy()
+    del Au
+    return {"workload": "underdetermined 2048x131072 (the spectral workload's A transposed), b ~ N(0, I), "
+                        "srht gradient-IHS on the dual from m = 1, x = A^T z",
+            "ms": ms, "dual_tol": tol, "err_bound": bound, "levels": rep.levels(), "iterations": rep.iterations,
+            "grad_passes": rep.grad_passes, "status": int(rep.status)}
+
+
 def minimal_iteration_run(ctx, A, b, p, x_star, stream, t_rule, tol):
     """The same solve stopped at the smallest iteration count t whose iterate is
     within 1e-5 of the FP64 direct solution (found by bisection on max_iter,
@@ -626,6 +671,7 @@ def main():
     forms = solver_forms(ihs, ctx, p, A, b, x_star, stream, args.steps)
     batched = batched_workload(ihs, stream)
     precision = precision_workload(ihs, stream)
+    dual = dual_workload(ihs, stream, p, A)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -650,7 +696,7 @@ def main():
                    "grad_passes_per_solve": r0.grad_passes, "ms_sketch_factor": r0.ms_sketch,
                    "oracle_minimal_iterations": min_iter,
                    "ms_iterate": r0.ms_iterate, "comparators_same_gpu": comparators, "forms_same_gpu": forms,
-                   "batched_same_gpu": batched, "precision_same_gpu": precision},
+                   "batched_same_gpu": batched, "precision_same_gpu": precision, "dual_same_gpu": dual},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(), "peak_source": peak_kind,
                      "kernel": "gradient pass (k_grad_v3 + k_grad_reduce)", "ms_per_launch": ms_grad,
