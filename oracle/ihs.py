@@ -1,7 +1,7 @@
 """Adaptive Polyak-IHS (Algorithm 1) and its gradient-only variant (Sec. 5), in
 float64, following Algorithm 1's steps in order.
 
-Readings of points the paper leaves open (each one is listed in the design doc):
+Readings of points the paper leaves open:
 
 * parameters: rho = 0.1, eta = 0.01 by default; cbar_gd = c_gd, cbar_p = c_p
   and the step sizes of Def 3.1 (Gaussian) / Def 3.2 (SRHT), as Thm 4.1 / 4.2
