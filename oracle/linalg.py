@@ -129,7 +129,7 @@ def _blocked_matvec(A, v, block=16384):
 
 
 def relative_error(A, nu, x, x_star):
-    """||Abar (x - x*)|| / ||Abar x*||, the spec accuracy metric and the
+    """||Abar (x - x*)|| / ||Abar x*||, the accuracy metric of every solution and the
     square root of delta_t / delta_0 for x_0 = 0 (Sec. 1.1)."""
     x, x_star = _f64(x), _f64(x_star)
     return prediction_norm(A, nu, x - x_star) / prediction_norm(A, nu, x_star)
