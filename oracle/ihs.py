@@ -48,7 +48,7 @@ class IHSResult:
 
 def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
                  m_init=1, x0=None, x1=None, tol=1e-5, max_iter=200, floor=0.0,
-                 sketch_fn=None, keep_history=False, dual_b=None):
+                 sketch_fn=None, keep_history=False, dual_b=None, nested=False):
     """Run Algorithm 1 (variant="polyak") or its gradient-only variant
     (variant="gd", Sec. 5) on min 1/2||Ax-b||^2 + nu^2/2 ||x||^2.
 
@@ -57,7 +57,12 @@ def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
     keep_history stores (t, x_t, SA in force) for every iterate (small n only).
     dual_b: run on the dual of App. A.2 instead, with A standing for the dual's
     data matrix (the transpose of the primal one) and the gradient
-    A^T A z - dual_b + nu^2 z in place of A^T (A z - b) + nu^2 z (b unused)."""
+    A^T A z - dual_b + nu^2 z in place of A^T (A z - b) + nu^2 z (b unused).
+    nested: every level draws its sketch with the key of level 0, so that the
+    sketches are nested: the Gaussian S_2m's first m rows are sqrt(1/2) S_m, and
+    the SRHT's 2m rows contain the m rows of S_m with the same signs (each S_m
+    is still a sketch of its kind; the draws are no longer independent across
+    levels, a departure from redrawing S at every doubling)."""
     A = np.asarray(A, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     if dual_b is not None:
@@ -85,8 +90,9 @@ def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
             g = g - dual_b
         return g, float(Av @ Av)
 
+    draw = (lambda lv: 0) if nested else (lambda lv: lv)
     # Draw S, form SA and cache the factor of H_S.
-    fac = linalg.WoodburyFactor(sketch_fn(A, m, kind, seed, level), nu)
+    fac = linalg.WoodburyFactor(sketch_fn(A, m, kind, seed, draw(level)), nu)
     levels = [m]
     # Initial gradient, preconditioned gradient and decrement r_1.
     g, ax2 = grad_at(x)
@@ -134,7 +140,7 @@ def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
                 trace.append(("double", t, m, ratio))
                 m = min(2 * m, m_cap)
                 level += 1
-                fac = linalg.WoodburyFactor(sketch_fn(A, m, kind, seed, level), nu)
+                fac = linalg.WoodburyFactor(sketch_fn(A, m, kind, seed, draw(level)), nu)
                 levels.append(m)
                 gt = fac.apply(g)
                 r = 0.5 * g @ gt
