@@ -237,18 +237,21 @@ def solver_forms(ihs, ctx, p, A, b, x_star, stream, steps):
     """The same solve in the forms this library adds: the learned warm start
     (m0 from the trained network, probe included in the time) with the SRHT
     sketch and with the BF16 / FP8 Gaussian sketch on tensor cores, and the
-    BF16 Gaussian sketch from m = 1.  Each form's tolerance is tightened until
-    its verified error is <= 1e-5; times are device time per solve."""
+    BF16 Gaussian sketch from m = 1, with independent and with nested draws
+    (only the new rows of each doubling computed).  Each form's tolerance is
+    tightened until its verified error is <= 1e-5; times are device time per
+    solve."""
     import torch
 
     from oracle import linalg
     from paper_2006_05874_gb300 import warmstart
 
     out = {}
-    forms = (("srht_warm", "srht", "fp32", True), ("gauss_bf16_warm", "gauss", "bf16", True),
-             ("gauss_fp8_warm", "gauss", "fp8", True), ("gauss_bf16_cold", "gauss", "bf16", False))
-    for name, kind, prec, warm in forms:
-        c2 = ihs.Context(kind=kind, variant="gd", precision=prec, tol=TOL, stream=stream)
+    forms = (("srht_warm", "srht", "fp32", True, 0), ("gauss_bf16_warm", "gauss", "bf16", True, 0),
+             ("gauss_fp8_warm", "gauss", "fp8", True, 0), ("gauss_bf16_cold", "gauss", "bf16", False, 0),
+             ("gauss_bf16_cold_nested", "gauss", "bf16", False, 1))
+    for name, kind, prec, warm, nested in forms:
+        c2 = ihs.Context(kind=kind, variant="gd", precision=prec, tol=TOL, stream=stream, nested=nested)
         ws2 = warmstart.WarmStart(c2) if warm else None
         x = torch.zeros(p.d, device="cuda")
 

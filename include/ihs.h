@@ -75,6 +75,13 @@ typedef struct ihs_params {
     double   floor;      /* noise-floor guard: a rejected step with
                             r_t <= floor^2 r_1 stops instead of doubling (0: off) */
     uint64_t seed;       /* Philox key of every random draw                      */
+    int32_t  nested;     /* 1: every level of ihs_solve draws with the key of
+                            level 0, so the sketches are nested (Gaussian: the
+                            first m rows of S_2m are S_m / sqrt 2 and are reused,
+                            only the new rows are computed; SRHT: the rows of S_m
+                            are a subset of those of S_2m).  Default 0: an
+                            independent draw per level, as the paper samples S. */
+    int32_t  reserved;   /* 0                                                    */
 } ihs_params;
 
 /* What ihs_solve did. */
@@ -148,6 +155,15 @@ int ihs_srht_rows(ihs_ctx* ctx, int64_t n_pad, int64_t m, uint64_t seed, int32_t
  * m <= n_pad.  Uses context scratch. */
 int ihs_sketch(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m,
                int32_t kind, uint64_t seed, int32_t level, float* SA);
+
+/* Rows [row0, row0 + mrows) of the Gaussian SA of size m (S_ji = z_ji / sqrt(m),
+ * z as for ihs_sketch, arithmetic per the context's precision) into SA_rows
+ * (mrows x d FP32, device).  Row j of z does not depend on m, so with a level
+ * fixed the sketch of size 2m is [S_m A / sqrt 2; these new rows]: the nested
+ * sketches of the solver's nested mode.  row0 % 4 == 0, row0 + mrows <= m;
+ * IHS_EINVAL otherwise. */
+int ihs_sketch_rows(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
+                    int32_t level, int64_t row0, int64_t mrows, float* SA_rows);
 
 /* Factor H_S = (SA)^T SA + nu^2 I (Eq. 3) for repeated applies: m < d caches
  * the FP64 Cholesky factor of nu^2 I_m + SA SA^T (Woodbury, App. B.4); m >= d

@@ -944,7 +944,7 @@ int level_change_impl(Batch& B, bool first) {
             return IHS_ENOMEM;
         }
         float* SA = static_cast<float*>(SA0);
-        IHS_TRY(ihs_sketch_enqueue(B.lane[0], g.A, g.n, g.d, q.m, prm.kind, prm.seed, q.level, SA));
+        IHS_TRY(ihs_sketch_enqueue(B.lane[0], g.A, g.n, g.d, q.m, prm.kind, prm.seed, prm.nested ? 0 : q.level, SA));
         g.sa[q.level] = SA;
     }
     IHS_CUDA_TRY(cudaEventRecord(B.lev[0], B.lstream[0]));
@@ -971,7 +971,8 @@ int level_change_impl(Batch& B, bool first) {
                 return IHS_ENOMEM;
             }
             q.SA = static_cast<float*>(sa);
-            IHS_TRY(ihs_sketch_enqueue(lc, q.in.A, q.in.n, q.in.d, q.m, prm.kind, prm.seed, q.level, q.SA));
+            IHS_TRY(ihs_sketch_enqueue(lc, q.in.A, q.in.n, q.in.d, q.m, prm.kind, prm.seed, prm.nested ? 0 : q.level,
+                                       q.SA));
             SA = q.SA;
         }
         IHS_TRY(ihs_factor_alloc_pool(lc, B.pool, SA, q.m, q.in.d, q.in.nu, &q.Fs));

@@ -47,7 +47,8 @@ enum ScratchSlot {
     SLOT_SOLVE_SA,        // solver-owned SA (m x d)
     SLOT_MISC,            // small device scalars (status word, reductions)
     SLOT_FACTOR,          // the solver's factor (K/L, block inverses, X, X^T, apply scratch)
-    SLOT_DUAL,            // underdetermined solves: A^T and a zero vector
+    SLOT_DUAL,            // underdetermined solves: A^T and the dual gradient's scratch
+    SLOT_SOLVE_SA2,       // nested sketches: the previous level's SA while the next one is formed
     SLOT_COUNT
 };
 
@@ -107,12 +108,14 @@ int ihs_check_status(ihs_ctx* ctx);   // reads and clears the device status word
 // Internal launch helpers (enqueue only, no synchronisation).
 int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
                      double nu, const float* x, float* g, double* d_axnorm2);
+int ihs_sketch_rows_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
+                            int32_t level, int64_t row0, int64_t mrows, float* SA_rows);
 int ihs_sketch_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m,
                        int32_t kind, uint64_t seed, int32_t level, float* SA);
 int ihs_gauss_fp32_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
                            int32_t level, float* SA);   // FP32 SIMT Gaussian sketch
 int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
-                         int32_t level, float* SA, int fp8);
+                         int32_t level, float* SA, int fp8, int64_t zrow0 = 0, int64_t m_scale = 0);   // rows [zrow0, zrow0 + m) of the sketch of size m_scale
 int ihs_rows_enqueue(ihs_ctx* ctx, int64_t n_pad, int64_t m, uint64_t seed, int32_t level,
                      int32_t* rows);
 int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F);       // enqueue + check pivots (syncs)

@@ -495,7 +495,7 @@ constexpr int kGBM = 64, kGBN = 64, kGBK = 32, kGThreads = 256;
 
 __global__ void __launch_bounds__(kGThreads)
 k_gauss_simt(const float* __restrict__ A, int64_t n, int d, int64_t m, int64_t rows_per_split, uint32_t level,
-             uint32_t k0, uint32_t k1, float2* __restrict__ part /* KS x m x d */) {
+             uint32_t k0, uint32_t k1, uint32_t zq0 /* first z row / 4 */, float2* __restrict__ part /* KS x m x d */) {
     __shared__ float zs[kGBK][kGBM + 4];
     __shared__ float as[kGBK][kGBN + 4];
     const int tid = threadIdx.x;
@@ -516,7 +516,7 @@ k_gauss_simt(const float* __restrict__ A, int64_t n, int d, int64_t m, int64_t r
             const int ii = e / (kGBM / 4), qq = e % (kGBM / 4);
             const int64_t i = i0 + ii;
             float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < i_end) z = gauss4((uint32_t)i, (uint32_t)((j0 >> 2) + qq), level, k0, k1);
+            if (i < i_end) z = gauss4((uint32_t)i, zq0 + (uint32_t)((j0 >> 2) + qq), level, k0, k1);
             zs[ii][qq * 4 + 0] = z.x;
             zs[ii][qq * 4 + 1] = z.y;
             zs[ii][qq * 4 + 2] = z.z;
@@ -634,8 +634,10 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
     return IHS_OK;
 }
 
+// Rows [zrow0, zrow0 + m) of the Gaussian sketch of size m_scale (zrow0 % 4 == 0).
 int gauss_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed, int32_t level,
-                  float* SA) {
+                  float* SA, int64_t zrow0 = 0, int64_t m_scale = 0) {
+    if (m_scale <= 0) m_scale = m;
     const int64_t MT = ceil_div64(m, kGBM), NT = ceil_div64(d, kGBN);
     int64_t KS = std::max<int64_t>(1, ceil_div64(4 * (int64_t)ctx->sm_count, MT * NT));
     KS = std::min<int64_t>(KS, ceil_div64(n, 4 * kGBK));
@@ -647,11 +649,12 @@ int gauss_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m,
     float2* part = static_cast<float2*>(pws);
     dim3 grid((unsigned)MT, (unsigned)NT, (unsigned)KS);
     k_gauss_simt<<<grid, kGThreads, 0, ctx->stream>>>(A, n, (int)d, m, rows_per_split, (uint32_t)level,
-                                                     (uint32_t)seed, (uint32_t)(seed >> 32), part);
+                                                     (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)(zrow0 >> 2),
+                                                     part);
     IHS_LAUNCH_CHECK();
     const int64_t count = m * d;
     const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
-    k_reduce_parts2<<<rgrid, 256, 0, ctx->stream>>>(part, (int)KS, count, 1.0 / sqrt((double)m), SA);
+    k_reduce_parts2<<<rgrid, 256, 0, ctx->stream>>>(part, (int)KS, count, 1.0 / sqrt((double)m_scale), SA);
     IHS_LAUNCH_CHECK();
     return IHS_OK;
 }
@@ -674,6 +677,21 @@ int ihs_sketch_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64
         return gauss_enqueue(ctx, A, n, d, m, seed, level, SA);
     }
     return IHS_EINVAL;
+}
+
+int ihs_sketch_rows_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
+                            int32_t level, int64_t row0, int64_t mrows, float* SA_rows) {
+    if (n < 1 || d < 1 || m < 1 || level < 0 || m > ((int64_t)1 << 31)) return IHS_EINVAL;
+    if (row0 < 0 || row0 % 4 || mrows < 1 || row0 + mrows > m) return IHS_EINVAL;
+    if (ctx->p.precision == IHS_PREC_BF16) return ihs_gauss_tc_enqueue(ctx, A, n, d, mrows, seed, level, SA_rows, 0, row0, m);
+    if (ctx->p.precision == IHS_PREC_FP8) return ihs_gauss_tc_enqueue(ctx, A, n, d, mrows, seed, level, SA_rows, 1, row0, m);
+    return gauss_enqueue(ctx, A, n, d, mrows, seed, level, SA_rows, row0, m);
+}
+
+extern "C" int ihs_sketch_rows(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
+                               int32_t level, int64_t row0, int64_t mrows, float* SA_rows) {
+    if (!ctx || !A || !SA_rows) return IHS_EINVAL;
+    return ihs_sketch_rows_enqueue(ctx, A, n, d, m, seed, level, row0, mrows, SA_rows);
 }
 
 extern "C" int ihs_sketch(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, int32_t kind,

@@ -285,19 +285,44 @@ struct Solver {
     ihs_factor_t* F;      // points at Fs once a level is factored
     ihs_factor_t Fs;      // scratch-backed factor of the current level
     float* SA;
+    int sa_slot;          // scratch slot holding SA (nested mode alternates two)
     int64_t m;
     int level;
     float ms_sketch, ms_iter, ms_grad;
 };
 
+// old rows of a nested Gaussian sketch: dst = src * scale
+__global__ void k_scale_copy(const float* __restrict__ src, int64_t count, float scale, float* __restrict__ dst) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = __fmul_rn(src[e], scale);
+}
+
 int sketch_level(Solver& S, int64_t m, int level) {
     ihs_ctx* ctx = S.ctx;
+    const bool nested = ctx->p.nested != 0;
+    const int draw = nested ? 0 : level;   // nested: every size drawn with the key of level 0
+    // nested Gaussian doubling: S_m A = [S_{m/2} A / sqrt 2; the new rows], the
+    // previous SA read from the slot it lives in, the new one formed in the other
+    const bool reuse = nested && ctx->p.kind == IHS_SKETCH_GAUSS && S.SA && S.m >= 4 && m > S.m && S.m % 4 == 0;
+    const int slot = reuse ? (S.sa_slot == SLOT_SOLVE_SA ? SLOT_SOLVE_SA2 : SLOT_SOLVE_SA) : SLOT_SOLVE_SA;
+    const float* old_SA = S.SA;
+    const int64_t old_m = S.m;
     S.F = nullptr;
     void* ws = nullptr;
-    IHS_TRY(ihs_scratch(ctx, SLOT_SOLVE_SA, (size_t)m * S.d * sizeof(float), &ws));
+    IHS_TRY(ihs_scratch(ctx, slot, (size_t)m * S.d * sizeof(float), &ws));
     S.SA = static_cast<float*>(ws);
+    S.sa_slot = slot;
     IHS_CUDA_TRY(cudaEventRecord(ctx->ev[0], ctx->stream));
-    IHS_TRY(ihs_sketch_enqueue(ctx, S.A, S.n, S.d, m, ctx->p.kind, ctx->p.seed, level, S.SA));
+    if (reuse) {
+        const int64_t count = old_m * S.d;
+        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
+        k_scale_copy<<<grid, 256, 0, ctx->stream>>>(old_SA, count, (float)sqrt((double)old_m / (double)m), S.SA);
+        IHS_LAUNCH_CHECK();
+        IHS_TRY(ihs_sketch_rows_enqueue(ctx, S.A, S.n, S.d, m, ctx->p.seed, draw, old_m, m - old_m,
+                                        S.SA + (size_t)old_m * S.d));
+    } else {
+        IHS_TRY(ihs_sketch_enqueue(ctx, S.A, S.n, S.d, m, ctx->p.kind, ctx->p.seed, draw, S.SA));
+    }
     IHS_TRY(ihs_factor_scratch(ctx, S.SA, m, S.d, S.nu, &S.Fs));   // synchronises (pivot check)
     S.F = &S.Fs;
     IHS_CUDA_TRY(cudaEventRecord(ctx->ev[1], ctx->stream));

@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("variant", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("m_init", ctypes.c_int64), ("rho", ctypes.c_double),
                 ("eta", ctypes.c_double), ("tol", ctypes.c_double), ("floor", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("nested", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -62,6 +62,7 @@ _SIGNATURES = {
     "ihs_srht_signs": ([_vp, _i64, _u64, _i32, _vp], ctypes.c_int),
     "ihs_srht_rows": ([_vp, _i64, _i64, _u64, _i32, _vp], ctypes.c_int),
     "ihs_sketch": ([_vp, _vp, _i64, _i64, _i64, _i32, _u64, _i32, _vp], ctypes.c_int),
+    "ihs_sketch_rows": ([_vp, _vp, _i64, _i64, _i64, _u64, _i32, _i64, _i64, _vp], ctypes.c_int),
     "ihs_factor": ([_vp, _vp, _i64, _i64, _dbl, ctypes.POINTER(_vp)], ctypes.c_int),
     "ihs_factor_destroy": ([_vp], ctypes.c_int),
     "ihs_apply_hinv": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
@@ -213,6 +214,12 @@ class Context:
 
     def srht_rows(self, n_pad, m, seed, level, rows):
         _check("ihs_srht_rows", _lib.ihs_srht_rows(self.handle, n_pad, m, seed, level, _ptr(rows)))
+
+    def sketch_rows(self, A, m, seed, level, row0, mrows, SA_rows):
+        """Rows [row0, row0 + mrows) of the Gaussian sketch of size m."""
+        n, d = A.shape
+        _check("ihs_sketch_rows", _lib.ihs_sketch_rows(self.handle, _ptr(A), n, d, m, seed, level, row0, mrows,
+                                                       _ptr(SA_rows)))
 
     def sketch(self, A, m, kind, seed, level, SA):
         n, d = A.shape
