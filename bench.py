@@ -155,11 +155,110 @@ def cpu_oracle_sample(p, budget_s=20.0):
         "value": dt * 1e3 * (N_ROWS / n_s),
         "unit": "ms",
         "cores": os.cpu_count(),
+        "cpu_model": cpu_model(),
         "kind": "oracle",
         "sample": "adaptive IHS (SRHT, gradient-only, FP64 numpy) on the first %d of %d rows, %d gradient passes, "
                   "levels %s; wall time %.2f s scaled by %d/%d" % (n_s, N_ROWS, res.grad_passes, res.levels, dt,
                                                                   N_ROWS, n_s),
     }
+
+
+def cpu_model():
+    """The host CPU's model name (x86 'model name' or Arm 'CPU part' lines)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            lines = f.read().splitlines()
+        for key in ("model name", "Model", "CPU part"):
+            for ln in lines:
+                if ln.startswith(key):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def cpu_oracle_single_thread(p, n_s=4096):
+    """The same oracle sample with one BLAS thread (a child process started with
+    the thread counts pinned to 1), time scaled by N_ROWS / n_s."""
+    import subprocess
+    import tempfile
+
+    with tempfile.TemporaryDirectory() as tmp:
+        np.save(os.path.join(tmp, "A.npy"), np.ascontiguousarray(p.A[:n_s]))
+        np.save(os.path.join(tmp, "b.npy"), np.ascontiguousarray(p.b[:n_s]))
+        code = ("import sys, time, json, numpy as np; sys.path.insert(0, %r); from oracle import ihs; "
+                "A = np.load(%r); b = np.load(%r); t0 = time.perf_counter(); "
+                "r = ihs.adaptive_ihs(A, b, %r, kind='srht', variant='gd', tol=%r); "
+                "print(json.dumps([time.perf_counter() - t0, r.grad_passes]))"
+                % (ROOT, os.path.join(tmp, "A.npy"), os.path.join(tmp, "b.npy"), float(p.nu), TOL))
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        dt, passes = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": dt * 1e3 * (N_ROWS / n_s), "unit": "ms", "cores": 1,
+            "sample": "first %d of %d rows, %d gradient passes; wall time %.2f s scaled by %d/%d"
+                      % (n_s, N_ROWS, passes, dt, N_ROWS, n_s)}
+
+
+def sketch_throughput(ihs, A, stream, peaks):
+    """Achieved HBM bandwidth of the SRHT sketch (whole call: row selection,
+    transform, partial reduction) at the sizes of a cold solve's first levels and
+    of its settled level: 4nd bytes read + 4md written per call."""
+    import torch
+
+    n, d = A.shape
+    ctx = ihs.Context(stream=stream)
+    out = {}
+    for m in (16, 1024):
+        SA = torch.empty(m, d, device="cuda")
+        for _ in range(3):
+            ctx.sketch(A, m, "srht", 0, 10, SA)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(10):
+            ctx.sketch(A, m, "srht", 0, 10, SA)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        gbs = (4.0 * n * d + 4.0 * m * d) / ms / 1e6
+        out["m%d" % m] = {"ms": ms, "achieved_gbs": gbs, "frac_measured": gbs / peaks["hbm_gbs"],
+                          "frac_nominal_7900": gbs / 7900.0}
+    ctx.destroy()
+    return out
+
+
+def config1_times(ihs, stream):
+    """Config 1 (exp. decay 4096 x 256, fits in L2: latency-bound): time to the
+    verified 1e-5 from m = 1 with the SRHT and the Gaussian sketch."""
+    import torch
+
+    from oracle import linalg
+    from paper_2006_05874_gb300 import problems
+
+    p = problems.exp_decay(n=4096, d=256, seed=0)
+    xs = linalg.direct_solve(p.A, p.b, p.nu)
+    A, b = torch.from_numpy(p.A).cuda(), torch.from_numpy(p.b).cuda()
+    out = {}
+    for kind in ("srht", "gauss"):
+        ctx = ihs.Context(kind=kind, variant="gd", tol=TOL, stream=stream)
+        x = torch.zeros(p.d, device="cuda")
+        for _ in range(2):
+            x.zero_()
+            ctx.solve(A, b, p.nu, x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            x.zero_()
+            rep = ctx.solve(A, b, p.nu, x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[kind] = {"ms": e0.elapsed_time(e1) / 5, "levels": rep.levels(), "iterations": rep.iterations,
+                     "rel_error": linalg.relative_error(p.A, p.nu, x.cpu().numpy(), xs)}
+        ctx.destroy()
+    return out
 
 
 def run_reference(args):
@@ -675,10 +774,16 @@ def main():
     batched = batched_workload(ihs, stream)
     precision = precision_workload(ihs, stream)
     dual = dual_workload(ihs, stream, p, A)
+    sketch_bw = sketch_throughput(ihs, A, stream, peaks)
+    cfg1 = config1_times(ihs, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(p)
+        try:
+            cpu["single_thread"] = cpu_oracle_single_thread(p)
+        except Exception as e:   # the all-cores figure above stands; say why this one is missing
+            cpu["single_thread"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     r0 = reps[-1]
     line = {
         "metric": "ms to 1e-5 rel. error vs FP64 oracle; grad-pass & sketch HBM GB/s",
@@ -699,9 +804,11 @@ def main():
                    "grad_passes_per_solve": r0.grad_passes, "ms_sketch_factor": r0.ms_sketch,
                    "oracle_minimal_iterations": min_iter,
                    "ms_iterate": r0.ms_iterate, "comparators_same_gpu": comparators, "forms_same_gpu": forms,
-                   "batched_same_gpu": batched, "precision_same_gpu": precision, "dual_same_gpu": dual},
+                   "batched_same_gpu": batched, "precision_same_gpu": precision, "dual_same_gpu": dual,
+                   "srht_sketch_bandwidth": sketch_bw, "config1_exp_decay_4096x256": cfg1},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(), "peak_source": peak_kind,
+                     "frac_nominal_7900": achieved / 7900.0,
                      "kernel": "gradient pass (k_grad_v3 + k_grad_reduce)", "ms_per_launch": ms_grad,
                      "algorithmic_bytes": bytes_per_pass},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * p.n * p.d + 4 * p.n,
