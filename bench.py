@@ -157,6 +157,7 @@ def cpu_oracle_sample(p, budget_s=20.0):
         "cores": os.cpu_count(),
         "cpu_model": cpu_model(),
         "kind": "oracle",
+        "rows_sampled": n_s,
         "sample": "adaptive IHS (SRHT, gradient-only, FP64 numpy) on the first %d of %d rows, %d gradient passes, "
                   "levels %s; wall time %.2f s scaled by %d/%d" % (n_s, N_ROWS, res.grad_passes, res.levels, dt,
                                                                   N_ROWS, n_s),
@@ -168,10 +169,13 @@ def cpu_model():
     try:
         with open("/proc/cpuinfo") as f:
             lines = f.read().splitlines()
+        arm_parts = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1",
+                     "0xd8e": "Arm Neoverse-N3", "0xd84": "Arm Neoverse-V3"}
         for key in ("model name", "Model", "CPU part"):
             for ln in lines:
                 if ln.startswith(key):
-                    return ln.split(":", 1)[1].strip()
+                    v = ln.split(":", 1)[1].strip()
+                    return "%s (CPU part %s)" % (arm_parts[v], v) if v in arm_parts else v
     except OSError:
         pass
     import platform
@@ -781,7 +785,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(p)
         try:
-            cpu["single_thread"] = cpu_oracle_single_thread(p)
+            cpu["single_thread"] = cpu_oracle_single_thread(p, n_s=cpu["rows_sampled"])
         except Exception as e:   # the all-cores figure above stands; say why this one is missing
             cpu["single_thread"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     r0 = reps[-1]
