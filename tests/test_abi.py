@@ -47,13 +47,15 @@ def test_struct_layout_matches_header(tmp_path):
 
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ihs.h"\n'
-                   'int main(){printf("%zu %zu %zu %zu\\n", sizeof(ihs_params), sizeof(ihs_report),'
-                   ' offsetof(ihs_report, m_levels), offsetof(ihs_params, seed));return 0;}\n')
+                   'int main(){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ihs_params), sizeof(ihs_report),'
+                   ' offsetof(ihs_report, m_levels), offsetof(ihs_params, seed), offsetof(ihs_params, nested),'
+                   ' sizeof(ihs_problem), offsetof(ihs_problem, m_init));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     assert [int(v) for v in out] == [ctypes.sizeof(ihs.Params), ctypes.sizeof(ihs.Report),
-                                     ihs.Report.m_levels.offset, ihs.Params.seed.offset]
+                                     ihs.Report.m_levels.offset, ihs.Params.seed.offset, ihs.Params.nested.offset,
+                                     ctypes.sizeof(ihs.Problem), ihs.Problem.m_init.offset]
 
 
 def test_host_only_calls_without_gpu(built_lib):
