@@ -1049,7 +1049,8 @@ inverse:
         // tmp21 = L21 X11   (L21 at rows [sz, 2sz), cols [0, sz) of the pair)
         k_pair_gemm<<<grid, 256, 0, s>>>(X, F->L, 1, k, sz, 2 * sz, sz, 0, 0, 0, X, tmp, sz, 0, 1.0f);
         IHS_LAUNCH_CHECK();
-        // X21 = -X22 tmp21
+        // X21 = -X22 tmp21 (X is both the A operand and C: X22 is read, the
+        // disjoint block X21 written)
         k_pair_gemm<<<grid, 256, 0, s>>>(X, nullptr, 0, k, sz, 2 * sz, sz, sz, sz, 0, tmp, X, sz, 0, -1.0f);
         IHS_LAUNCH_CHECK();
     }
