@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 N_ROWS, D_COLS, DE_TARGET, NOISE, SEED = 131072, 2048, 100.0, 0.01, 0
 TOL = 1e-5
 WORKLOAD = "spectral_131072x2048_poly1_de100_srht_gd"
+METRIC = "ms to 1e-5 rel. error vs FP64 oracle; grad-pass & sketch HBM GB/s"
 
 
 GRAD_PROFILE = os.path.join(ROOT, "profiles", "grad_pass_131072x2048.txt")
@@ -286,7 +287,7 @@ def run_reference(args):
         vals.append(base["value"])
     v = statistics.median(vals)
     base["value"] = v
-    line = {"metric": "ms to 1e-5 rel. error vs FP64 oracle", "value": v, "unit": "ms", "n_gpus": args.gpus,
+    line = {"metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": {"workload": WORKLOAD},
@@ -790,7 +791,7 @@ def main():
             cpu["single_thread"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     r0 = reps[-1]
     line = {
-        "metric": "ms to 1e-5 rel. error vs FP64 oracle; grad-pass & sketch HBM GB/s",
+        "metric": METRIC,
         "value": ms_per,
         "unit": "ms",
         "n_gpus": world,
