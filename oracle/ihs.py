@@ -109,7 +109,7 @@ def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
             break
         accepted = False
         if variant == "polyak":
-            # Polyak candidate, judged by (r_p^+ / r_1)^(1/t).
+            # Polyak candidate, tested by (r_p^+ / r_1)^(1/t).
             xp = x - prm.mu_p * gt + prm.beta_p * (x - x_prev)
             gp, ax2p = grad_at(xp)
             gtp = fac.apply(gp)
@@ -120,7 +120,7 @@ def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
                 x_prev, x, g, gt, r, ax2 = x, xp, gp, gtp, rp, ax2p
                 accepted = True
         if not accepted:
-            # Gradient-IHS candidate, judged by r_gd^+ / r_t.
+            # Gradient-IHS candidate, tested by r_gd^+ / r_t.
             xg = x - prm.mu_gd * gt
             gg, ax2g = grad_at(xg)
             gtg = fac.apply(gg)
