@@ -278,8 +278,10 @@ def run_reference(args):
         if os.environ.get("IHS_REF_FULL") else None
     if p is None:
         p = make_problem("cuda" if _has_cuda() else None)
-    for _ in range(args.warmup):
-        pass
+    from oracle import ihs as oracle_ihs
+
+    for _ in range(args.warmup):  # untimed: the smallest sample, warming BLAS threads and caches
+        oracle_ihs.adaptive_ihs(p.A[:4096], p.b[:4096], p.nu, kind="srht", variant="gd", tol=TOL)
     vals = []
     base = None
     for _ in range(args.steps):
