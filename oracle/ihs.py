@@ -104,8 +104,11 @@ def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
     status = "maxiter"
     t = 1
     while t < max_iter:
-        if r <= 0.0 or math.sqrt(2.0 * prm.Lam * r) <= tol * math.sqrt(ax2 + nu * nu * (x @ x)):
+        scale = tol * math.sqrt(ax2 + nu * nu * (x @ x))
+        if r <= 0.0 or math.sqrt(2.0 * prm.Lam * r) <= scale:
             status = "converged"
+            # the stopping test's value sqrt(2 Lambda r_t) / (tol ||Abar x_t||), <= 1
+            trace.append(("stop", t, m, math.sqrt(2.0 * prm.Lam * max(r, 0.0)) / scale if scale > 0 else 0.0))
             break
         accepted = False
         if variant == "polyak":
@@ -119,6 +122,8 @@ def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
                 trace.append(("polyak", t, m, ratio))
                 x_prev, x, g, gt, r, ax2 = x, xp, gp, gtp, rp, ax2p
                 accepted = True
+            else:
+                trace.append(("polyak_reject", t, m, ratio))
         if not accepted:
             # Gradient-IHS candidate, tested by r_gd^+ / r_t.
             xg = x - prm.mu_gd * gt

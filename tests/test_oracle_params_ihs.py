@@ -96,6 +96,10 @@ def test_adaptive_ihs_reaches_direct_solution(exp_problem, kind, variant):
             assert ratio <= prm.c_gd
         elif ev == "polyak":
             assert ratio <= prm.c_p
+        elif ev == "polyak_reject":
+            assert ratio > prm.c_p
+        elif ev == "stop":
+            assert ratio <= 1.0
         elif ev == "double":
             assert ratio > prm.c_gd
     # the schedule is a doubling sequence

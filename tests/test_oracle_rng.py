@@ -117,3 +117,31 @@ def test_gaussian_rows_match_full():
     full = rng.gaussian_z(11, 200, seed=8, level=2)
     rows = [0, 3, 5, 10]
     assert np.array_equal(rng.gaussian_z_rows(rows, 200, seed=8, level=2), full[rows])
+
+
+def test_sign_layout_known_answer():
+    """Seed 0, level 0: block 0's first Philox call has key (0, 0) and counter
+    (0, 0, 0, 0), whose output is the first published known answer.  Row
+    q = 32 j + w (w < 4) of block 0 takes bit j of word w: eps = +1 for a 0 bit."""
+    c0, c1, c2, c3, k0, k1, *words = _kat_rows()[0]
+    assert (c0, c1, c2, c3, k0, k1) == (0, 0, 0, 0, 0, 0)
+    eps = rng.signs(1024, seed=0, level=0)
+    for w in range(4):
+        for j in range(32):
+            bit = (words[w] >> j) & 1
+            assert eps[32 * j + w] == (1 if bit == 0 else -1), (w, j)
+
+
+def test_sign_blocks_independent():
+    """Every pair of 1024-row blocks is uncorrelated: a layout that reused one
+    block's words for every block, or overlapped the counters of neighbouring
+    blocks, gives correlations of 1 or about 1/2."""
+    blocks = 64
+    e = rng.signs(1024 * blocks, seed=1, level=2).astype(np.float64).reshape(blocks, 1024)
+    corr = e @ e.T / 1024.0
+    off = corr[~np.eye(blocks, dtype=bool)]
+    assert np.max(np.abs(off)) < 5.0 / np.sqrt(1024.0)
+    # and within a block the 32 words' bit columns are uncorrelated too
+    w = e[0].reshape(32, 32)          # [bit j, word w] of block 0
+    cw = w.T @ w / 32.0
+    assert np.max(np.abs(cw[~np.eye(32, dtype=bool)])) < 0.8
