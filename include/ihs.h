@@ -187,22 +187,27 @@ int ihs_grad(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
  * call cudaMalloc/cudaFree: code whose device memory belongs to another
  * allocator (a framework's caching pool, a fixed arena sized up front) and
  * latency-critical loops that must not block in cudaMalloc/cudaFree, which
- * synchronise the device.  The paper has no counterpart; this is a library
- * facility around its gradient of Eq. 1.
+ * synchronise the device.  The paper has no counterpart.
  *
- * Same result as ihs_grad (same kernels, same fixed-order reduction), but it
- * takes no context and allocates nothing: its scratch is a file-scope device
- * array of about 10 MiB (partials of at most 160 CTAs x 8192 columns) that
- * every GPU which loads the library holds until the process exits.
+ * It launches the same kernels with the same grid and the same fixed-order
+ * reduction as ihs_grad for these inputs, so on a GPU with at most 160 SMs
+ * (GB300 has 152) the two return the same bits; on a larger GPU the grid is
+ * sized as if it had 160 SMs and the results agree within the gradient pass's
+ * rounding bound.  It takes no context and allocates nothing: its
+ * scratch is a file-scope device array of about 10 MiB (partials of at most
+ * 160 x 8192 columns) that every GPU which loads the library holds until the
+ * process exits.
  *  - stream: a cudaStream_t (NULL = legacy default stream) on the current
  *    device.  Asynchronous: returns once the work is enqueued.
- *  - A (n x d), b (n), x (d), g (d): device FP32; axnorm2: device double
- *    receiving ||A x||^2, or NULL.
+ *  - A (n x d), b (n), x (d), g (d): device FP32 on the current device;
+ *    axnorm2: device double receiving ||A x||^2, or NULL.
  *  - Limits: 4 <= d <= 8192, d % 4 == 0, n >= 1, A and x 16-byte aligned,
  *    nu >= 0 and finite; anything else returns IHS_EINVAL before any work.
- *  - The first call on a device looks up the device address of the scratch
- *    array (cudaGetSymbolAddress, once per device, with that device current);
- *    make that first call before any stream capture.
+ *  - Each call made outside stream capture looks up the device address of the
+ *    scratch array (cudaGetSymbolAddress, with the stream's device current),
+ *    so calls stay valid across cudaDeviceReset.  A call on a capturing stream
+ *    reuses the address found by an earlier call on that device: make one call
+ *    before any stream capture (IHS_EINVAL otherwise).
  *  - Every call on a device shares the one scratch array (each call rewrites
  *    it fully and clears its status word first): calls that overlap on the
  *    GPU, e.g. from two streams at once, race and must be serialised.
@@ -229,6 +234,68 @@ int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d
  * sizes).  IHS_EINVAL when n > d, nu <= 0 or a pointer is NULL. */
 int ihs_solve_dual(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
                    double nu, double tol, float* x, ihs_report* rep_h);
+
+/* ---- decision trace and resumable solves --------------------------------- */
+/* The controller's decisions, in order, as Algorithm 1 takes them (an auxiliary
+ * record: the paper prints no trace).  `ratio` is the quantity the decision
+ * tested: (r_p / r_1)^(1/t) against cbar_p for the Polyak candidate, r_gd / r_t
+ * against cbar_gd for the gradient-IHS candidate (and for a doubling), and for
+ * a stop the stopping test's value sqrt(2 Lambda r_t) / (tol ||Abar x_t||) <= 1. */
+#define IHS_EV_STOP           0  /* stopping rule met before iteration t           */
+#define IHS_EV_POLYAK         1  /* Polyak candidate accepted                      */
+#define IHS_EV_POLYAK_REJECT  2  /* Polyak candidate rejected                      */
+#define IHS_EV_GD             3  /* gradient-IHS candidate accepted                */
+#define IHS_EV_GD_AT_CAP      4  /* rejected at the cap of m, accepted anyway       */
+#define IHS_EV_DOUBLE         5  /* both rejected: m <- 2m, a new sketch           */
+#define IHS_EV_FLOOR          6  /* rejected at the noise floor: stop              */
+
+typedef struct ihs_event {
+    int32_t kind;    /* IHS_EV_*                                                */
+    int32_t t;       /* iteration index the decision belongs to                 */
+    int64_t m;       /* sketch size in force when it was taken                  */
+    double  r;       /* r_t at that moment (Lemma 4.1 decrement)                */
+    double  ratio;   /* the tested value (see above)                            */
+} ihs_event;
+
+/* Copy up to `cap` events of the context's last solve (ihs_solve,
+ * ihs_solve_resume or ihs_solve_dual) to ev_h (host) and their total count to
+ * *count_h (host; may exceed cap).  ev_h may be NULL when cap == 0. */
+int ihs_trace_events(const ihs_ctx* ctx, ihs_event* ev_h, int32_t cap, int32_t* count_h);
+
+/* Also append every decision to a text file as one JSON object per line
+ * ({"t":..,"m":..,"event":"gd","r":..,"ratio":..}), flushed per line, so that a
+ * long solve can be followed while it runs.  path_h (host string) NULL or ""
+ * closes the file.  IHS_EINVAL if the file cannot be opened. */
+int ihs_ctx_set_trace_file(ihs_ctx* ctx, const char* path_h);
+
+/* Where a solve stands between iterations: enough to continue it later with
+ * the same result (an auxiliary facility; the paper's warm starts along a
+ * regularisation path, Sec. 5, restart from x_t).  The sketch in force is not
+ * stored: it is keyed by (seed, level) and redrawn on resume. */
+typedef struct ihs_state {
+    int32_t t;           /* iteration index of x_t; 0 = not started           */
+    int32_t level;       /* log2 of the sketch size in force                   */
+    int64_t m;           /* that sketch size                                   */
+    double  r1;          /* r_1 of the run (base of the Polyak ratio)          */
+    int32_t grad_passes; /* gradient passes so far                             */
+    int32_t n_levels;    /* sketches drawn so far                              */
+} ihs_state;
+
+/* ihs_solve that starts from, and returns, an ihs_state.  x (device, d): x_t on
+ * entry, the last iterate on exit.  x_prev (device, d): x_{t-1} on entry (read
+ * by the Polyak candidate) and on exit.  st_h (host): st_h->t == 0 starts a new
+ * run from x_1 = x (x_prev is then set to x, level from params.m_init);
+ * otherwise the run continues at (t, level, r1) with the sketch of that level
+ * redrawn.  params.max_iter bounds the total t, so a run split into calls with
+ * rising limits takes the decisions of one uninterrupted run and, in the
+ * default (non-nested) mode, returns the same bits; a nested-mode resume draws
+ * the level's sketch in one piece, equal up to rounding.  On return *st_h
+ * holds the state at exit (IHS_EMAXITER: resumable; IHS_OK: converged).
+ * Errors as ihs_solve; IHS_EINVAL for an inconsistent state (m != 2^level,
+ * t < 0, r1 <= 0 when t > 0). */
+int ihs_solve_resume(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
+                     double nu, double tol, float* x, float* x_prev, ihs_state* st_h,
+                     ihs_report* rep_h);
 
 /* ---- batched solves ------------------------------------------------------- */
 /* One ridge problem of a batch.  A (n x d, row-major FP32), b (n) and x (d)

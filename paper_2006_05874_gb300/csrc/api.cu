@@ -9,6 +9,7 @@
 #include "common.cuh"
 
 #include <atomic>
+#include <vector>
 
 namespace {
 thread_local char g_last_error[512];
@@ -114,6 +115,7 @@ extern "C" int ihs_ctx_destroy(ihs_ctx* c) {
         cudaStreamSynchronize(c->aux);
         cudaStreamDestroy(c->aux);
     }
+    ihs_trace_free(c);
     delete c;
     return IHS_OK;
 }
@@ -180,5 +182,89 @@ int ihs_check_status(ihs_ctx* c) {
         if (h & IHS_DEV_NOTPD) return IHS_ENOTPD;
     }
     IHS_CUDA_TRY(cudaGetLastError());
+    return IHS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Decision log of the controller.
+
+namespace {
+
+struct TraceLog {
+    std::vector<ihs_event> ev;
+    FILE* file = nullptr;
+};
+
+TraceLog* trace_of(ihs_ctx* c, bool create) {
+    if (!c->trace && create) c->trace = new (std::nothrow) TraceLog;
+    return static_cast<TraceLog*>(c->trace);
+}
+
+const char* event_name(int kind) {
+    switch (kind) {
+        case IHS_EV_STOP: return "stop";
+        case IHS_EV_POLYAK: return "polyak";
+        case IHS_EV_POLYAK_REJECT: return "polyak_reject";
+        case IHS_EV_GD: return "gd";
+        case IHS_EV_GD_AT_CAP: return "gd_at_cap";
+        case IHS_EV_DOUBLE: return "double";
+        case IHS_EV_FLOOR: return "floor";
+        default: return "unknown";
+    }
+}
+
+}  // namespace
+
+void ihs_trace_reset(ihs_ctx* c) {
+    TraceLog* T = trace_of(c, true);
+    if (T) T->ev.clear();
+}
+
+void ihs_trace_add(ihs_ctx* c, int kind, int t, int64_t m, double r, double ratio) {
+    TraceLog* T = trace_of(c, true);
+    if (!T) return;
+    ihs_event e;
+    e.kind = kind;
+    e.t = t;
+    e.m = m;
+    e.r = r;
+    e.ratio = ratio;
+    T->ev.push_back(e);
+    if (T->file) {
+        fprintf(T->file, "{\"t\": %d, \"m\": %lld, \"event\": \"%s\", \"r\": %.17g, \"ratio\": %.17g}\n", t,
+                (long long)m, event_name(kind), r, ratio);
+        fflush(T->file);
+    }
+}
+
+void ihs_trace_free(ihs_ctx* c) {
+    TraceLog* T = trace_of(c, false);
+    if (!T) return;
+    if (T->file) fclose(T->file);
+    delete T;
+    c->trace = nullptr;
+}
+
+extern "C" int ihs_trace_events(const ihs_ctx* c, ihs_event* ev, int32_t cap, int32_t* count) {
+    if (!c || !count || cap < 0 || (cap > 0 && !ev)) return IHS_EINVAL;
+    const TraceLog* T = static_cast<const TraceLog*>(c->trace);
+    const size_t total = T ? T->ev.size() : 0;
+    *count = (int32_t)total;
+    for (size_t i = 0; i < total && i < (size_t)cap; ++i) ev[i] = T->ev[i];
+    return IHS_OK;
+}
+
+extern "C" int ihs_ctx_set_trace_file(ihs_ctx* c, const char* path) {
+    if (!c) return IHS_EINVAL;
+    TraceLog* T = trace_of(c, true);
+    if (!T) return IHS_ENOMEM;
+    if (T->file) {
+        fclose(T->file);
+        T->file = nullptr;
+    }
+    if (path && path[0]) {
+        T->file = fopen(path, "a");
+        if (!T->file) return IHS_EINVAL;
+    }
     return IHS_OK;
 }

@@ -1247,6 +1247,7 @@ void ihs_lanes_destroy(void* lanes) {
 
 extern "C" int ihs_solve_batched(ihs_ctx* ctx, const ihs_problem* probs_h, int32_t count, double tol,
                                  ihs_report* reps_h) {
+    IhsRange range("ihs_solve_batched");
     if (!ctx || !probs_h || count < 1) return IHS_EINVAL;
     if (ctx->p.variant != IHS_VARIANT_GD) {
         ihs_set_error("ihs_solve_batched runs the gradient-IHS variant only");

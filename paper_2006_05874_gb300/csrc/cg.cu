@@ -70,6 +70,7 @@ __global__ void k_neg_inplace(float* a, int64_t n) {
 
 extern "C" int ihs_cg(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu, double tol,
                       int32_t max_iter, int32_t precond_kind, float* x, ihs_report* rep_h) {
+    IhsRange range("ihs_cg");
     if (!ctx || !A || !b || !x || n < 1 || d < 1 || !(nu > 0.0) || !isfinite(nu) || !(tol > 0.0) || max_iter < 1)
         return IHS_EINVAL;
     if (precond_kind != -1 && precond_kind != IHS_SKETCH_SRHT && precond_kind != IHS_SKETCH_GAUSS) return IHS_EINVAL;

@@ -7,6 +7,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ihs.h"
 
 #define IHS_CUDA_TRY(expr)                                  \
@@ -70,6 +72,22 @@ struct ihs_ctx {
     cudaEvent_t fev[8];      // fork/join events of the look-ahead Cholesky
     void* lanes;             // batched solves: sub-contexts, streams and memory pool kept across calls
     int no_coop;             // 1: factorisations use the multi-launch form (many run side by side)
+    void* trace;             // decision log of the last solve (api.cu), NULL until first use
+};
+
+// Decision log of the controller (api.cu): cleared at the start of a solve,
+// one entry per decision, mirrored to the context's JSON-lines file if set.
+void ihs_trace_reset(ihs_ctx* ctx);
+void ihs_trace_add(ihs_ctx* ctx, int kind, int t, int64_t m, double r, double ratio);
+void ihs_trace_free(ihs_ctx* ctx);
+
+// NVTX range for the scope of a library call or phase (a no-op unless a
+// profiler is attached).
+struct IhsRange {
+    explicit IhsRange(const char* name) { nvtxRangePushA(name); }
+    ~IhsRange() { nvtxRangePop(); }
+    IhsRange(const IhsRange&) = delete;
+    IhsRange& operator=(const IhsRange&) = delete;
 };
 
 void ihs_lanes_destroy(void* lanes);   // batch.cu

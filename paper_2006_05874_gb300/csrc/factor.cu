@@ -1238,6 +1238,7 @@ void ihs_factor_release_pool(ihs_factor_t* F, cudaStream_t s) {
 }
 
 extern "C" int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** out) {
+    IhsRange range("ihs_factor");
     if (!out) return IHS_EINVAL;
     *out = nullptr;
     ihs_factor_t* F = nullptr;
@@ -1265,6 +1266,7 @@ extern "C" int ihs_factor_destroy(ihs_factor_t* F) {
 }
 
 extern "C" int ihs_apply_hinv(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt, double* r_h) {
+    IhsRange range("ihs_apply_hinv");
     if (!ctx || !F || !g || !gt) return IHS_EINVAL;
     double* d_r = F->work + factor_work_doubles(F->k, F->m, F->d) - 8;
     IHS_TRY(ihs_apply_enqueue(ctx, F, g, gt, d_r));

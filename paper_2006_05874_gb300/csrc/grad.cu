@@ -768,8 +768,16 @@ FastCfg pick_fast(int d) {
     return {256, 8, 1};
 }
 
+// Where a gradient launch goes: stream, SM count (grid size) and the status
+// word its bounded waits report to.
+struct GradTarget {
+    cudaStream_t stream;
+    int sm_count;
+    unsigned* status;
+};
+
 template <int TPR, int CPT, int RT, int MINB>
-int launch_fast(ihs_ctx* ctx, const float* A, const float* b, const float* x, int64_t n, int d, float2* part,
+int launch_fast(const GradTarget& tg, const float* A, const float* b, const float* x, int64_t n, int d, float2* part,
                 double* part_ax2, int* G_out) {
     constexpr int RP = kThreads / TPR;
     constexpr int R = RT * RP;
@@ -783,19 +791,18 @@ int launch_fast(ihs_ctx* ctx, const float* A, const float* b, const float* x, in
     const size_t comb = (size_t)RP * d * sizeof(Acc2);
     if (smem < comb) smem = comb;
     const int64_t ntiles = ceil_div64(n, R);
-    int64_t G = (int64_t)MINB * ctx->sm_count;
+    int64_t G = (int64_t)MINB * tg.sm_count;
     if (G > ntiles) G = ntiles;
     auto kern = k_grad_fast<TPR, CPT, RT, MINB>;
     IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
-    kern<<<(unsigned)G, kThreads, smem, ctx->stream>>>(A, b, x, n, d, ntiles, stages, part, part_ax2,
-                                                      ctx->d_status);
+    kern<<<(unsigned)G, kThreads, smem, tg.stream>>>(A, b, x, n, d, ntiles, stages, part, part_ax2, tg.status);
     IHS_LAUNCH_CHECK();
     *G_out = (int)G;
     return IHS_OK;
 }
 
 template <int NSEG, int CPT, bool FULL>
-int launch_v3(ihs_ctx* ctx, const float* A, const float* b, const float* x, int64_t n, int d, float2* part,
+int launch_v3(const GradTarget& tg, const float* A, const float* b, const float* x, int64_t n, int d, float2* part,
               double* part_ax2, int* G_out) {
     // two rows per row group: a tile is 64 KB at d = 1024 ... 8192, so the
     // per-tile hand-offs are spread over twice the elements
@@ -806,11 +813,11 @@ int launch_v3(ihs_ctx* ctx, const float* A, const float* b, const float* x, int6
     if (S < 3) return IHS_EINVAL;
     const size_t smem = V3Layout(S, R, d, kV3Consumers * 32 * RPW).total;
     const int64_t ntiles = ceil_div64(n, R);
-    int64_t G = ctx->sm_count;
+    int64_t G = tg.sm_count;
     if (G > ntiles) G = ntiles;
     auto kern = k_grad_v3<NSEG, CPT, FULL, RPW>;
     IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
-    kern<<<(unsigned)G, kV3Threads, smem, ctx->stream>>>(A, b, x, n, d, ntiles, S, part, part_ax2, ctx->d_status);
+    kern<<<(unsigned)G, kV3Threads, smem, tg.stream>>>(A, b, x, n, d, ntiles, S, part, part_ax2, tg.status);
     IHS_LAUNCH_CHECK();
     *G_out = (int)G;
     return IHS_OK;
@@ -826,6 +833,36 @@ int pick_v3(int64_t d) {
     return nseg;
 }
 
+// The fused pass for 16-byte aligned A and x, d % 4 == 0, d <= 8192: the
+// wide-row pipeline for 1024 <= d <= 8192, the register reduce-scatter kernel
+// (two CTAs per SM) below; partials of G CTAs into part / part_ax2.
+int grad_pass_fast(const GradTarget& tg, const float* A, const float* b, const float* x, int64_t n, int64_t d,
+                   float2* part, double* part_ax2, int* G_out) {
+    int& G = *G_out;
+    const int wpr = pick_v3(d);
+    if (wpr) {
+        int st;
+        const bool full = (d % (wpr * 512)) == 0;
+        if (wpr == 2) st = full ? launch_v3<2, 1, true>(tg, A, b, x, n, (int)d, part, part_ax2, &G)
+                                : launch_v3<2, 1, false>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (wpr == 4) st = full ? launch_v3<4, 1, true>(tg, A, b, x, n, (int)d, part, part_ax2, &G)
+                                     : launch_v3<4, 1, false>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+        else if (wpr == 8) st = full ? launch_v3<8, 2, true>(tg, A, b, x, n, (int)d, part, part_ax2, &G)
+                                     : launch_v3<8, 2, false>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+        else st = full ? launch_v3<16, 4, true>(tg, A, b, x, n, (int)d, part, part_ax2, &G)
+                       : launch_v3<16, 4, false>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+        return st;
+    }
+    const FastCfg c = pick_fast((int)d);
+    if (c.tpr == 32) return launch_fast<32, 1, 8, 2>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+    if (c.tpr == 64) return launch_fast<64, 1, 8, 2>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+    if (c.tpr == 128) return launch_fast<128, 1, 8, 2>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+    if (c.cpt == 1) return launch_fast<256, 1, 8, 2>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+    if (c.cpt == 2) return launch_fast<256, 2, 4, 2>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+    if (c.cpt == 4) return launch_fast<256, 4, 2, 1>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+    return launch_fast<256, 8, 1, 1>(tg, A, b, x, n, (int)d, part, part_ax2, &G);
+}
+
 }  // namespace
 
 int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
@@ -839,30 +876,9 @@ int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, in
     float2* part = static_cast<float2*>(ws);
     double* part_ax2 = reinterpret_cast<double*>(static_cast<char*>(ws) + part_bytes);
     int G = 0;
-    const int wpr = aligned ? pick_v3(d) : 0;
-    if (wpr) {
-        int st;
-        const bool full = (d % (wpr * 512)) == 0;
-        if (wpr == 2) st = full ? launch_v3<2, 1, true>(ctx, A, b, x, n, (int)d, part, part_ax2, &G)
-                                : launch_v3<2, 1, false>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (wpr == 4) st = full ? launch_v3<4, 1, true>(ctx, A, b, x, n, (int)d, part, part_ax2, &G)
-                                     : launch_v3<4, 1, false>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (wpr == 8) st = full ? launch_v3<8, 2, true>(ctx, A, b, x, n, (int)d, part, part_ax2, &G)
-                                     : launch_v3<8, 2, false>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else st = full ? launch_v3<16, 4, true>(ctx, A, b, x, n, (int)d, part, part_ax2, &G)
-                       : launch_v3<16, 4, false>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        IHS_TRY(st);
-    } else if (aligned && n >= 1) {
-        const FastCfg c = pick_fast((int)d);
-        int st;
-        if (c.tpr == 32) st = launch_fast<32, 1, 8, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (c.tpr == 64) st = launch_fast<64, 1, 8, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (c.tpr == 128) st = launch_fast<128, 1, 8, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (c.cpt == 1) st = launch_fast<256, 1, 8, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (c.cpt == 2) st = launch_fast<256, 2, 4, 2>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else if (c.cpt == 4) st = launch_fast<256, 4, 2, 1>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        else st = launch_fast<256, 8, 1, 1>(ctx, A, b, x, n, (int)d, part, part_ax2, &G);
-        IHS_TRY(st);
+    const GradTarget tg{ctx->stream, ctx->sm_count, ctx->d_status};
+    if (aligned) {
+        IHS_TRY(grad_pass_fast(tg, A, b, x, n, d, part, part_ax2, &G));
     } else {
         const int64_t rblocks = ceil_div64(n, 128);
         void* rws = nullptr;
@@ -892,6 +908,7 @@ int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, in
 
 extern "C" int ihs_grad(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
                         const float* x, float* g, double* axnorm2_h) {
+    IhsRange range("ihs_grad");
     if (!ctx || !A || !b || !x || !g) return IHS_EINVAL;
     if (!(nu >= 0.0) || n < 1 || d < 1) return IHS_EINVAL;
     double* d_ax = nullptr;
@@ -920,18 +937,23 @@ extern "C" int ihs_grad(ihs_ctx* ctx, const float* A, const float* b, int64_t n,
 // needs no context and allocates nothing: its scratch (the per-CTA partial
 // sums and a status word) lives in a file-scope __device__ array of fixed
 // size, which every GPU that loads the library holds until the process exits.
+// It launches the same kernels with the same grid as ihs_grad (for 16-byte
+// aligned A and x and d % 4 == 0), so on a GPU with at most 160 SMs the two
+// return the same bits.
 #include <mutex>
 
-#define IHS_NOALLOC_MAX_CTAS 160
+#define IHS_NOALLOC_MAX_SMS 160
 #define IHS_NOALLOC_MAX_D 8192
 
 namespace {
 
-constexpr size_t kNoallocPartBytes = (size_t)IHS_NOALLOC_MAX_CTAS * IHS_NOALLOC_MAX_D * sizeof(float2);
-constexpr size_t kNoallocAx2Bytes = (size_t)IHS_NOALLOC_MAX_CTAS * sizeof(double);
+// Partials: G CTAs x d columns of float2, G = SMs (d >= 1024) or 2 x SMs
+// (d < 1024), so G x d <= 160 x 8192 in both cases.
+constexpr size_t kNoallocPartBytes = (size_t)IHS_NOALLOC_MAX_SMS * IHS_NOALLOC_MAX_D * sizeof(float2);
+constexpr size_t kNoallocAx2Bytes = (size_t)2 * IHS_NOALLOC_MAX_SMS * sizeof(double);
 constexpr size_t kNoallocBytes = kNoallocPartBytes + kNoallocAx2Bytes + 256;   // + status word
 
-// ~10 MiB: 160 x 8192 float2 partials, 160 double partials, a status word.
+// ~10 MiB: 160 x 8192 float2 partials, 320 double partials, a status word.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 struct NoallocDevice {
@@ -942,23 +964,34 @@ struct NoallocDevice {
 NoallocDevice g_noalloc_dev[128];
 std::mutex g_noalloc_mu;
 
-// Once per device, with that device current: the device address of the
-// scratch array (the host-side symbol is only a stand-in) and the SM count.
-int noalloc_setup(NoallocDevice** out) {
+// The device address of the scratch array on the current device (the
+// host-side symbol is only a stand-in) and the SM count.  The address is
+// looked up again on every call made outside stream capture (cheap, and
+// correct after the module was reloaded, e.g. following cudaDeviceReset); a
+// call on a capturing stream uses the address cached by an earlier call on the
+// same device, and fails with IHS_EINVAL if there was none.
+int noalloc_setup(cudaStream_t stream, NoallocDevice** out) {
     int dev = 0;
     IHS_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 128) return IHS_EINVAL;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    IHS_CUDA_TRY(cudaStreamIsCapturing(stream, &cap));
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     NoallocDevice& nd = g_noalloc_dev[dev];
+    if (cap != cudaStreamCaptureStatusNone) {
+        if (!nd.ready) return IHS_EINVAL;
+        *out = &nd;
+        return IHS_OK;
+    }
+    void* ptr = nullptr;
+    IHS_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
     if (!nd.ready) {
-        void* ptr = nullptr;
-        IHS_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
         int sms = 0;
         IHS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        nd.scratch = static_cast<unsigned char*>(ptr);
         nd.sm_count = sms;
-        nd.ready = true;
     }
+    nd.scratch = static_cast<unsigned char*>(ptr);
+    nd.ready = true;
     *out = &nd;
     return IHS_OK;
 }
@@ -993,30 +1026,6 @@ __global__ void k_grad_reduce_noalloc(const float2* __restrict__ part, const dou
     }
 }
 
-template <int TPR, int CPT, int RT>
-int launch_fast_noalloc(cudaStream_t stream, int sm_count, const float* A, const float* b, const float* x,
-                        int64_t n, int d, float2* part, double* part_ax2, unsigned* status, int* G_out) {
-    constexpr int RP = kThreads / TPR;
-    constexpr int R = RT * RP;
-    constexpr int W = TPR / 32;
-    const size_t stage_bytes = (size_t)R * d * sizeof(float);
-    const size_t budget = 200 * 1024;
-    int stages = 8;
-    while (stages > 2 && FastLayout(stages, R, W, d).total > budget) --stages;
-    size_t smem = FastLayout(stages, R, W, d).total;
-    if (smem > budget || stage_bytes * stages > budget) return IHS_EINVAL;
-    const size_t comb = (size_t)RP * d * sizeof(Acc2);
-    if (smem < comb) smem = comb;
-    const int64_t ntiles = ceil_div64(n, R);
-    int64_t G = std::min<int64_t>(std::min<int64_t>(sm_count, IHS_NOALLOC_MAX_CTAS), ntiles);
-    auto kern = k_grad_fast<TPR, CPT, RT, 1>;
-    IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
-    kern<<<(unsigned)G, kThreads, smem, stream>>>(A, b, x, n, d, ntiles, stages, part, part_ax2, status);
-    IHS_LAUNCH_CHECK();
-    *G_out = (int)G;
-    return IHS_OK;
-}
-
 }  // namespace
 
 extern "C" int ihs_grad_noalloc(void* stream_v, const float* A, const float* b, int64_t n, int64_t d, double nu,
@@ -1025,25 +1034,17 @@ extern "C" int ihs_grad_noalloc(void* stream_v, const float* A, const float* b, 
     if (n < 1 || d < 4 || d > IHS_NOALLOC_MAX_D || d % 4 != 0) return IHS_EINVAL;
     if (!(nu >= 0.0) || !isfinite(nu)) return IHS_EINVAL;
     if ((uintptr_t)A % 16 != 0 || (uintptr_t)x % 16 != 0) return IHS_EINVAL;
-    NoallocDevice* nd = nullptr;
-    IHS_TRY(noalloc_setup(&nd));
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    NoallocDevice* nd = nullptr;
+    IHS_TRY(noalloc_setup(stream, &nd));
     float2* part = reinterpret_cast<float2*>(nd->scratch);
     double* part_ax2 = reinterpret_cast<double*>(nd->scratch + kNoallocPartBytes);
     unsigned* status = reinterpret_cast<unsigned*>(nd->scratch + kNoallocPartBytes + kNoallocAx2Bytes);
     // The status word must start at zero; the partials are fully rewritten.
     IHS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned), stream));
-    const FastCfg c = pick_fast((int)d);
+    const GradTarget tg{stream, std::min(nd->sm_count, IHS_NOALLOC_MAX_SMS), status};
     int G = 0;
-    int st;
-    if (c.tpr == 32) st = launch_fast_noalloc<32, 1, 8>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
-    else if (c.tpr == 64) st = launch_fast_noalloc<64, 1, 8>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
-    else if (c.tpr == 128) st = launch_fast_noalloc<128, 1, 8>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
-    else if (c.cpt == 1) st = launch_fast_noalloc<256, 1, 8>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
-    else if (c.cpt == 2) st = launch_fast_noalloc<256, 2, 4>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
-    else if (c.cpt == 4) st = launch_fast_noalloc<256, 4, 2>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
-    else st = launch_fast_noalloc<256, 8, 1>(stream, nd->sm_count, A, b, x, n, (int)d, part, part_ax2, status, &G);
-    IHS_TRY(st);
+    IHS_TRY(grad_pass_fast(tg, A, b, x, n, d, part, part_ax2, &G));
     k_grad_reduce_noalloc<<<(unsigned)ceil_div64(d, 32), 256, 0, stream>>>(part, part_ax2, G, (int)d, nu * nu, x, g,
                                                                           axnorm2, status);
     IHS_LAUNCH_CHECK();

@@ -368,6 +368,7 @@ extern "C" int ihs_mlp_train_step(ihs_ctx* ctx, float* params, float* adam_m, fl
 
 extern "C" int ihs_warm_start(ihs_ctx* ctx, const float* params, const float* A, int64_t n, int64_t d, double nu,
                               uint64_t seed, int64_t* m0, float* pred_h) {
+    IhsRange range("ihs_warm_start");
     if (!ctx || !params || !A || !m0 || n < 1 || d < 1 || !(nu > 0.0)) return IHS_EINVAL;
     void* ws = nullptr;
     // features and prediction live past the probe's scratch in the same slot

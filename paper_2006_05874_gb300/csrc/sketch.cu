@@ -690,12 +690,14 @@ int ihs_sketch_rows_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, 
 
 extern "C" int ihs_sketch_rows(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
                                int32_t level, int64_t row0, int64_t mrows, float* SA_rows) {
+    IhsRange range("ihs_sketch_rows");
     if (!ctx || !A || !SA_rows) return IHS_EINVAL;
     return ihs_sketch_rows_enqueue(ctx, A, n, d, m, seed, level, row0, mrows, SA_rows);
 }
 
 extern "C" int ihs_sketch(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, int32_t kind,
                           uint64_t seed, int32_t level, float* SA) {
+    IhsRange range("ihs_sketch");
     if (!ctx || !A || !SA) return IHS_EINVAL;
     IHS_TRY(ihs_sketch_enqueue(ctx, A, n, d, m, kind, seed, level, SA));
     return IHS_OK;

@@ -403,18 +403,29 @@ int make_candidate(Solver& S, int ix, int igt, int ixp, double mu, double beta, 
     return IHS_OK;
 }
 
-int solve_impl(Solver& S, double tol, ihs_report* rep) {
+// st (may be NULL): st->t > 0 continues a run at (t, level, r1) from x_t in
+// vec[X] and x_{t-1} in `x_prev_in`; on return *st holds the state at exit and
+// x_{T-1} is copied to `x_prev_out` (both may be NULL).
+int solve_impl(Solver& S, double tol, ihs_report* rep, ihs_state* st = nullptr, const float* x_prev_in = nullptr,
+               float* x_prev_out = nullptr) {
     ihs_ctx* ctx = S.ctx;
     const ihs_params& p = ctx->p;
     const Params prm = make_params(p.kind, p.rho, p.eta);
     const int64_t m_cap = p.kind == IHS_SKETCH_SRHT ? next_pow2_64(S.n) : S.n;
-    int64_t m = std::min<int64_t>(p.m_init, m_cap);
+    const bool resume = st && st->t > 0;
+    int64_t m = resume ? st->m : std::min<int64_t>(p.m_init, m_cap);
     int level = 0;
-    while (((int64_t)1 << level) < m) ++level;
+    if (resume) {
+        level = st->level;
+    } else {
+        while (((int64_t)1 << level) < m) ++level;
+    }
+    ihs_trace_reset(ctx);
     enum { X = 0, XP = 1, G = 2, GT = 3, XC = 4, GC = 5, GTC = 6 };
     int ix = X, ixp = XP, ig = G, igt = GT, ixc = XC, igc = GC, igtc = GTC;
     const size_t vbytes = (size_t)S.d * sizeof(float);
-    IHS_CUDA_TRY(cudaMemcpyAsync(S.vec[XP], S.vec[X], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    const float* xp_src = (resume && x_prev_in) ? x_prev_in : S.vec[X];
+    IHS_CUDA_TRY(cudaMemcpyAsync(S.vec[XP], xp_src, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (S.bsub) IHS_CUDA_TRY(cudaMemcpyAsync(S.vlo[XP], S.vlo[X], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
 
     IHS_TRY(sketch_level(S, m, level));
@@ -423,16 +434,18 @@ int solve_impl(Solver& S, double tol, ihs_report* rep) {
     double r, ax2, xx;
     IHS_TRY(evaluate(S, ix, ig, igt, &r, &ax2, &xx, true));
     rep->grad_passes = 1;
-    const double r1 = r;
+    const double r1 = resume ? st->r1 : r;
     rep->r1 = r1;
-    int t = 1;
+    int t = resume ? st->t : 1;
     int status = IHS_EMAXITER;
     while (true) {
         if (!isfinite(r) || !isfinite(ax2)) {
             status = IHS_ENONFINITE;
             break;
         }
-        if (r <= 0.0 || sqrt(2.0 * prm.Lam * r) <= tol * sqrt(ax2 + S.nu * S.nu * xx)) {
+        const double scale = tol * sqrt(ax2 + S.nu * S.nu * xx);
+        if (r <= 0.0 || sqrt(2.0 * prm.Lam * r) <= scale) {
+            ihs_trace_add(ctx, IHS_EV_STOP, t, S.m, r, scale > 0.0 ? sqrt(2.0 * prm.Lam * fmax(r, 0.0)) / scale : 0.0);
             status = IHS_OK;
             break;
         }
@@ -445,6 +458,8 @@ int solve_impl(Solver& S, double tol, ihs_report* rep) {
             xxc = ctx->pinned[2];
             rep->grad_passes++;
             const double ratio = rc > 0.0 ? pow(rc / r1, 1.0 / t) : 0.0;
+            ihs_trace_add(ctx, (isfinite(rc) && ratio <= prm.c_p) ? IHS_EV_POLYAK : IHS_EV_POLYAK_REJECT, t, S.m, r,
+                          ratio);
             if (isfinite(rc) && ratio <= prm.c_p) {
                 std::swap(ixp, ix);
                 std::swap(ix, ixc);   // x_prev <- x, x <- xc, xc <- old x_prev
@@ -469,6 +484,7 @@ int solve_impl(Solver& S, double tol, ihs_report* rep) {
             }
             const double ratio = rc / r;
             if (ratio <= prm.c_gd || S.m >= m_cap) {
+                ihs_trace_add(ctx, ratio <= prm.c_gd ? IHS_EV_GD : IHS_EV_GD_AT_CAP, t, S.m, r, ratio);
                 if (!(ratio <= prm.c_gd)) rep->flags |= 1;
                 std::swap(ixp, ix);
                 std::swap(ix, ixc);
@@ -480,10 +496,12 @@ int solve_impl(Solver& S, double tol, ihs_report* rep) {
                 rep->accepted_gd++;
                 accepted = true;
             } else if (p.floor > 0.0 && r <= p.floor * p.floor * r1) {
+                ihs_trace_add(ctx, IHS_EV_FLOOR, t, S.m, r, ratio);
                 rep->flags |= 2;
                 status = IHS_OK;
                 break;
             } else {
+                ihs_trace_add(ctx, IHS_EV_DOUBLE, t, S.m, r, ratio);
                 rep->rejected++;
                 const int64_t m_new = std::min<int64_t>(2 * S.m, m_cap);
                 IHS_TRY(sketch_level(S, m_new, S.level + 1));
@@ -495,10 +513,20 @@ int solve_impl(Solver& S, double tol, ihs_report* rep) {
         }
         ++t;
     }
+    if (x_prev_out)
+        IHS_CUDA_TRY(cudaMemcpyAsync(x_prev_out, S.vec[ixp], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (ix != X) {
         IHS_CUDA_TRY(cudaMemcpyAsync(S.vec[X], S.vec[ix], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
         if (S.bsub) IHS_CUDA_TRY(cudaMemcpyAsync(S.vlo[X], S.vlo[ix], vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
-        IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (st) {
+        st->grad_passes = (resume ? st->grad_passes : 0) + rep->grad_passes;
+        st->n_levels = (resume ? st->n_levels : 0) + rep->n_levels;
+        st->t = t;
+        st->level = S.level;
+        st->m = S.m;
+        st->r1 = r1;
     }
     rep->status = status;
     rep->iterations = t;
@@ -518,6 +546,7 @@ extern "C" int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n
     if (!ctx || !A || !b || !x) return IHS_EINVAL;
     if (n < 1 || d < 1 || n < d || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
     if (!(tol > 0.0)) tol = ctx->p.tol;
+    IhsRange range("ihs_solve");
     ihs_report rep;
     memset(&rep, 0, sizeof(rep));
     Solver S;
@@ -544,6 +573,45 @@ extern "C" int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n
     return st;
 }
 
+extern "C" int ihs_solve_resume(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
+                                double tol, float* x, float* x_prev, ihs_state* st_h, ihs_report* rep_h) {
+    if (!ctx || !A || !b || !x || !x_prev || !st_h) return IHS_EINVAL;
+    if (n < 1 || d < 1 || n < d || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
+    if (st_h->t < 0) return IHS_EINVAL;
+    if (st_h->t > 0) {
+        const int64_t m_cap = ctx->p.kind == IHS_SKETCH_SRHT ? next_pow2_64(n) : n;
+        if (st_h->level < 0 || st_h->level > 62 || st_h->m < 1 || st_h->m > m_cap || !(st_h->r1 > 0.0) ||
+            (st_h->m != ((int64_t)1 << st_h->level) && st_h->m != m_cap))
+            return IHS_EINVAL;
+    }
+    if (!(tol > 0.0)) tol = ctx->p.tol;
+    IhsRange range("ihs_solve_resume");
+    ihs_report rep;
+    memset(&rep, 0, sizeof(rep));
+    Solver S;
+    memset(&S, 0, sizeof(S));
+    S.ctx = ctx;
+    S.A = A;
+    S.b = b;
+    S.n = n;
+    S.d = d;
+    S.nu = nu;
+    void* ws = nullptr;
+    const size_t vb = ((size_t)d * sizeof(float) + 255) & ~(size_t)255;
+    IHS_TRY(ihs_scratch(ctx, SLOT_SOLVE, 7 * vb + 8192 * sizeof(double), &ws));
+    char* base = static_cast<char*>(ws);
+    S.vec[0] = x;
+    for (int i = 1; i < 7; ++i) S.vec[i] = reinterpret_cast<float*>(base + i * vb);
+    S.dsc = reinterpret_cast<double*>(base + 7 * vb);
+    const int st = solve_impl(S, tol, &rep, st_h, x_prev, x_prev);
+    if (rep_h) *rep_h = rep;
+    if (st == IHS_OK || st == IHS_EMAXITER) {
+        const int s2 = ihs_check_status(ctx);
+        if (s2 != IHS_OK) return s2;
+    }
+    return st;
+}
+
 // Underdetermined case (App. A.2): the controller runs on the dual
 // z* = argmin 1/2 ||A^T z||^2 + nu^2/2 ||z||^2 - b^T z, an overdetermined
 // problem with data matrix A^T (d x n) and gradient A A^T z - b + nu^2 z
@@ -551,6 +619,7 @@ extern "C" int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n
 // over the d rows of A^T.  x = A^T z at the end.
 extern "C" int ihs_solve_dual(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
                               double tol, float* x, ihs_report* rep_h) {
+    IhsRange range("ihs_solve_dual");
     if (!ctx || !A || !b || !x) return IHS_EINVAL;
     if (n < 1 || d < 1 || n > d || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
     if (!(tol > 0.0)) tol = ctx->p.tol;

@@ -50,6 +50,23 @@ class Report(ctypes.Structure):
         return [int(self.m_levels[i]) for i in range(min(self.n_levels, REPORT_MAX_LEVELS))]
 
 
+EVENT_NAMES = {0: "stop", 1: "polyak", 2: "polyak_reject", 3: "gd", 4: "gd_at_cap", 5: "double", 6: "floor"}
+
+
+class Event(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("t", ctypes.c_int32), ("m", ctypes.c_int64), ("r", ctypes.c_double),
+                ("ratio", ctypes.c_double)]
+
+    def as_tuple(self):
+        """(event name, t, m, ratio), the layout of the oracle's trace entries."""
+        return (EVENT_NAMES.get(self.kind, str(self.kind)), int(self.t), int(self.m), float(self.ratio))
+
+
+class State(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int32), ("level", ctypes.c_int32), ("m", ctypes.c_int64), ("r1", ctypes.c_double),
+                ("grad_passes", ctypes.c_int32), ("n_levels", ctypes.c_int32)]
+
+
 _vp, _i64, _i32, _u64, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
 _SIGNATURES = {
     "ihs_version": ([], ctypes.c_char_p),
@@ -68,6 +85,10 @@ _SIGNATURES = {
     "ihs_apply_hinv": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
     "ihs_grad": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
     "ihs_solve": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
+    "ihs_solve_resume": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, _vp, ctypes.POINTER(State),
+                          ctypes.POINTER(Report)], ctypes.c_int),
+    "ihs_trace_events": ([_vp, ctypes.POINTER(Event), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
+    "ihs_ctx_set_trace_file": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "ihs_solve_dual": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_cg": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i32, _i32, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_grad_noalloc": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, _vp], ctypes.c_int),
@@ -134,8 +155,21 @@ def grad_noalloc(A, b, nu, x, g, axnorm2=None, stream=None):
     allocation (scratch in a fixed device array; see include/ihs.h)."""
     import torch
 
+    dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream() if stream is None else stream
+    if stream.device.index != dev:
+        raise ValueError("the stream is on cuda:%d, the current device is cuda:%d" % (stream.device.index, dev))
+    for name, t, dtype in (("A", A, torch.float32), ("b", b, torch.float32), ("x", x, torch.float32),
+                           ("g", g, torch.float32), ("axnorm2", axnorm2, torch.float64)):
+        if t is None:
+            continue
+        if t.device.type != "cuda" or t.device.index != dev:
+            raise ValueError("%s must be on the current device cuda:%d (got %s)" % (name, dev, t.device))
+        if t.dtype != dtype:
+            raise ValueError("%s must be %s (got %s)" % (name, dtype, t.dtype))
     n, d = A.shape
+    if b.numel() != n or x.numel() != d or g.numel() != d or (axnorm2 is not None and axnorm2.numel() < 1):
+        raise ValueError("shapes: A %s, b %d, x %d, g %d" % (tuple(A.shape), b.numel(), x.numel(), g.numel()))
     _check("ihs_grad_noalloc", load().ihs_grad_noalloc(ctypes.c_void_p(stream.cuda_stream), _ptr(A), _ptr(b), n, d,
                                                        float(nu), _ptr(x), _ptr(g), _ptr(axnorm2)))
 
@@ -246,6 +280,31 @@ class Context:
         if st != IHS_OK and (st != IHS_EMAXITER or raise_on_maxiter):
             _check("ihs_solve", st)
         return rep
+
+    def solve_resume(self, A, b, nu, x, x_prev, state=None, tol=0.0):
+        """ihs_solve_resume: continue a run from `state` (None or t == 0: start
+        from x).  Returns (report, state); x and x_prev are updated in place."""
+        n, d = A.shape
+        state = State() if state is None else state
+        rep = Report()
+        st = _lib.ihs_solve_resume(self.handle, _ptr(A), _ptr(b), n, d, float(nu), float(tol), _ptr(x),
+                                   _ptr(x_prev), ctypes.byref(state), ctypes.byref(rep))
+        if st not in (IHS_OK, IHS_EMAXITER):
+            _check("ihs_solve_resume", st)
+        return rep, state
+
+    def trace(self):
+        """Decisions of the last solve as (event, t, m, ratio) tuples."""
+        count = _i32(0)
+        _check("ihs_trace_events", _lib.ihs_trace_events(self.handle, None, 0, ctypes.byref(count)))
+        buf = (Event * max(1, count.value))()
+        _check("ihs_trace_events", _lib.ihs_trace_events(self.handle, buf, count.value, ctypes.byref(count)))
+        return [buf[i].as_tuple() for i in range(count.value)]
+
+    def set_trace_file(self, path):
+        """Append each decision to `path` as a JSON line (None closes the file)."""
+        _check("ihs_ctx_set_trace_file",
+               _lib.ihs_ctx_set_trace_file(self.handle, None if path is None else str(path).encode()))
 
     def solve_dual(self, A, b, nu, x, tol=0.0, raise_on_maxiter=False):
         """Underdetermined A (n <= d): the dual iteration, x = A^T z on return."""

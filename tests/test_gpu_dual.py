@@ -7,7 +7,7 @@ import pytest
 from oracle import ihs as oracle_ihs
 from oracle import linalg
 from paper_2006_05874_gb300 import problems
-from test_gpu_solve import _schedule_matches
+from schedule_parity import assert_same_schedule
 
 pytestmark = pytest.mark.gpu
 # The dual's own stopping criterion; the primal error is up to sigma_1^2 / nu^2
@@ -34,7 +34,7 @@ def test_dual_exp_decay(ctx, torch_cuda, kind):
     xs = linalg.direct_solve_dual(A64, b.astype(np.float64), p.nu)
     assert linalg.relative_error(A64, p.nu, x, xs) <= 1e-5
     _, ref = oracle_ihs.adaptive_ihs_dual(A64, b.astype(np.float64), p.nu, kind=kind, tol=1e-8)
-    assert _schedule_matches(rep.levels(), ref, kind), (rep.levels(), ref.levels)
+    assert_same_schedule(ctx.trace(), ref.trace, kind)
 
 
 def test_dual_spectral(ctx, torch_cuda):
@@ -47,7 +47,7 @@ def test_dual_spectral(ctx, torch_cuda):
     xs = linalg.direct_solve_dual(A64, b.astype(np.float64), p.nu)
     assert linalg.relative_error(A64, p.nu, x, xs) <= 1e-5
     _, ref = oracle_ihs.adaptive_ihs_dual(A64, b.astype(np.float64), p.nu, kind="srht", tol=1e-7)
-    assert _schedule_matches(rep.levels(), ref, "srht"), (rep.levels(), ref.levels)
+    assert_same_schedule(ctx.trace(), ref.trace, "srht")
 
 
 @pytest.mark.parametrize("n,d", [(250, 3001), (37, 37), (1, 500)])

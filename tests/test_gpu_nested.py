@@ -7,7 +7,7 @@ import pytest
 from oracle import ihs as oracle_ihs
 from oracle import linalg, sketch
 from paper_2006_05874_gb300 import problems
-from test_gpu_solve import _schedule_matches
+from schedule_parity import assert_same_schedule
 
 pytestmark = pytest.mark.gpu
 
@@ -66,7 +66,7 @@ def test_nested_solve_matches_oracle(ctx, torch_cuda, kind):
     assert rep.status == 0
     assert linalg.relative_error(p.A, p.nu, x.cpu().numpy(), xs) <= 1e-5
     ref = oracle_ihs.adaptive_ihs(p.A, p.b, p.nu, kind=kind, variant="gd", tol=1e-5, nested=True)
-    assert _schedule_matches(rep.levels(), ref, kind), (rep.levels(), ref.levels)
+    assert_same_schedule(ctx.trace(), ref.trace, kind)
 
 
 def test_nested_bf16_solve_accuracy(ctx, torch_cuda):

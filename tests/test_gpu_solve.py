@@ -5,26 +5,11 @@ import numpy as np
 import pytest
 
 from oracle import ihs as oracle_ihs
-from oracle import linalg, params
+from oracle import linalg
 from paper_2006_05874_gb300 import problems
+from schedule_parity import assert_same_schedule
 
 pytestmark = pytest.mark.gpu
-
-
-def _schedule_matches(gpu_levels, ref, kind):
-    """Equal schedules, or a first difference at an oracle decision whose ratio
-    lies within 1e-3 (relative) of the threshold (a tie the arithmetic of the
-    two sides may decide differently)."""
-    if gpu_levels == ref.levels:
-        return True
-    prm = params.ihs_params(kind)
-    decisions = [e for e in ref.trace if e[0] in ("gd", "double")]
-    k = next(i for i, (a, b) in enumerate(zip(gpu_levels, ref.levels)) if a != b) if any(
-        a != b for a, b in zip(gpu_levels, ref.levels)) else min(len(gpu_levels), len(ref.levels))
-    for ev in decisions:
-        if abs(ev[3] - prm.c_gd) <= 1e-3 * prm.c_gd:
-            return True
-    return False
 
 
 @pytest.fixture(scope="module")
@@ -45,7 +30,7 @@ def test_solve_exp_decay(ctx, torch_cuda, exp_problem, kind, variant):
     err = linalg.relative_error(p.A, p.nu, x.cpu().numpy(), xs)
     assert err <= 1e-5
     ref = oracle_ihs.adaptive_ihs(p.A, p.b, p.nu, kind=kind, variant=variant, tol=1e-5)
-    assert _schedule_matches(rep.levels(), ref, kind), (rep.levels(), ref.levels)
+    assert_same_schedule(ctx.trace(), ref.trace, kind)
 
 
 def test_solve_spectral_small(ctx, torch_cuda):
@@ -58,7 +43,7 @@ def test_solve_spectral_small(ctx, torch_cuda):
     assert rep.status == 0
     assert linalg.relative_error(p.A, p.nu, x.cpu().numpy(), xs) <= 1e-5
     ref = oracle_ihs.adaptive_ihs(p.A, p.b, p.nu, kind="srht", variant="gd", tol=1e-5)
-    assert _schedule_matches(rep.levels(), ref, "srht"), (rep.levels(), ref.levels)
+    assert_same_schedule(ctx.trace(), ref.trace, "srht")
 
 
 def test_solve_warm_start_level(ctx, torch_cuda, exp_problem):
@@ -78,3 +63,69 @@ def test_solve_rejects_bad_args(ctx, torch_cuda):
     A = torch.zeros(4, 8, device="cuda")   # n < d
     with pytest.raises(ihs.IHSError):
         ctx.solve(A, torch.zeros(4, device="cuda"), 1.0, torch.zeros(8, device="cuda"))
+
+
+def test_trace_file_matches_events(ctx, torch_cuda, exp_problem, tmp_path):
+    import json
+
+    torch = torch_cuda
+    p, _ = exp_problem
+    path = tmp_path / "trace.jsonl"
+    ctx.set_params(kind="srht", variant="polyak", tol=1e-5, m_init=1)
+    ctx.set_trace_file(path)
+    try:
+        x = torch.zeros(p.d, device="cuda")
+        ctx.solve(torch.from_numpy(p.A).cuda(), torch.from_numpy(p.b).cuda(), p.nu, x)
+    finally:
+        ctx.set_trace_file(None)
+    lines = [json.loads(line) for line in path.read_text().splitlines()]
+    events = ctx.trace()
+    assert len(lines) == len(events) > 0
+    for rec, ev in zip(lines, events):
+        assert (rec["event"], rec["t"], rec["m"]) == ev[:3]
+        assert rec["ratio"] == ev[3]
+    assert events[-1][0] == "stop" and events[-1][3] <= 1.0
+
+
+@pytest.mark.parametrize("variant", ["gd", "polyak"])
+def test_resume_reproduces_uninterrupted_run(ctx, torch_cuda, exp_problem, variant):
+    """A run stopped by max_iter and resumed from its state takes the same
+    decisions and returns the same bits as one uninterrupted run (keyed sketches,
+    deterministic kernels)."""
+    torch = torch_cuda
+    p, xs = exp_problem
+    A, b = torch.from_numpy(p.A).cuda(), torch.from_numpy(p.b).cuda()
+    ctx.set_params(kind="srht", variant=variant, tol=1e-5, m_init=1, max_iter=500)
+    x_full = torch.zeros(p.d, device="cuda")
+    rep_full = ctx.solve(A, b, p.nu, x_full)
+    full_trace = ctx.trace()
+    assert rep_full.status == 0 and rep_full.iterations > 4
+
+    x = torch.zeros(p.d, device="cuda")
+    x_prev = torch.zeros(p.d, device="cuda")
+    state, pieces = None, []
+    for limit in (2, rep_full.iterations // 2 + 1, 500):
+        ctx.set_params(kind="srht", variant=variant, tol=1e-5, m_init=1, max_iter=limit)
+        rep, state = ctx.solve_resume(A, b, p.nu, x, x_prev, state)
+        pieces += ctx.trace()
+    assert rep.status == 0
+    assert state.t == rep_full.iterations and state.m == rep_full.m_final
+    assert state.n_levels >= rep_full.n_levels
+    assert pieces == full_trace
+    assert torch.equal(x, x_full)
+    assert linalg.relative_error(p.A, p.nu, x.cpu().numpy(), xs) <= 1e-5
+
+
+def test_resume_rejects_inconsistent_state(ctx, torch_cuda):
+    from paper_2006_05874_gb300 import ihs
+
+    torch = torch_cuda
+    A = torch.zeros(64, 8, device="cuda")
+    b = torch.zeros(64, device="cuda")
+    x, xp = torch.zeros(8, device="cuda"), torch.zeros(8, device="cuda")
+    bad = ihs.State(t=3, level=2, m=8, r1=1.0)          # m != 2^level
+    with pytest.raises(ihs.IHSError):
+        ctx.solve_resume(A, b, 0.5, x, xp, bad)
+    bad = ihs.State(t=3, level=2, m=4, r1=0.0)          # r1 must be positive
+    with pytest.raises(ihs.IHSError):
+        ctx.solve_resume(A, b, 0.5, x, xp, bad)
