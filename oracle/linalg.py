@@ -86,6 +86,24 @@ def direct_solve(A, b, nu):
     return x
 
 
+def direct_solve_path(A, bs, nus):
+    """x*_k = (A^T A + nu_k^2 I)^{-1} A^T b_k for a regularisation path on one A
+    (Sec. 5's nu-paths): the float64 Gram A^T A is formed once, then each point
+    is the Cholesky solve of Eq. 1's normal equations with one refinement step,
+    exactly as `direct_solve` does for a single point."""
+    d = A.shape[1]
+    G = gram_blocked(A)
+    out = []
+    for b, nu in zip(bs, nus):
+        H = G + nu * nu * np.eye(d)
+        rhs = atb_blocked(A, b)
+        L = np.linalg.cholesky(H)
+        x = _chol_solve(L, rhs)
+        x = x + _chol_solve(L, rhs - H @ x)
+        out.append(x)
+    return out
+
+
 def _chol_solve(L, v):
     import scipy.linalg as sla
 

@@ -178,7 +178,14 @@ int ihs_check_status(ihs_ctx* c) {
     IHS_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (h) {
         IHS_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
-        if (h & IHS_DEV_TIMEOUT) return IHS_ETIMEOUT;
+        if (h & IHS_DEV_TIMEOUT) {
+            // a fused apply that gave up leaves its barrier counter and last-CTA
+            // ticket (words 32..41) behind: start both again from zero
+            IHS_CUDA_TRY(cudaMemsetAsync(c->d_status + 32, 0, 10 * sizeof(unsigned), c->stream));
+            IHS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+            c->apply_epoch = 0;
+            return IHS_ETIMEOUT;
+        }
         if (h & IHS_DEV_NOTPD) return IHS_ENOTPD;
     }
     IHS_CUDA_TRY(cudaGetLastError());

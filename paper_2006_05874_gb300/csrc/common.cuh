@@ -73,6 +73,7 @@ struct ihs_ctx {
     void* lanes;             // batched solves: sub-contexts, streams and memory pool kept across calls
     int no_coop;             // 1: factorisations use the multi-launch form (many run side by side)
     void* trace;             // decision log of the last solve (api.cu), NULL until first use
+    uint64_t apply_epoch;    // arrivals so far on the fused apply's grid-barrier counter
 };
 
 // Decision log of the controller (api.cu): cleared at the start of a solve,
@@ -104,7 +105,19 @@ struct ihs_factor {
     float* XT;            // its transpose (upper)
     double* work;         // apply scratch vectors and reduction slots
     int owned;            // 1: the buffers above are this handle's own allocations
+    // fused apply (one cooperative launch, apply.cu); fused == 0 takes the
+    // multi-launch apply and leaves the three buffers below unset
+    int fused;
+    float2* Kdf;          // K = nu^2 I + SA SA^T (or SA^T SA + nu^2 I), k x k, both triangles, double-float
+    float* SAT;           // (SA)^T, d x m FP32 (Woodbury form only)
+    float2* Y;            // four partial-sum buffers of apply_partials(k, m, d) pairs each
 };
+
+// Fused apply (apply.cu).
+bool ihs_apply_fused_ok(int64_t k, int64_t m, int64_t d);
+size_t ihs_apply_partials(int64_t k, int64_t m, int64_t d);   // float2 entries per partial buffer
+int ihs_apply_prepare(ihs_ctx* ctx, ihs_factor_t* F);          // Kdf (before the Cholesky) and SAT
+int ihs_apply_fused(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt, double* d_r);
 
 int ihs_scratch(ihs_ctx* ctx, int slot, size_t bytes, void** out);
 
@@ -274,6 +287,26 @@ struct Acc2 {
         lo = __fadd_rn(lo, __fadd_rn(e, l2));
     }
 };
+
+// v as hi + lo with integer operations (no FP64 instruction: conversions from
+// double run at the FP64 rate): hi keeps the sign, the exponent and the top 23
+// stored mantissa bits (truncated), lo the remaining 29 bits rounded to 24,
+// 48 bits in all.  Magnitudes outside [2^-74, 2^127] take the FP64 conversion.
+__device__ __forceinline__ float2 df_split(double v) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const unsigned h32 = (unsigned)(bits >> 32), l32 = (unsigned)bits;
+    const int e32 = (int)((h32 >> 20) & 0x7FFu) - 1023 + 127;   // binary32 biased exponent of v
+    if (e32 < 53 || e32 > 254) {
+        if (v == 0.0) return make_float2(0.f, 0.f);
+        const float hi = __double2float_rn(v);
+        return make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+    const unsigned sign = h32 & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((unsigned)e32 << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
+    const float scale = __uint_as_float((unsigned)(e32 - 52) << 23);   // 2^(exponent of v - 52)
+    const float lo = __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale);
+    return make_float2(hi, sign ? -lo : lo);
+}
 
 __device__ __forceinline__ Acc2 acc2_shfl_xor(Acc2 a, int mask) {
     Acc2 o;

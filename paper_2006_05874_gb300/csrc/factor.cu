@@ -425,26 +425,6 @@ __device__ __forceinline__ void df_fma_acc(Acc2& acc, float2 a, float2 b) {
     acc.lo = __fadd_rn(acc.lo, __fadd_rn(__fadd_rn(e, cross), es));
 }
 
-// v as hi + lo with integer operations (no FP64 instruction: conversions from
-// double run at the FP64 rate): hi keeps the sign, the exponent and the top 23
-// stored mantissa bits (truncated), lo the remaining 29 bits rounded to 24,
-// 48 bits in all.  Magnitudes outside [2^-74, 2^127] take the FP64 conversion.
-__device__ __forceinline__ float2 df_split(double v) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-    const unsigned h32 = (unsigned)(bits >> 32), l32 = (unsigned)bits;
-    const int e32 = (int)((h32 >> 20) & 0x7FFu) - 1023 + 127;   // binary32 biased exponent of v
-    if (e32 < 53 || e32 > 254) {
-        if (v == 0.0) return make_float2(0.f, 0.f);
-        const float hi = __double2float_rn(v);
-        return make_float2(hi, __double2float_rn(v - (double)hi));
-    }
-    const unsigned sign = h32 & 0x80000000u;
-    const float hi = __uint_as_float(sign | ((unsigned)e32 << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
-    const float scale = __uint_as_float((unsigned)(e32 - 52) << 23);   // 2^(exponent of v - 52)
-    const float lo = __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale);
-    return make_float2(hi, sign ? -lo : lo);
-}
-
 // x y for double-float operands, renormalised: about 2^-47 relative
 __device__ __forceinline__ float2 df_mul2(float2 x, float2 y) {
     float p, e;
@@ -464,10 +444,130 @@ __device__ __forceinline__ float2 df_fnms(float2 k, float2 x, float2 y) {
     return make_float2(t, __fsub_rn(e, __fsub_rn(t, s)));
 }
 
+// 1 / sqrt(p) for a positive double-float p: the single-precision estimate
+// rsqrtf(p.hi) refined by two Newton-Raphson steps for f(y) = 1/y^2 - p,
+// y <- y + y (1 - p y^2) / 2, with the residual 1 - p y^2 formed in
+// double-float (each step squares the relative error: 2^-23 -> 2^-45 ->
+// the double-float rounding level).
+__device__ __forceinline__ float2 df_rsqrt(float2 p) {
+    float2 y = make_float2(rsqrtf(p.x), 0.f);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const float2 q = df_mul2(p, df_mul2(y, y));   // p y^2, close to 1
+        float s, e;
+        two_sum(1.0f, -q.x, s, e);
+        const float r = __fadd_rn(s, __fsub_rn(e, q.y));   // 1 - p y^2 (small)
+        const float h = __fmul_rn(__fmul_rn(0.5f, y.x), r);
+        float hi, lo;
+        two_sum(y.x, h, hi, lo);
+        y = make_float2(hi, __fadd_rn(lo, __fadd_rn(y.y, __fmul_rn(__fmul_rn(0.5f, y.y), r))));
+    }
+    return y;
+}
+
+// The diagonal block [j0, j0 + nb) of the persistent Cholesky, in place, in
+// double-float arithmetic on the FP32 pipes (about 2^-46 relative; the FP64
+// pipe runs at a small fraction of the FP32 rate and a dependent FP64
+// reciprocal square root costs hundreds of nanoseconds, which the 32-pivot
+// chain would pay 32 times per block step).  Same schedule as chol_potrf:
+// thread 0 runs the pivot chain with one column of look-ahead while threads
+// 32..255 apply column j to the packed trailing entries; columns stay
+// unscaled until a final pass forms L_rc = a_rc / sqrt(p_c).  L goes back to
+// Kmat in FP64, 1 / L_cc to Wd[0..CB).  Rows and columns >= nb are padded with
+// the identity; a non-positive or non-finite pivot sets IHS_DEV_NOTPD (and is
+// replaced by 1).
+struct CholSmemDf {
+    float2 a[CB][CB + 1];
+    float2 dinv[CB];
+    int bad;
+};
+
+__device__ void chol_potrf_df(CholSmemDf& S, double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
+                              double* __restrict__ Wd, unsigned* status) {
+    static_assert(CB == 32, "the packed entry mapping assumes CB = 32 and 256 threads");
+    const int tid = threadIdx.x;
+    if (tid == 0) S.bad = 0;
+    for (int e = tid; e < CB * CB; e += 256) {
+        const int r = e / CB, c = e % CB;
+        float2 v = make_float2(0.f, 0.f);
+        if (c <= r) {
+            if (r < nb) v = c < nb ? df_split(__ldcg(Kmat + (j0 + r) * k + j0 + c)) : make_float2(0.f, 0.f);
+            else v = make_float2(r == c ? 1.f : 0.f, 0.f);
+        }
+        S.a[r][c] = v;
+    }
+    int er[3], ec[3], ei[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int e = tid - 32 + 224 * q;
+        ei[q] = e;
+        int g = 0;
+        if (e >= 0 && e < CB * (CB + 1) / 2) {
+            g = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+            while (g * (g + 1) / 2 > e) --g;
+            while ((g + 1) * (g + 2) / 2 <= e) ++g;
+        } else {
+            ei[q] = 1 << 20;   // never active
+        }
+        ec[q] = CB - 1 - g;
+        er[q] = ec[q] + (e - g * (g + 1) / 2);
+    }
+    __syncthreads();
+    float2 ri = make_float2(0.f, 0.f);   // thread 0: 1 / sqrt(p_j) of the current step
+    if (tid == 0) {
+        float2 p = S.a[0][0];
+        if (!(p.x > 0.f) || !isfinite(p.x)) {
+            S.bad = 1;
+            p = make_float2(1.f, 0.f);
+            S.a[0][0] = p;
+        }
+        ri = df_rsqrt(p);
+        S.dinv[0] = ri;
+    }
+    __syncthreads();
+    for (int j = 0; j < CB - 1; ++j) {
+        if (tid == 0) {
+            const float2 l = df_mul2(S.a[j + 1][j], ri);
+            float2 p = df_fnms(S.a[j + 1][j + 1], l, l);
+            if (!(p.x > 0.f) || !isfinite(p.x)) {
+                S.bad = 1;
+                p = make_float2(1.f, 0.f);
+            }
+            S.a[j + 1][j + 1] = p;
+            ri = df_rsqrt(p);
+            S.dinv[j + 1] = ri;
+        } else if (tid >= 32) {
+            const int active = (CB - 1 - j) * (CB - j) / 2;
+            const int diag_next = (CB - 2 - j) * (CB - 1 - j) / 2;   // entry (j+1, j+1): thread 0's
+            if (tid - 32 < active) {
+                const float2 rj = S.dinv[j];
+                const float2 ip2 = df_mul2(rj, rj);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (ei[q] < active && ei[q] != diag_next) {
+                        const int r = er[q], c = ec[q];
+                        S.a[r][c] = df_fnms(S.a[r][c], df_mul2(S.a[r][j], ip2), S.a[c][j]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < CB * CB; e += 256) {
+        const int r = e / CB, c = e % CB;
+        if (c <= r && r < nb && c < nb) {
+            const float2 l = df_mul2(S.a[r][c], S.dinv[c]);
+            Kmat[(j0 + r) * k + j0 + c] = (double)l.x + (double)l.y;
+        }
+    }
+    if (tid < CB) Wd[tid] = tid < nb ? (double)S.dinv[tid].x + (double)S.dinv[tid].y : 0.0;   // 1 / L_cc
+    if (tid == 0 && S.bad) atomicOr(status, IHS_DEV_NOTPD);
+}
+
 __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Kmat, int64_t k,
                                                          double* __restrict__ Wall, unsigned* bar,
                                                          unsigned* status) {
-    __shared__ CholSmem S;
+    __shared__ CholSmemDf S;
     // operands of the panel, column and trailing products as double-float pairs
     __shared__ float2 fa[CB][CB + 1];
     __shared__ float2 fb[CB][CB + 1];
@@ -483,7 +583,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
         const int64_t j0 = jb * CB;
         const int nb = (int)min((int64_t)CB, k - j0);
         // ---- phase P: diagonal block jb | rest of the update by panel jb-1
-        if (cta == 0) chol_potrf<false>(S, Kmat, k, j0, nb, Wall + jb * CB, status);
+        if (cta == 0) chol_potrf_df(S, Kmat, k, j0, nb, Wall + jb * CB, status);
         if (jb > 0 && (cta > 0 || G == 1)) {
             const int64_t j1 = j0;                 // trailing region starts at block jb
             const int64_t Tr = ceil_div64(k - j1, CB);
@@ -599,15 +699,16 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
         if (!grid_sync_bounded(bar, nbar, status)) return;
         const int64_t rest = k - j0 - nb;
         if (rest <= 0) break;
-        // ---- phase N: panel jb = K L_jj^{-T} by forward substitution, 8 rows per
-        // work item: warp w solves row r0 + w, lane c holds column c
+        // ---- phase N: panel jb = K L_jj^{-T} by forward substitution, 16 rows per
+        // work item: warp w solves rows r0 + w and r0 + 8 + w side by side (two
+        // independent chains), lane c holds column c
         {
             const double* dinv = Wall + jb * CB;   // 1 / L_cc
-            const int64_t items = ceil_div64(rest, 8);
+            const int64_t items = ceil_div64(rest, 16);
             const int lane = tid & 31, wq = tid >> 5;
             bool loaded = false;
             for (int64_t it = cta; it < items; it += G) {
-                const int64_t r0 = j0 + nb + it * 8;
+                const int64_t r0 = j0 + nb + it * 16;
                 if (!loaded) {
                     // L_jj and 1 / L_cc as double-float pairs, once per step
                     for (int e = tid; e < CB * CB; e += 256) {
@@ -618,50 +719,70 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                     __syncthreads();
                     loaded = true;
                 }
-                // substitution in double-float (FP32 latencies on the dependent chain)
-                const int64_t r = r0 + wq;
-                float2 kv = df_split((r < k && lane < nb) ? __ldcg(Kmat + r * k + j0 + lane) : 0.0);
-                float2 x = make_float2(0.f, 0.f);
+                // substitution in double-float (FP32 latencies on the dependent chains)
+                const int64_t ra = r0 + wq, rb = r0 + 8 + wq;
+                float2 ka = df_split((ra < k && lane < nb) ? __ldcg(Kmat + ra * k + j0 + lane) : 0.0);
+                float2 kb = df_split((rb < k && lane < nb) ? __ldcg(Kmat + rb * k + j0 + lane) : 0.0);
+                float2 xa = make_float2(0.f, 0.f), xb = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < CB; ++c) {
-                    const float2 kc = make_float2(__shfl_sync(0xffffffffu, kv.x, c), __shfl_sync(0xffffffffu, kv.y, c));
-                    const float2 xc = df_mul2(kc, fb[0][c]);
-                    if (lane == c) x = xc;
-                    else if (lane > c) kv = df_fnms(kv, xc, fa[lane][c]);
+                    const float2 kca = make_float2(__shfl_sync(0xffffffffu, ka.x, c), __shfl_sync(0xffffffffu, ka.y, c));
+                    const float2 kcb = make_float2(__shfl_sync(0xffffffffu, kb.x, c), __shfl_sync(0xffffffffu, kb.y, c));
+                    const float2 dc = fb[0][c];
+                    const float2 xca = df_mul2(kca, dc);
+                    const float2 xcb = df_mul2(kcb, dc);
+                    if (lane == c) {
+                        xa = xca;
+                        xb = xcb;
+                    } else if (lane > c) {
+                        const float2 lc = fa[lane][c];
+                        ka = df_fnms(ka, xca, lc);
+                        kb = df_fnms(kb, xcb, lc);
+                    }
                 }
-                if (r < k && lane < nb) Kmat[r * k + j0 + lane] = (double)x.x + (double)x.y;
-                if (r < k) Pdf[r * CB + lane] = x;   // 0 for lanes >= nb
+                if (ra < k && lane < nb) Kmat[ra * k + j0 + lane] = (double)xa.x + (double)xa.y;
+                if (ra < k) Pdf[ra * CB + lane] = xa;   // 0 for lanes >= nb
+                if (rb < k && lane < nb) Kmat[rb * k + j0 + lane] = (double)xb.x + (double)xb.y;
+                if (rb < k) Pdf[rb * CB + lane] = xb;
             }
         }
         if (!grid_sync_bounded(bar, nbar, status)) return;
-        // ---- phase S: column block jb+1 updated by panel jb
+        // ---- phase S: column block jb+1 updated by panel jb, 16 rows per work
+        // item (thread (ty, tx) takes rows ty and ty + 8 of the item, column tx)
         {
             const int64_t j1 = j0 + nb;
             const int ncol = (int)min((int64_t)CB, k - j1);
-            const int64_t items = ceil_div64(k - j1, 8);
+            const int64_t items = ceil_div64(k - j1, 16);
             for (int64_t it = cta; it < items; it += G) {
-                const int64_t r0 = j1 + it * 8;
+                const int64_t r0 = j1 + it * 16;
                 __syncthreads();
                 for (int e = tid; e < CB * CB; e += 256) {
                     const int c = e / CB, q = e % CB;
                     fb[c][q] = c < ncol ? __ldcg(Pdf + (j1 + c) * CB + q) : make_float2(0.f, 0.f);
                 }
-                {
-                    const int r = tid / CB, q = tid % CB;
+                for (int e = tid; e < 16 * CB; e += 256) {
+                    const int r = e / CB, q = e % CB;
                     fa[r][q] = r0 + r < k ? __ldcg(Pdf + (r0 + r) * CB + q) : make_float2(0.f, 0.f);
                 }
                 __syncthreads();
                 const int tx = tid % CB, ty = tid / CB;
-                Acc2 acc0{0.f, 0.f}, acc1{0.f, 0.f};
+                Acc2 a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f};
 #pragma unroll
                 for (int q = 0; q < CB; q += 2) {
-                    df_fma_acc(acc0, fa[ty][q], fb[tx][q]);
-                    df_fma_acc(acc1, fa[ty][q + 1], fb[tx][q + 1]);
+                    const float2 f0 = fb[tx][q], f1 = fb[tx][q + 1];
+                    df_fma_acc(a0, fa[ty][q], f0);
+                    df_fma_acc(a1, fa[ty][q + 1], f1);
+                    df_fma_acc(b0, fa[ty + 8][q], f0);
+                    df_fma_acc(b1, fa[ty + 8][q + 1], f1);
                 }
-                const int64_t r = r0 + ty, c = j1 + tx;
-                if (r < k && tx < ncol && c <= r)
-                    Kmat[r * k + c] = __ldcg(Kmat + r * k + c) -
-                                      (((double)acc0.hi + (double)acc0.lo) + ((double)acc1.hi + (double)acc1.lo));
+                const int64_t c = j1 + tx;
+                const int64_t ra = r0 + ty, rb = r0 + 8 + ty;
+                if (ra < k && tx < ncol && c <= ra)
+                    Kmat[ra * k + c] = __ldcg(Kmat + ra * k + c) -
+                                       (((double)a0.hi + (double)a0.lo) + ((double)a1.hi + (double)a1.lo));
+                if (rb < k && tx < ncol && c <= rb)
+                    Kmat[rb * k + c] = __ldcg(Kmat + rb * k + c) -
+                                       (((double)b0.hi + (double)b0.lo) + ((double)b1.hi + (double)b1.lo));
             }
         }
         if (!grid_sync_bounded(bar, nbar, status)) return;
@@ -974,6 +1095,8 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
             IHS_LAUNCH_CHECK();
         }
     }
+    // the fused apply's copies of K (before the Cholesky overwrites it) and SA^T
+    IHS_TRY(ihs_apply_prepare(ctx, F));
     // Blocked right-looking Cholesky with one step of look-ahead: on the main
     // stream, diagonal block jb, its panel and the update of block column jb+1;
     // on the auxiliary stream, the rest of the trailing update of step jb,
@@ -1065,6 +1188,7 @@ inverse:
 // (K u = nu^2 u + SA (SA^T u), or SA^T (SA u) + nu^2 u); vectors and dot
 // products are double-float (binary32 pairs with compensated sums).
 int ihs_apply_enqueue(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt, double* d_r) {
+    if (F->fused) return ihs_apply_fused(ctx, F, g, gt, d_r);
     cudaStream_t s = ctx->stream;
     const int64_t k = F->k, d = F->d, m = F->m;
     const int64_t mx = std::max(m, d);
@@ -1143,8 +1267,46 @@ static size_t factor_work_doubles(int64_t k, int64_t m, int64_t d) {
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t* F) {
-    if (!ctx || !SA || !F || m < 1 || d < 1 || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
+// Byte offsets of a factor's buffers in one block: K/L (FP64 k x k), the
+// diagonal-block inverses W, X = L^{-1} and X^T (FP32), the multi-launch
+// apply's work area, and for the fused apply the double-float K, SA^T and
+// four partial-sum buffers (+ one FP64 slot per CTA).
+struct FactorLayout {
+    size_t L, W, X, XT, work, Kdf, SAT, Y, total;
+};
+
+static FactorLayout factor_layout(int64_t k, int64_t m, int64_t d, bool fused, int sm_count) {
+    const int64_t T = ceil_div64(k, FB);
+    const size_t kk = (size_t)k * k;
+    FactorLayout l;
+    size_t o = 0;
+    l.L = o;
+    o += align256(kk * sizeof(double));
+    l.W = o;
+    o += align256((size_t)T * FB * FB * sizeof(double));
+    l.X = o;
+    o += align256(kk * sizeof(float));
+    l.XT = o;
+    o += align256(kk * sizeof(float));
+    l.work = o;
+    o += align256(factor_work_doubles(k, m, d) * sizeof(double));
+    l.Kdf = l.SAT = l.Y = 0;
+    if (fused) {
+        l.Kdf = o;
+        o += align256(kk * sizeof(float2));
+        if (m < d) {
+            l.SAT = o;
+            o += align256((size_t)m * d * sizeof(float));
+        }
+        l.Y = o;
+        o += align256((4 * ihs_apply_partials(k, m, d)) * sizeof(float2) + (size_t)sm_count * sizeof(double));
+    }
+    l.total = o;
+    return l;
+}
+
+static void factor_init(ihs_factor_t* F, ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, int owned,
+                        bool allow_fused) {
     memset(F, 0, sizeof(*F));
     F->ctx = ctx;
     F->SA = SA;
@@ -1153,20 +1315,30 @@ int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, doub
     F->nu = nu;
     F->woodbury = m < d ? 1 : 0;
     F->k = F->woodbury ? m : d;
-    F->owned = 0;
-    const int64_t k = F->k;
-    const int64_t T = ceil_div64(k, FB);
-    const size_t kk = (size_t)k * k;
-    const size_t bL = align256(kk * sizeof(double)), bW = align256((size_t)T * FB * FB * sizeof(double));
-    const size_t bX = align256(kk * sizeof(float)), bwork = align256(factor_work_doubles(k, m, d) * sizeof(double));
+    F->owned = owned;
+    F->fused = (allow_fused && !ctx->no_coop && ((uintptr_t)SA % 16) == 0 && ihs_apply_fused_ok(F->k, m, d)) ? 1 : 0;
+}
+
+static void factor_bind(ihs_factor_t* F, char* base, const FactorLayout& l) {
+    F->L = reinterpret_cast<double*>(base + l.L);
+    F->W = reinterpret_cast<double*>(base + l.W);
+    F->X = reinterpret_cast<float*>(base + l.X);
+    F->XT = reinterpret_cast<float*>(base + l.XT);
+    F->work = reinterpret_cast<double*>(base + l.work);
+    if (F->fused) {
+        F->Kdf = reinterpret_cast<float2*>(base + l.Kdf);
+        F->SAT = F->woodbury ? reinterpret_cast<float*>(base + l.SAT) : nullptr;
+        F->Y = reinterpret_cast<float2*>(base + l.Y);
+    }
+}
+
+int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t* F) {
+    if (!ctx || !SA || !F || m < 1 || d < 1 || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
+    factor_init(F, ctx, SA, m, d, nu, 0, true);
+    const FactorLayout l = factor_layout(F->k, m, d, F->fused, ctx->sm_count);
     void* ws = nullptr;
-    IHS_TRY(ihs_scratch(ctx, SLOT_FACTOR, bL + bW + 2 * bX + bwork, &ws));
-    char* base = static_cast<char*>(ws);
-    F->L = reinterpret_cast<double*>(base);
-    F->W = reinterpret_cast<double*>(base + bL);
-    F->X = reinterpret_cast<float*>(base + bL + bW);
-    F->XT = reinterpret_cast<float*>(base + bL + bW + bX);
-    F->work = reinterpret_cast<double*>(base + bL + bW + 2 * bX);
+    IHS_TRY(ihs_scratch(ctx, SLOT_FACTOR, l.total, &ws));
+    factor_bind(F, static_cast<char*>(ws), l);
     return ihs_factor_build(ctx, F);
 }
 
@@ -1175,60 +1347,34 @@ int ihs_factor_alloc(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double
     *out = nullptr;
     ihs_factor_t* F = new (std::nothrow) ihs_factor_t;
     if (!F) return IHS_ENOMEM;
-    memset(F, 0, sizeof(*F));
-    F->ctx = ctx;
-    F->SA = SA;
-    F->m = m;
-    F->d = d;
-    F->nu = nu;
-    F->woodbury = m < d ? 1 : 0;
-    F->k = F->woodbury ? m : d;
-    F->owned = 1;
-    const int64_t k = F->k;
-    const int64_t T = ceil_div64(k, FB);
-    const size_t kk = (size_t)k * k;
-    if (cudaMalloc(&F->L, kk * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&F->W, (size_t)T * FB * FB * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&F->X, kk * sizeof(float)) != cudaSuccess || cudaMalloc(&F->XT, kk * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&F->work, factor_work_doubles(k, m, d) * sizeof(double)) != cudaSuccess) {
+    factor_init(F, ctx, SA, m, d, nu, 1, true);
+    const FactorLayout l = factor_layout(F->k, m, d, F->fused, ctx->sm_count);
+    void* base = nullptr;
+    if (cudaMalloc(&base, l.total) != cudaSuccess) {
         cudaGetLastError();
-        ihs_factor_destroy(F);
+        delete F;
         return IHS_ENOMEM;
     }
+    factor_bind(F, static_cast<char*>(base), l);
     *out = F;
     return IHS_OK;
 }
 
 // Factor storage in one block from a stream-ordered memory pool, allocated
-// on ctx's stream (owned = 2; release with ihs_factor_release_pool).
+// on ctx's stream (owned = 2; release with ihs_factor_release_pool).  These
+// factors serve contexts that run many solves side by side and take the
+// multi-launch apply.
 int ihs_factor_alloc_pool(ihs_ctx* ctx, cudaMemPool_t pool, const float* SA, int64_t m, int64_t d, double nu,
                           ihs_factor_t* F) {
     if (!ctx || !SA || !F || m < 1 || d < 1 || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
-    memset(F, 0, sizeof(*F));
-    F->ctx = ctx;
-    F->SA = SA;
-    F->m = m;
-    F->d = d;
-    F->nu = nu;
-    F->woodbury = m < d ? 1 : 0;
-    F->k = F->woodbury ? m : d;
-    F->owned = 2;
-    const int64_t k = F->k;
-    const int64_t T = ceil_div64(k, FB);
-    const size_t kk = (size_t)k * k;
-    const size_t bL = align256(kk * sizeof(double)), bW = align256((size_t)T * FB * FB * sizeof(double));
-    const size_t bX = align256(kk * sizeof(float)), bwork = align256(factor_work_doubles(k, m, d) * sizeof(double));
+    factor_init(F, ctx, SA, m, d, nu, 2, false);
+    const FactorLayout l = factor_layout(F->k, m, d, false, ctx->sm_count);
     void* base = nullptr;
-    if (cudaMallocFromPoolAsync(&base, bL + bW + 2 * bX + bwork, pool, ctx->stream) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&base, l.total, pool, ctx->stream) != cudaSuccess) {
         cudaGetLastError();
         return IHS_ENOMEM;
     }
-    char* b = static_cast<char*>(base);
-    F->L = reinterpret_cast<double*>(b);
-    F->W = reinterpret_cast<double*>(b + bL);
-    F->X = reinterpret_cast<float*>(b + bL + bW);
-    F->XT = reinterpret_cast<float*>(b + bL + bW + bX);
-    F->work = reinterpret_cast<double*>(b + bL + bW + 2 * bX);
+    factor_bind(F, static_cast<char*>(base), l);
     return IHS_OK;
 }
 
@@ -1256,11 +1402,7 @@ extern "C" int ihs_factor_destroy(ihs_factor_t* F) {
     if (!F) return IHS_OK;
     if (F->owned != 1) return IHS_EINVAL;   // scratch- or pool-backed factors are released by their owner
     if (F->ctx) cudaStreamSynchronize(F->ctx->stream);
-    if (F->L) cudaFree(F->L);
-    if (F->W) cudaFree(F->W);
-    if (F->X) cudaFree(F->X);
-    if (F->XT) cudaFree(F->XT);
-    if (F->work) cudaFree(F->work);
+    if (F->L) cudaFree(F->L);   // the start of the factor's one block
     delete F;
     return IHS_OK;
 }

@@ -566,7 +566,8 @@ extern "C" int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n
     S.dsc = reinterpret_cast<double*>(base + 7 * vb);
     const int st = solve_impl(S, tol, &rep);
     if (rep_h) *rep_h = rep;
-    if (st == IHS_OK || st == IHS_EMAXITER) {
+    if (st == IHS_OK || st == IHS_EMAXITER || st == IHS_ENONFINITE) {
+        // a device wait that gave up poisons r (non-finite): report the cause
         const int s2 = ihs_check_status(ctx);
         if (s2 != IHS_OK) return s2;
     }
@@ -605,7 +606,8 @@ extern "C" int ihs_solve_resume(ihs_ctx* ctx, const float* A, const float* b, in
     S.dsc = reinterpret_cast<double*>(base + 7 * vb);
     const int st = solve_impl(S, tol, &rep, st_h, x_prev, x_prev);
     if (rep_h) *rep_h = rep;
-    if (st == IHS_OK || st == IHS_EMAXITER) {
+    if (st == IHS_OK || st == IHS_EMAXITER || st == IHS_ENONFINITE) {
+        // a device wait that gave up poisons r (non-finite): report the cause
         const int s2 = ihs_check_status(ctx);
         if (s2 != IHS_OK) return s2;
     }

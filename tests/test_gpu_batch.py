@@ -145,3 +145,43 @@ def test_batch_per_problem_initial_sizes(ctx, torch_cuda):
         assert linalg.relative_error(A, nu, x.cpu().numpy(), linalg.direct_solve(A, b, nu)) <= 1e-5
     with pytest.raises(Exception):
         ctx.solve_batched(dev[:1], m_init=[3])
+
+
+def test_batch_config4_scale_sample(ctx, torch_cuda):
+    """At the batched workload's own scale: a 32-point ridge path on one
+    262144 x 1024 A (sigma_j = j^-1/2, nu log-spaced over the workload's
+    1e-4 .. 1e1, every other point of its 64) plus 32 independent Gaussian-entry
+    problems from its recipe (n ~ U{2^10..2^14}, d ~ U{32..512}, nu = 1), in one
+    batch; every one of the 64 solutions against the FP64 direct solve."""
+    torch = torch_cuda
+    ctx.set_params(kind="srht", variant="gd", tol=1e-5, m_init=1, max_iter=1000)
+    n, d = 262144, 1024
+    p = problems.spectral(n, d, sigma=np.arange(1, d + 1) ** -0.5, nu=1.0, seed=41, device="cuda")
+    nus = np.logspace(-4, 1, 64)[::2]
+    rng = np.random.default_rng(41)
+    A64 = p.A.astype(np.float64)
+    bs = [(A64 @ rng.standard_normal(d) + 0.01 * rng.standard_normal(n)).astype(np.float32) for _ in nus]
+    ind = []
+    for _ in range(32):
+        nn = int(rng.integers(1 << 10, (1 << 14) + 1))
+        dd = int(rng.integers(32, 513))
+        A = rng.standard_normal((nn, dd)).astype(np.float32)
+        b = (A @ rng.standard_normal(dd) + 0.1 * rng.standard_normal(nn)).astype(np.float32)
+        ind.append((A, b, 1.0))
+    Ad = _dev(torch, p.A)
+    dev = [(Ad, _dev(torch, b), float(nu), torch.zeros(d, device="cuda")) for b, nu in zip(bs, nus)]
+    dev += [(_dev(torch, A), _dev(torch, b), nu, torch.zeros(A.shape[1], device="cuda")) for A, b, nu in ind]
+    reps = ctx.solve_batched(dev)
+    xs_path = linalg.direct_solve_path(p.A, bs, nus)
+    worst = 0.0
+    for k, (xs, nu) in enumerate(zip(xs_path, nus)):
+        assert reps[k].status == 0, (k, reps[k].status)
+        err = linalg.relative_error(p.A, nu, dev[k][3].cpu().numpy(), xs)
+        worst = max(worst, err)
+        assert err <= 1e-5, (nu, err)
+    for k, (A, b, nu) in enumerate(ind):
+        rep = reps[len(nus) + k]
+        assert rep.status == 0
+        err = linalg.relative_error(A, nu, dev[len(nus) + k][3].cpu().numpy(), linalg.direct_solve(A, b, nu))
+        worst = max(worst, err)
+        assert err <= 1e-5, (A.shape, err)

@@ -70,3 +70,37 @@ def test_factor_rejects_bad_nu(ctx, torch_cuda):
         with pytest.raises(ihs.IHSError) as e:
             ctx.factor(SA, nu)
         assert e.value.status == ihs.IHS_EINVAL
+
+
+def _spectral_sketch(m, d, seed):
+    """An m x d sketch-like matrix with the singular values of the spectral
+    workload (sigma_j = 1/j, random orthonormal right factor), so that
+    K = nu^2 I + SA SA^T (or SA^T SA + nu^2 I) is as ill-conditioned as in the
+    solver's own factorisations (kappa ~ 1/nu^2)."""
+    g = np.random.default_rng(seed)
+    k = min(m, d)
+    V, _ = np.linalg.qr(g.standard_normal((d, k)))
+    U, _ = np.linalg.qr(g.standard_normal((m, k)))
+    s = 1.0 / np.arange(1, k + 1)
+    return ((U * s) @ V.T).astype(np.float32)
+
+
+@pytest.mark.parametrize("m,d,nu", [(1024, 2048, 0.015313), (2048, 2048, 0.015313), (4096, 2048, 0.015313),
+                                    (2048, 4096, 0.035637), (8192, 4096, 0.035637)])
+def test_apply_parity_solver_sizes(ctx, torch_cuda, m, d, nu):
+    """The factor sizes the solver reaches on the spectral workload (k = min(m, d)
+    up to 2048, the persistent Cholesky's full size) and on the 1048576 x 4096
+    precision workload (k = 4096 at m = 8192), with the workloads' nu."""
+    torch = torch_cuda
+    SA = _spectral_sketch(m, d, seed=m + d)
+    g = problems.random_vector(d, seed=d + 5)
+    F = ctx.factor(torch.from_numpy(SA).cuda(), nu)
+    gt = torch.empty(d, device="cuda")
+    r = F.apply_hinv(torch.from_numpy(g).cuda(), gt)
+    F.destroy()
+    ref = linalg.WoodburyFactor(SA, nu)
+    gt_ref = ref.apply(g)
+    err = np.linalg.norm(gt.cpu().numpy() - gt_ref) / np.linalg.norm(gt_ref)
+    assert err <= 1e-6, err
+    r_ref = linalg.newton_decrement(g, gt_ref)
+    assert abs(r - r_ref) <= 1e-9 * abs(r_ref)

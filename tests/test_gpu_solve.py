@@ -129,3 +129,23 @@ def test_resume_rejects_inconsistent_state(ctx, torch_cuda):
     bad = ihs.State(t=3, level=2, m=4, r1=0.0)          # r1 must be positive
     with pytest.raises(ihs.IHSError):
         ctx.solve_resume(A, b, 0.5, x, xp, bad)
+
+
+@pytest.mark.slow
+def test_solve_spectral_full_size_schedule(ctx, torch_cuda):
+    """The headline workload itself (131072 x 2048, sigma_j = 1/j, d_e = 100):
+    SRHT gradient-IHS from m = 1, decision by decision against the oracle's
+    full-size FP64 run of the same draws, and the solution against the FP64
+    direct solve (the oracle takes about a minute here)."""
+    torch = torch_cuda
+    p = problems.spectral(131072, 2048, de_target=100.0, seed=0, device="cuda")
+    ctx.set_params(kind="srht", variant="gd", tol=1e-5, m_init=1, max_iter=500)
+    x = torch.zeros(p.d, device="cuda")
+    rep = ctx.solve(torch.from_numpy(p.A).cuda(), torch.from_numpy(p.b).cuda(), p.nu, x)
+    assert rep.status == 0
+    events = ctx.trace()
+    xs = linalg.direct_solve(p.A, p.b, p.nu)
+    assert linalg.relative_error(p.A, p.nu, x.cpu().numpy(), xs) <= 1e-5
+    ref = oracle_ihs.adaptive_ihs(p.A, p.b, p.nu, kind="srht", variant="gd", tol=1e-5)
+    assert ref.levels[-1] >= 1024
+    assert_same_schedule(events, ref.trace, "srht")

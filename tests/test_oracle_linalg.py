@@ -154,3 +154,20 @@ def test_relative_error_metric():
     xs = linalg.direct_solve(A, b, nu)
     assert linalg.relative_error(A, nu, xs, xs) == 0.0
     assert np.isclose(linalg.relative_error(A, nu, np.zeros(4), xs), 1.0)
+
+
+def test_direct_solve_path_matches_single_points():
+    """The shared-Gram path solve equals the closed form V diag(s/(s^2+nu^2)) U^T b
+    at every nu (the path's A is built from known factors, in float64)."""
+    g = np.random.default_rng(31)
+    n, d = 600, 40
+    U, _ = np.linalg.qr(g.standard_normal((n, d)))
+    V, _ = np.linalg.qr(g.standard_normal((d, d)))
+    s = np.arange(1, d + 1) ** -0.5
+    A = (U * s) @ V.T
+    nus = np.logspace(-3, 1, 5)
+    bs = [g.standard_normal(n) for _ in nus]
+    xs = linalg.direct_solve_path(A, bs, nus)
+    for x, b, nu in zip(xs, bs, nus):
+        ref = linalg.svd_solve(U, s, V, b, nu)
+        assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
