@@ -139,30 +139,59 @@ def oracle_reference_solution(p):
     return linalg.direct_solve(p.A, p.b, p.nu)
 
 
-def cpu_oracle_sample(p, budget_s=20.0):
-    """The CPU oracle's adaptive IHS (FP64, as it stands) on the first n_s rows
-    of the workload; time scaled by N_ROWS / n_s (work per pass is linear in n)."""
+def cpu_oracle_full(p):
+    """One oracle solve of the whole workload (adaptive IHS, SRHT, gradient-only,
+    FP64 numpy, as it stands) on the host cores: wall time and its schedule."""
     from oracle import ihs as oracle_ihs
 
-    n_s = 4096
-    while True:
-        t0 = time.perf_counter()
-        res = oracle_ihs.adaptive_ihs(p.A[:n_s], p.b[:n_s], p.nu, kind="srht", variant="gd", tol=TOL)
-        dt = time.perf_counter() - t0
-        if dt > budget_s / 3 or n_s * 2 > N_ROWS:
-            break
-        n_s *= 2
+    t0 = time.perf_counter()
+    res = oracle_ihs.adaptive_ihs(p.A, p.b, p.nu, kind="srht", variant="gd", tol=TOL)
+    dt = time.perf_counter() - t0
     return {
-        "value": dt * 1e3 * (N_ROWS / n_s),
+        "value": dt * 1e3,
         "unit": "ms",
         "cores": os.cpu_count(),
         "cpu_model": cpu_model(),
         "kind": "oracle",
-        "rows_sampled": n_s,
-        "sample": "adaptive IHS (SRHT, gradient-only, FP64 numpy) on the first %d of %d rows, %d gradient passes, "
-                  "levels %s; wall time %.2f s scaled by %d/%d" % (n_s, N_ROWS, res.grad_passes, res.levels, dt,
-                                                                  N_ROWS, n_s),
+        "sample": "one full-size solve: adaptive IHS (SRHT, gradient-only, FP64 numpy) on all %d x %d rows, "
+                  "%d gradient passes, levels %s, wall time %.1f s" % (p.n, p.d, res.grad_passes, res.levels, dt),
+        "grad_passes": res.grad_passes,
+        "levels": res.levels,
     }
+
+
+def oracle_component_sample(p, levels, passes):
+    """A bounded sample of the same full-size workload: the oracle's pieces
+    timed once each on the whole matrix (one gradient evaluation, one SRHT sketch
+    at the largest level, the factor at every level's size, one apply) and
+    composed by the counts of the oracle's own full-size run:
+    levels x sketch + sum of factors + passes x (gradient + apply)."""
+    from oracle import linalg
+    from oracle import sketch as SK
+
+    A64 = p.A.astype(np.float64)
+    b64 = p.b.astype(np.float64)
+    x = np.zeros(p.d)
+    t0 = time.perf_counter()
+    Av = A64 @ x
+    g = A64.T @ (Av - b64) + p.nu * p.nu * x
+    t_grad = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    SA = SK.srht_sketch(A64, levels[-1], SEED, len(levels) - 1)
+    t_sketch = time.perf_counter() - t0
+    t_factor = 0.0
+    for m in levels:
+        t0 = time.perf_counter()
+        fac = linalg.WoodburyFactor(SA[:m], p.nu)
+        t_factor += time.perf_counter() - t0
+    t0 = time.perf_counter()
+    fac.apply(g)
+    t_apply = time.perf_counter() - t0
+    total = len(levels) * t_sketch + t_factor + passes * (t_grad + t_apply)
+    return {"value": total * 1e3, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "projection from full-size pieces (%d x %d): gradient %.2f s, SRHT sketch %.2f s, factors at "
+                      "levels %s %.2f s, apply %.3f s; composed as %d sketches + factors + %d x (gradient + apply)"
+                      % (p.n, p.d, t_grad, t_sketch, levels, t_factor, t_apply, len(levels), passes)}
 
 
 def cpu_model():
@@ -184,26 +213,26 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def cpu_oracle_single_thread(p, n_s=4096):
-    """The same oracle sample with one BLAS thread (a child process started with
-    the thread counts pinned to 1), time scaled by N_ROWS / n_s."""
+def cpu_oracle_single_thread(p):
+    """The full-size oracle solve with one BLAS thread (a child process started
+    with the thread counts pinned to 1)."""
     import subprocess
     import tempfile
 
     with tempfile.TemporaryDirectory() as tmp:
-        np.save(os.path.join(tmp, "A.npy"), np.ascontiguousarray(p.A[:n_s]))
-        np.save(os.path.join(tmp, "b.npy"), np.ascontiguousarray(p.b[:n_s]))
+        np.save(os.path.join(tmp, "A.npy"), np.ascontiguousarray(p.A))
+        np.save(os.path.join(tmp, "b.npy"), np.ascontiguousarray(p.b))
         code = ("import sys, time, json, numpy as np; sys.path.insert(0, %r); from oracle import ihs; "
                 "A = np.load(%r); b = np.load(%r); t0 = time.perf_counter(); "
                 "r = ihs.adaptive_ihs(A, b, %r, kind='srht', variant='gd', tol=%r); "
                 "print(json.dumps([time.perf_counter() - t0, r.grad_passes]))"
                 % (ROOT, os.path.join(tmp, "A.npy"), os.path.join(tmp, "b.npy"), float(p.nu), TOL))
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
         dt, passes = json.loads(out.stdout.strip().splitlines()[-1])
-    return {"value": dt * 1e3 * (N_ROWS / n_s), "unit": "ms", "cores": 1,
-            "sample": "first %d of %d rows, %d gradient passes; wall time %.2f s scaled by %d/%d"
-                      % (n_s, N_ROWS, passes, dt, N_ROWS, n_s)}
+    return {"value": dt * 1e3, "unit": "ms", "cores": 1,
+            "sample": "one full-size solve (%d x %d), %d gradient passes, one BLAS thread; wall time %.1f s"
+                      % (p.n, p.d, passes, dt)}
 
 
 def sketch_throughput(ihs, A, stream, peaks):
@@ -267,28 +296,31 @@ def config1_times(ihs, stream):
 
 
 def run_reference(args):
-    """--impl reference: the CPU FP64 oracle on the host cores, same metric."""
+    """--impl reference: the CPU FP64 oracle on the host cores, same metric.
+
+    The problem is built on the host (numpy, no GPU work in this arm).  One
+    untimed full-size oracle solve gives the oracle's schedule and its wall time
+    (reported as full_size_check); each timed step is a bounded sample of the
+    same full-size workload: the oracle's pieces timed on the whole matrix and
+    composed by that schedule's counts (a projection, labelled as one)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2006_05874_gb300 import problems
 
-    # generate on CPU (no GPU work in this arm): the same construction, numpy
-    p = problems.spectral(n=N_ROWS, d=D_COLS, de_target=DE_TARGET, noise=NOISE, seed=SEED, device=None) \
-        if os.environ.get("IHS_REF_FULL") else None
-    if p is None:
-        p = make_problem("cuda" if _has_cuda() else None)
-    from oracle import ihs as oracle_ihs
-
-    for _ in range(args.warmup):  # untimed: the smallest sample, warming BLAS threads and caches
-        oracle_ihs.adaptive_ihs(p.A[:4096], p.b[:4096], p.nu, kind="srht", variant="gd", tol=TOL)
+    p = problems.spectral(n=N_ROWS, d=D_COLS, de_target=DE_TARGET, noise=NOISE, seed=SEED, device=None)
+    full = cpu_oracle_full(p)
+    for _ in range(max(0, args.warmup - 1)):   # untimed: warms BLAS threads and caches
+        oracle_component_sample(p, full["levels"][:2], 1)
     vals = []
     base = None
     for _ in range(args.steps):
-        base = cpu_oracle_sample(p, budget_s=6.0)
+        base = oracle_component_sample(p, full["levels"], full["grad_passes"])
         vals.append(base["value"])
     v = statistics.median(vals)
     base["value"] = v
+    base["cpu_model"] = cpu_model()
+    base["full_size_check"] = {"value": full["value"], "unit": "ms", "sample": full["sample"]}
     line = {"metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -508,13 +540,17 @@ def precision_workload(ihs, stream):
 
     A, b, sigma = problems.precision_instance()
     n, d = A.shape
+    grad_ms = []
     Ah = A.cpu().numpy()
     bh = b.cpu().numpy().astype(np.float64)
     out = {}
     for de in (50, 200, 1000):
         nu = problems.nu_for_target(sigma, de)
-        for prec in ("bf16", "fp8"):
-            ctx = ihs.Context(kind="gauss", variant="gd", precision=prec, tol=TOL, stream=stream)
+        for prec in ("bf16", "fp8", "srht_fp32"):
+            if prec == "srht_fp32":
+                ctx = ihs.Context(kind="srht", variant="gd", precision="fp32", tol=TOL, stream=stream)
+            else:
+                ctx = ihs.Context(kind="gauss", variant="gd", precision=prec, tol=TOL, stream=stream)
             x = torch.zeros(d, device="cuda")
             ctx.solve(A, b, nu, x)   # warm-up (scratch)
             # the solver's stopping rule decides; tol shrinks until the FP64 bound is <= 1e-5
@@ -542,12 +578,26 @@ def precision_workload(ihs, stream):
                 if bound <= TOL:
                     break
                 tol *= 0.3
+            ms_pass = rep.ms_grad / max(1, rep.grad_passes)
             out["de%d_%s" % (de, prec)] = {"nu": nu, "ms": ms, "tol": tol, "err_bound": bound,
                                            "levels": rep.levels(), "iterations": rep.iterations,
-                                           "grad_passes": rep.grad_passes, "status": int(rep.status)}
+                                           "grad_passes": rep.grad_passes, "status": int(rep.status),
+                                           "ms_sketch_factor": rep.ms_sketch, "ms_grad_per_pass": ms_pass}
+            grad_ms.append(ms_pass)
             ctx.destroy()
     del A
-    return {"workload": "precision 1048576x4096 (16 GB), sigma_j=exp(-j/300), gauss gd from m=1", "cases": out}
+    # the gradient pass at this size: algorithmic 4nd + 4n + 8d bytes per pass
+    # over the median pass time of all solves above (CUDA events in the solver)
+    alg = 4.0 * n * d + 4.0 * n + 8.0 * d
+    ms_med = statistics.median(grad_ms)
+    peaks, source = measured_peaks()
+    roof = {"bound": "hbm", "kernel": "gradient pass (k_grad_v3 + k_grad_reduce), 1048576 x 4096",
+            "algorithmic_bytes": alg, "ms_per_launch": ms_med, "achieved": alg / (ms_med * 1e-3) / 1e9,
+            "unit": "GB/s", "peak": peaks["hbm_gbs"], "peak_source": source}
+    roof["frac"] = roof["achieved"] / peaks["hbm_gbs"]
+    return {"workload": "precision 1048576x4096 (16 GB), sigma_j=exp(-j/300), gradient-IHS from m=1: "
+                        "Gaussian BF16 / FP8 on tensor cores and plain FP32 SRHT",
+            "grad_roofline": roof, "cases": out}
 
 
 def dual_workload(ihs, stream, p, A):
@@ -786,9 +836,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(p)
+        cpu = cpu_oracle_full(p)
         try:
-            cpu["single_thread"] = cpu_oracle_single_thread(p, n_s=cpu["rows_sampled"])
+            cpu["single_thread"] = cpu_oracle_single_thread(p)
         except Exception as e:   # the all-cores figure above stands; say why this one is missing
             cpu["single_thread"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     r0 = reps[-1]
@@ -811,7 +861,7 @@ def main():
                    "grad_passes_per_solve": r0.grad_passes, "ms_sketch_factor": r0.ms_sketch,
                    "oracle_minimal_iterations": min_iter,
                    "ms_iterate": r0.ms_iterate, "comparators_same_gpu": comparators, "forms_same_gpu": forms,
-                   "batched_same_gpu": batched, "precision_same_gpu": precision, "dual_same_gpu": dual,
+                   "batched_same_gpu": batched, "dual_same_gpu": dual,
                    "srht_sketch_bandwidth": sketch_bw, "config1_exp_decay_4096x256": cfg1},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(), "peak_source": peak_kind,
@@ -820,6 +870,11 @@ def main():
                      "algorithmic_bytes": bytes_per_pass},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * p.n * p.d + 4 * p.n,
                 "d2h_bytes_per_step": 4 * p.d},
+        "same_gpu_summary": {"ihs_srht_from_m1_ms": ms_per, "cg_ms": comparators.get("cg", {}).get("ms"),
+                             "pcg_srht_ms": comparators.get("pcg_srht", {}).get("ms"),
+                             "warm_srht_ms": forms.get("srht_warm", {}).get("ms"),
+                             "warm_bf16_gauss_ms": forms.get("gauss_bf16_warm", {}).get("ms")},
+        "config3_precision_1048576x4096": precision,
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,

@@ -502,7 +502,9 @@ int ihs_apply_prepare(ihs_ctx* ctx, ihs_factor_t* F) {
 
 int ihs_apply_fused(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt, double* d_r) {
     const size_t smem = fused_smem_bytes(F->k, F->m, F->d, F->woodbury);
-    IHS_CUDA_TRY(ihs_allow_smem(k_apply_fused, smem));
+    // one fixed limit for every launch (the kernel also holds 4 KB of static
+    // shared memory, so the device's whole opt-in maximum cannot be granted)
+    IHS_CUDA_TRY(cudaFuncSetAttribute(k_apply_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     int per_sm = 0;
     IHS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_fused, kApplyThreads, smem));
     if (per_sm < 1) return IHS_EINVAL;

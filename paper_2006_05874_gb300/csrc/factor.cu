@@ -1401,7 +1401,8 @@ extern "C" int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, d
 extern "C" int ihs_factor_destroy(ihs_factor_t* F) {
     if (!F) return IHS_OK;
     if (F->owned != 1) return IHS_EINVAL;   // scratch- or pool-backed factors are released by their owner
-    if (F->ctx) cudaStreamSynchronize(F->ctx->stream);
+    // cudaFree waits for the device's outstanding work on the block; the context
+    // is not touched (it may already be destroyed)
     if (F->L) cudaFree(F->L);   // the start of the factor's one block
     delete F;
     return IHS_OK;

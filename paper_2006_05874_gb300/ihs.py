@@ -222,7 +222,10 @@ class Context:
     def __init__(self, params=None, stream=None, **kw):
         import torch
 
+        import weakref
+
         lib = load()
+        self._factors = weakref.WeakSet()
         self.params = params if params is not None else default_params(**kw)
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -264,7 +267,9 @@ class Context:
         m, d = SA.shape
         h = ctypes.c_void_p()
         _check("ihs_factor", _lib.ihs_factor(self.handle, _ptr(SA), m, d, float(nu), ctypes.byref(h)))
-        return Factor(self, h, SA)
+        f = Factor(self, h, SA)
+        self._factors.add(f)
+        return f
 
     def grad(self, A, b, nu, x, g, want_axnorm2=True):
         n, d = A.shape
@@ -391,6 +396,8 @@ class Context:
 
     def destroy(self):
         if getattr(self, "handle", None):
+            for f in list(getattr(self, "_factors", ())):   # factors first: they were made on this context
+                f.destroy()
             _lib.ihs_ctx_destroy(self.handle)
             self.handle = None
 
