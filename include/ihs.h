@@ -297,6 +297,56 @@ int ihs_solve_resume(ihs_ctx* ctx, const float* A, const float* b, int64_t n, in
                      double nu, double tol, float* x, float* x_prev, ihs_state* st_h,
                      ihs_report* rep_h);
 
+/* ---- row-sharded data path (several GPUs, one process each) ------------- */
+/* The method's data-parallel structure: the gradient of Eq. 1 is a sum over
+ * row blocks, A^T (A x - b) = sum_p A_p^T (A_p x - b_p), and so is the sketch,
+ * S A = sum_p S_{:,p} A_p (Sec. 1: the per-iteration products are where
+ * distributed computation is needed).  A rank holds rows [row0, row0 + n) of a
+ * matrix of n_total rows; its terms are summed over ranks, and the factor and
+ * the controller run replicated on the summed values.  The draws are keyed by
+ * global row index, so the summed sketch is the whole matrix's sketch: SRHT
+ * signs and Hadamard parities of global rows (row0 a multiple of 1024, and a
+ * shard ends on a multiple of 1024 unless it holds the last rows), Gaussian
+ * columns z_{:,i} of global i.  FP8 Gaussian sketches scale each shard's
+ * columns by that shard's own maxima (its term matches the unsharded FP8
+ * sketch only to the E4M3 rounding). */
+
+/* This shard's term of SA (m x d, device FP32, with the definition's 1/sqrt(m)
+ * factor): the sum over shards is ihs_sketch of the whole A.
+ * kind and seed/level as ihs_sketch; m <= n_pad(n_total) (SRHT) or n_total
+ * (Gaussian).  Asynchronous. */
+int ihs_sketch_shard(ihs_ctx* ctx, const float* A_local, int64_t n, int64_t d, int64_t row0,
+                     int64_t n_total, int64_t m, int32_t kind, uint64_t seed, int32_t level,
+                     float* SA_part);
+
+/* This shard's gradient terms in FP64, unrounded (d + 1 doubles, device):
+ * gp[0..d) = A_p^T (A_p x - b_p), gp[d] = ||A_p x||^2.  The gradient of Eq. 1
+ * is sum_p gp[0..d) + nu^2 x.  Asynchronous. */
+int ihs_grad_shard(ihs_ctx* ctx, const float* A_local, const float* b_local, int64_t n, int64_t d,
+                   const float* x, double* gp);
+
+/* In-place sum of a device buffer over the ranks of a sharded solve:
+ * `count` elements of IHS_DTYPE_F32 or IHS_DTYPE_F64 at `buf`, whose contents
+ * come from work already enqueued on `stream` (a cudaStream_t).  The callback
+ * must order the sum after that work (e.g. an NCCL all-reduce enqueued on the
+ * stream, or a synchronisation first) and have finished it, or enqueued it on
+ * the stream, when it returns; every rank must receive the same sums.  Return
+ * 0 on success; anything else makes the solve return IHS_ECUDA. */
+#define IHS_DTYPE_F32 0
+#define IHS_DTYPE_F64 1
+typedef int (*ihs_allreduce_fn)(void* user, void* buf, int64_t count, int32_t dtype, void* stream);
+
+/* ihs_solve on a row shard: every rank calls it with its rows (A_local n x d,
+ * b_local n, device FP32) and the same ctx parameters, nu, tol and x_1; the
+ * sketch of each level (m x d floats) and the gradient partials of each pass
+ * (d + 1 doubles) are summed by `allreduce` (called from this host thread,
+ * user passed through), and every rank takes the same decisions and returns
+ * the same x.  Requirements as ihs_sketch_shard; params.nested must be 0.
+ * Returns as ihs_solve. */
+int ihs_solve_sharded(ihs_ctx* ctx, const float* A_local, const float* b_local, int64_t n, int64_t d,
+                      int64_t row0, int64_t n_total, double nu, double tol, float* x,
+                      ihs_report* rep_h, ihs_allreduce_fn allreduce, void* user);
+
 /* ---- batched solves ------------------------------------------------------- */
 /* One ridge problem of a batch.  A (n x d, row-major FP32), b (n) and x (d)
  * are device buffers owned by the caller; x holds x_1 on entry and x_T on

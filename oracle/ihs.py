@@ -48,12 +48,14 @@ class IHSResult:
 
 def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
                  m_init=1, x0=None, x1=None, tol=1e-5, max_iter=200, floor=0.0,
-                 sketch_fn=None, keep_history=False, dual_b=None, nested=False):
+                 sketch_fn=None, keep_history=False, dual_b=None, nested=False, grad_fn=None):
     """Run Algorithm 1 (variant="polyak") or its gradient-only variant
     (variant="gd", Sec. 5) on min 1/2||Ax-b||^2 + nu^2/2 ||x||^2.
 
     sketch_fn(A, m, kind, seed, level) -> SA may replace the oracle's own sketch
     (used to run the method on externally given sketches in tests).
+    grad_fn(v) -> (A^T (A v - b) + nu^2 v, ||A v||^2) may replace the oracle's own
+    gradient (a rank of a row-sharded run sums its rows' terms with the others').
     keep_history stores (t, x_t, SA in force) for every iterate (small n only).
     dual_b: run on the dual of App. A.2 instead, with A standing for the dual's
     data matrix (the transpose of the primal one) and the gradient
@@ -84,6 +86,8 @@ def adaptive_ihs(A, b, nu, kind="srht", variant="gd", seed=0, rho=0.1, eta=0.01,
     def grad_at(v):
         nonlocal passes
         passes += 1
+        if grad_fn is not None:
+            return grad_fn(v)
         Av = A @ v
         g = A.T @ (Av - b) + nu * nu * v
         if dual_b is not None:

@@ -146,7 +146,16 @@ int ihs_sketch_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64
 int ihs_gauss_fp32_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
                            int32_t level, float* SA);   // FP32 SIMT Gaussian sketch
 int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
-                         int32_t level, float* SA, int fp8, int64_t zrow0 = 0, int64_t m_scale = 0);   // rows [zrow0, zrow0 + m) of the sketch of size m_scale
+                         int32_t level, float* SA, int fp8, int64_t zrow0 = 0, int64_t m_scale = 0,
+                         int64_t grow0 = 0);   // rows [zrow0, zrow0 + m) of the sketch of size m_scale; A's row 0 is global row grow0
+// A row shard's term of the sketch (rows [row0, row0 + n) of n_total) and of
+// the gradient (FP64 partial sums, d + 1 doubles: A^T (A x - b) and ||A x||^2).
+int ihs_sketch_shard_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t row0, int64_t n_total,
+                             int64_t m, int32_t kind, uint64_t seed, int32_t level, float* SA_part);
+int ihs_grad_partial_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, const float* x,
+                             double* gp);
+int ihs_grad_finish_enqueue(ihs_ctx* ctx, const double* gp, int64_t d, double nu, const float* x, float* g,
+                            double* d_axnorm2);
 int ihs_rows_enqueue(ihs_ctx* ctx, int64_t n_pad, int64_t m, uint64_t seed, int32_t level,
                      int32_t* rows);
 int ihs_factor_build(ihs_ctx* ctx, ihs_factor_t* F);       // enqueue + check pivots (syncs)

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 k_gauss_tc(const __grid_constant__ CUtensorMap amap, const float* __restrict__ A, int64_t n, int d, int64_t m,
            int64_t rows_per_split,
            uint32_t level, uint32_t k0, uint32_t k1, uint32_t zq0 /* first z row / 4 */,
-           const float* __restrict__ col_recip, unsigned* status,
+           uint32_t ibase /* global row of A's row 0 */, const float* __restrict__ col_recip, unsigned* status,
            float* __restrict__ part /* KS x m x d */) {
     constexpr int RB = (int)tc_rb(FMT);                 // operand bytes per row per chunk
     constexpr uint32_t ZB = TC_M * RB, STAGE = tc_stage(FMT);
@@ -149,7 +149,7 @@ k_gauss_tc(const __grid_constant__ CUtensorMap amap, const float* __restrict__ A
             if (q < nq) {
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
-                    const float4 z = gauss4_fast((uint32_t)(i0 + 2 * ig + t), zq0 + (uint32_t)((j0 >> 2) + q), level, k0, k1);
+                    const float4 z = gauss4_fast(ibase + (uint32_t)(i0 + 2 * ig + t), zq0 + (uint32_t)((j0 >> 2) + q), level, k0, k1);
                     zv[0][t] = z.x;
                     zv[1][t] = z.y;
                     zv[2][t] = z.z;
@@ -346,7 +346,7 @@ __global__ void k_reduce_parts_tc(const float* __restrict__ part, int K, int64_t
 }  // namespace
 
 int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed, int32_t level,
-                         float* SA, int fp8, int64_t zrow0, int64_t m_scale) {
+                         float* SA, int fp8, int64_t zrow0, int64_t m_scale, int64_t grow0) {
     if (m_scale <= 0) m_scale = m;
     CUtensorMap amap;
     memset(&amap, 0, sizeof(amap));
@@ -389,7 +389,8 @@ int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int
     auto launch = [&](auto kern, int fmt, const float* crec) -> int {
         IHS_CUDA_TRY(ihs_allow_smem(kern, tc_smem(fmt)));
         kern<<<grid, TC_THREADS, tc_smem(fmt), ctx->stream>>>(amap, A, n, (int)d, m, rows_per_split, (uint32_t)level,
-                                                              k0, k1, (uint32_t)(zrow0 >> 2), crec, ctx->d_status, part);
+                                                              k0, k1, (uint32_t)(zrow0 >> 2), (uint32_t)grow0, crec,
+                                                              ctx->d_status, part);
         return IHS_OK;
     };
     if (fp8) IHS_TRY(tma ? launch(k_gauss_tc<1, true>, 1, crecip) : launch(k_gauss_tc<1, false>, 1, crecip));

@@ -865,8 +865,10 @@ int grad_pass_fast(const GradTarget& tg, const float* A, const float* b, const f
 
 }  // namespace
 
-int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
-                     const float* x, float* g, double* d_axnorm2) {
+// The per-CTA (or per-row-group) partial sums of A^T (A x - b) and ||A x||^2:
+// G partials of d float2 pairs at *part, G doubles at *part_ax2.
+static int grad_partials(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, const float* x,
+                         float2** part_out, double** part_ax2_out, int* G_out) {
     if (n < 1 || d < 1 || d > (1 << 20)) return IHS_EINVAL;
     const bool aligned = ((uintptr_t)A % 16 == 0) && ((uintptr_t)x % 16 == 0) && (d % 4 == 0) && d <= 8192;
     const int64_t Gmax = 4 * (int64_t)ctx->sm_count + 1024;
@@ -899,9 +901,88 @@ int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, in
         k_fold_doubles<<<1, 1, 0, ctx->stream>>>(rpart, rblocks, part_ax2, G);
         IHS_LAUNCH_CHECK();
     }
+    *part_out = part;
+    *part_ax2_out = part_ax2;
+    *G_out = G;
+    return IHS_OK;
+}
+
+int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
+                     const float* x, float* g, double* d_axnorm2) {
+    float2* part = nullptr;
+    double* part_ax2 = nullptr;
+    int G = 0;
+    IHS_TRY(grad_partials(ctx, A, b, n, d, x, &part, &part_ax2, &G));
     k_grad_reduce<<<(unsigned)ceil_div64(d, 32), 256, 0, ctx->stream>>>(part, part_ax2, G, (int)d, nu * nu, x, g,
                                                                         d_axnorm2);
     IHS_LAUNCH_CHECK();
+    return IHS_OK;
+}
+
+namespace {
+
+// gp[c] = sum of the partials of column c, gp[d] = sum of the ||A x||^2
+// partials: the same fixed-order FP64 sums as k_grad_reduce, left unrounded
+// and without nu^2 x, for a row shard whose sums other shards add to.
+__global__ void k_grad_reduce_f64(const float2* __restrict__ part, const double* __restrict__ part_ax2, int G, int d,
+                                  double* __restrict__ gp) {
+    __shared__ double sm[8][33];
+    const int cx = threadIdx.x & 31, sy = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + cx;
+    double s = 0.0;
+    if (col < d) {
+        for (int gi = sy; gi < G; gi += 8) {
+            const float2 v = part[(size_t)gi * d + col];
+            s += (double)v.x + (double)v.y;
+        }
+    }
+    sm[sy][cx] = s;
+    __syncthreads();
+    if (sy == 0 && col < d) {
+        double t = sm[0][cx];
+        for (int k = 1; k < 8; ++k) t += sm[k][cx];
+        gp[col] = t;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double t = 0.0;
+        for (int gi = 0; gi < G; ++gi) t += part_ax2[gi];
+        gp[d] = t;
+    }
+}
+
+// g = fl32(gp + nu^2 x) and ||A x||^2 = gp[d] from the summed shard partials.
+__global__ void k_grad_finish(const double* __restrict__ gp, int d, double nu2, const float* __restrict__ x,
+                              float* __restrict__ g, double* __restrict__ axnorm2) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < d) g[c] = (float)(gp[c] + nu2 * (double)x[c]);
+    if (c == 0 && axnorm2) *axnorm2 = gp[d];
+}
+
+}  // namespace
+
+int ihs_grad_partial_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, const float* x,
+                             double* gp) {
+    float2* part = nullptr;
+    double* part_ax2 = nullptr;
+    int G = 0;
+    IHS_TRY(grad_partials(ctx, A, b, n, d, x, &part, &part_ax2, &G));
+    k_grad_reduce_f64<<<(unsigned)ceil_div64(d, 32), 256, 0, ctx->stream>>>(part, part_ax2, G, (int)d, gp);
+    IHS_LAUNCH_CHECK();
+    return IHS_OK;
+}
+
+int ihs_grad_finish_enqueue(ihs_ctx* ctx, const double* gp, int64_t d, double nu, const float* x, float* g,
+                            double* d_axnorm2) {
+    k_grad_finish<<<(unsigned)ceil_div64(d, 256), 256, 0, ctx->stream>>>(gp, (int)d, nu * nu, x, g, d_axnorm2);
+    IHS_LAUNCH_CHECK();
+    return IHS_OK;
+}
+
+extern "C" int ihs_grad_shard(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, const float* x,
+                              double* gp) {
+    IhsRange range("ihs_grad_shard");
+    if (!ctx || !A || !b || !x || !gp) return IHS_EINVAL;
+    IHS_TRY(ihs_grad_partial_enqueue(ctx, A, b, n, d, x, gp));
     return IHS_OK;
 }
 

@@ -24,6 +24,7 @@ constexpr int kSrhtThreads = 512;
 __global__ void __launch_bounds__(kSrhtThreads)
 k_srht_fwht(const float* __restrict__ A, int64_t n, int d, int64_t m, int Q, int logQ, int64_t P, int PG,
             const int32_t* __restrict__ rows, uint32_t level, uint32_t k0, uint32_t k1, int acc_in_smem,
+            int64_t grow0 /* global index of A's row 0, a multiple of Q */,
             float* __restrict__ out /* PG x m x d partials */) {
     extern __shared__ __align__(16) float sm[];
     const int CP = kSrhtC + 1;   // padded row stride
@@ -49,7 +50,7 @@ k_srht_fwht(const float* __restrict__ A, int64_t n, int d, int64_t m, int Q, int
     for (int64_t p = p0; p < p1; ++p) {
         __syncthreads();
         for (int q = tid; q < Q; q += kSrhtThreads) {
-            const uint64_t i = (uint64_t)(p * Q + q);
+            const uint64_t i = (uint64_t)(grow0 + p * Q + q);
             sg[q] = srht_sign_bit(i, level, k0, k1) ? -1.f : 1.f;
         }
         __syncthreads();
@@ -80,7 +81,7 @@ k_srht_fwht(const float* __restrict__ A, int64_t n, int d, int64_t m, int Q, int
             const uint32_t lo = r & (uint32_t)(Q - 1);
             const uint64_t hi = (uint64_t)(r >> logQ);
             const float v = X[lo * CP + c];
-            const float sv = (__popcll(hi & (uint64_t)p) & 1) ? -v : v;
+            const float sv = (__popcll(hi & (uint64_t)(grow0 / Q + p)) & 1) ? -v : v;
             if (acc_in_smem) {
                 acc[e] += sv;
             } else if (c < ncol) {
@@ -155,7 +156,8 @@ __host__ __device__ inline size_t r32_smem_bytes(int ma) {
 template <int MA>
 __global__ void __launch_bounds__(kR32T, 1)
 k_srht_r32(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t m_total, int64_t row_off, int64_t P,
-           int PG, const int32_t* __restrict__ rows, uint32_t level, uint32_t k0, uint32_t k1, unsigned* status,
+           int PG, const int32_t* __restrict__ rows, uint32_t level, uint32_t k0, uint32_t k1, int64_t gblk,
+           unsigned* status,
            float* __restrict__ out /* PG x m_total x d partials; this launch writes rows [row_off, row_off + m) */) {
     extern __shared__ __align__(128) unsigned char smraw[];
     float* stage = reinterpret_cast<float*>(smraw);                                   // 2 x 1024 x 16
@@ -206,7 +208,7 @@ k_srht_r32(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t m
     for (; b < nblk; ++b) {
         const int64_t p = p0 + b;
         if (tid < 8) {
-            const uint4 w = srht_sign_words((uint64_t)p * 8 + tid, level, k0, k1);
+            const uint4 w = srht_sign_words((uint64_t)(gblk + p) * 8 + tid, level, k0, k1);
             sbits[4 * tid + 0] = w.x;
             sbits[4 * tid + 1] = w.y;
             sbits[4 * tid + 2] = w.z;
@@ -237,7 +239,7 @@ k_srht_r32(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t m
         __syncthreads();
         // every slot accumulates (slots >= m read T[0] and are never stored):
         // no branches on the gather path
-        const int pb = (int)p;
+        const int pb = (int)(gblk + p);   // global 1024-row block index
         const unsigned char* Tc = reinterpret_cast<const unsigned char*>(T + c);
 #pragma unroll
         for (int i = 0; i < MA; ++i) {
@@ -306,7 +308,8 @@ template <int MA>
 __global__ void __launch_bounds__(kQ5T, 2)
 k_srht_q512(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t m_total, int64_t row_off,
             int64_t P5, int PG, const int32_t* __restrict__ rows, uint32_t level, uint32_t k0, uint32_t k1,
-            unsigned* status, float* __restrict__ out /* PG x m_total x d partials */) {
+            int64_t gblk /* global 1024-row block of A's row 0 */, unsigned* status,
+            float* __restrict__ out /* PG x m_total x d partials */) {
     extern __shared__ __align__(128) unsigned char smraw[];
     float* stage = reinterpret_cast<float*>(smraw);                                   // 3 x 512 x 16
     uint32_t* sbits = reinterpret_cast<uint32_t*>(smraw + kQ5S * kQ5Stage);           // 32 sign words
@@ -360,7 +363,7 @@ k_srht_q512(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t 
     for (; b < nblk; ++b) {
         const int64_t q = q0 + b;
         if (tid < 8) {
-            const uint4 w = srht_sign_words((uint64_t)(q >> 1) * 8 + tid, level, k0, k1);
+            const uint4 w = srht_sign_words((uint64_t)(gblk + (q >> 1)) * 8 + tid, level, k0, k1);
             sbits[4 * tid + 0] = w.x;
             sbits[4 * tid + 1] = w.y;
             sbits[4 * tid + 2] = w.z;
@@ -402,7 +405,7 @@ k_srht_q512(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t 
         // order these generic writes before the TMA load that will refill the stage
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        const int qb = (int)q;
+        const int qb = (int)(2 * gblk + q);   // global 512-row block index
         const unsigned char* Tc = reinterpret_cast<const unsigned char*>(st + c);
 #pragma unroll
         for (int i = 0; i < MA; ++i) {
@@ -437,7 +440,7 @@ k_srht_q512(const __grid_constant__ CUtensorMap amap, int d, int64_t m, int64_t 
 
 template <int MA>
 int launch_q512(ihs_ctx* ctx, const CUtensorMap& amap, int d, int64_t mc, int64_t m, int64_t c0, int64_t P5, int PG,
-                const int32_t* rows, int32_t level, uint64_t seed, float* part) {
+                const int32_t* rows, int32_t level, uint64_t seed, int64_t gblk, float* part) {
     const size_t smem = q5_smem_bytes(MA);
     auto kern = k_srht_q512<MA>;
     IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
@@ -446,20 +449,20 @@ int launch_q512(ihs_ctx* ctx, const CUtensorMap& amap, int d, int64_t mc, int64_
                                       (int)cudaSharedmemCarveoutMaxShared));
     dim3 grid((unsigned)ceil_div64(d, kQ5C), (unsigned)PG);
     kern<<<grid, kQ5T, smem, ctx->stream>>>(amap, d, mc, m, c0, P5, PG, rows, (uint32_t)level, (uint32_t)seed,
-                                           (uint32_t)(seed >> 32), ctx->d_status, part);
+                                           (uint32_t)(seed >> 32), gblk, ctx->d_status, part);
     IHS_LAUNCH_CHECK();
     return IHS_OK;
 }
 
 template <int MA>
 int launch_r32(ihs_ctx* ctx, const CUtensorMap& amap, int d, int64_t mc, int64_t m, int64_t c0, int64_t P, int PG,
-               const int32_t* rows, int32_t level, uint64_t seed, float* part) {
+               const int32_t* rows, int32_t level, uint64_t seed, int64_t gblk, float* part) {
     const size_t smem = r32_smem_bytes(MA);
     auto kern = k_srht_r32<MA>;
     IHS_CUDA_TRY(ihs_allow_smem(kern, smem));
     dim3 grid((unsigned)ceil_div64(d, kR32C), (unsigned)PG);
     kern<<<grid, kR32T, smem, ctx->stream>>>(amap, d, mc, m, c0, P, PG, rows, (uint32_t)level, (uint32_t)seed,
-                                            (uint32_t)(seed >> 32), ctx->d_status, part);
+                                            (uint32_t)(seed >> 32), gblk, ctx->d_status, part);
     IHS_LAUNCH_CHECK();
     return IHS_OK;
 }
@@ -495,7 +498,8 @@ constexpr int kGBM = 64, kGBN = 64, kGBK = 32, kGThreads = 256;
 
 __global__ void __launch_bounds__(kGThreads)
 k_gauss_simt(const float* __restrict__ A, int64_t n, int d, int64_t m, int64_t rows_per_split, uint32_t level,
-             uint32_t k0, uint32_t k1, uint32_t zq0 /* first z row / 4 */, float2* __restrict__ part /* KS x m x d */) {
+             uint32_t k0, uint32_t k1, uint32_t zq0 /* first z row / 4 */, uint32_t ibase /* global row of A's row 0 */,
+             float2* __restrict__ part /* KS x m x d */) {
     __shared__ float zs[kGBK][kGBM + 4];
     __shared__ float as[kGBK][kGBN + 4];
     const int tid = threadIdx.x;
@@ -516,7 +520,7 @@ k_gauss_simt(const float* __restrict__ A, int64_t n, int d, int64_t m, int64_t r
             const int ii = e / (kGBM / 4), qq = e % (kGBM / 4);
             const int64_t i = i0 + ii;
             float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < i_end) z = gauss4((uint32_t)i, zq0 + (uint32_t)((j0 >> 2) + qq), level, k0, k1);
+            if (i < i_end) z = gauss4(ibase + (uint32_t)i, zq0 + (uint32_t)((j0 >> 2) + qq), level, k0, k1);
             zs[ii][qq * 4 + 0] = z.x;
             zs[ii][qq * 4 + 1] = z.y;
             zs[ii][qq * 4 + 2] = z.z;
@@ -558,14 +562,22 @@ k_gauss_simt(const float* __restrict__ A, int64_t n, int d, int64_t m, int64_t r
     }
 }
 
+// A holds rows [grow0, grow0 + n) of a matrix of n_total rows (a row shard;
+// grow0 = 0 and n_total = n for the whole matrix): the sketch of the whole
+// matrix restricted to these rows, i.e. this shard's term of SA = sum over
+// shards.  grow0 must be a multiple of 1024 (whole transform blocks).
 int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed, int32_t level,
-                 float* SA) {
-    const int64_t n_pad = next_pow2_64(n);
+                 float* SA, int64_t grow0 = 0, int64_t n_total = 0) {
+    if (n_total <= 0) n_total = n;
+    const int64_t n_pad = next_pow2_64(n_total);
     if (m > n_pad) return IHS_EINVAL;
     const int Q = (int)std::min<int64_t>(n_pad, kSrhtQmax);
     int logQ = 0;
     while ((1 << logQ) < Q) ++logQ;
-    const int64_t P = n_pad / Q;
+    if (grow0 % Q) return IHS_EINVAL;
+    // the whole matrix: every block of the padded n_pad rows; a shard: its own blocks
+    const int64_t P = (grow0 == 0 && n == n_total) ? n_pad / Q : ceil_div64(n, Q);
+    const int64_t gblk = grow0 / 1024;
     const int64_t CT = ceil_div64(d, kSrhtC);
     int64_t PG = std::max<int64_t>(1, ceil_div64(2 * (int64_t)ctx->sm_count, CT));
     PG = std::min<int64_t>(PG, P);
@@ -607,12 +619,12 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
         for (int64_t c0 = 0; c0 < m; c0 += chunk) {
             const int64_t mc = std::min<int64_t>(chunk, m - c0);
             int st;
-            if (mc <= 16) st = launch_q512<1>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, part);
-            else if (mc <= 64) st = launch_q512<4>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, part);
-            else if (mc <= 128) st = launch_q512<8>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, part);
-            else if (mc <= 256) st = launch_q512<16>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, part);
-            else if (mc <= 32 * 16) st = launch_r32<16>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, part);
-            else st = launch_r32<32>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, part);
+            if (mc <= 16) st = launch_q512<1>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, gblk, part);
+            else if (mc <= 64) st = launch_q512<4>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, gblk, part);
+            else if (mc <= 128) st = launch_q512<8>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, gblk, part);
+            else if (mc <= 256) st = launch_q512<16>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, gblk, part);
+            else if (mc <= 32 * 16) st = launch_r32<16>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, gblk, part);
+            else st = launch_r32<32>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, gblk, part);
             IHS_TRY(st);
         }
     } else {
@@ -624,7 +636,7 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
         dim3 grid((unsigned)CT, (unsigned)PG);
         k_srht_fwht<<<grid, kSrhtThreads, smem, ctx->stream>>>(A, n, (int)d, m, Q, logQ, P, (int)PG, rows,
                                                               (uint32_t)level, (uint32_t)seed,
-                                                              (uint32_t)(seed >> 32), acc_in_smem, part);
+                                                              (uint32_t)(seed >> 32), acc_in_smem, grow0, part);
         IHS_LAUNCH_CHECK();
     }
     const int64_t count = m * d;
@@ -636,7 +648,7 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
 
 // Rows [zrow0, zrow0 + m) of the Gaussian sketch of size m_scale (zrow0 % 4 == 0).
 int gauss_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed, int32_t level,
-                  float* SA, int64_t zrow0 = 0, int64_t m_scale = 0) {
+                  float* SA, int64_t zrow0 = 0, int64_t m_scale = 0, int64_t grow0 = 0) {
     if (m_scale <= 0) m_scale = m;
     const int64_t MT = ceil_div64(m, kGBM), NT = ceil_div64(d, kGBN);
     int64_t KS = std::max<int64_t>(1, ceil_div64(4 * (int64_t)ctx->sm_count, MT * NT));
@@ -650,7 +662,7 @@ int gauss_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m,
     dim3 grid((unsigned)MT, (unsigned)NT, (unsigned)KS);
     k_gauss_simt<<<grid, kGThreads, 0, ctx->stream>>>(A, n, (int)d, m, rows_per_split, (uint32_t)level,
                                                      (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)(zrow0 >> 2),
-                                                     part);
+                                                     (uint32_t)grow0, part);
     IHS_LAUNCH_CHECK();
     const int64_t count = m * d;
     const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
@@ -677,6 +689,35 @@ int ihs_sketch_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64
         return gauss_enqueue(ctx, A, n, d, m, seed, level, SA);
     }
     return IHS_EINVAL;
+}
+
+int ihs_sketch_shard_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t row0, int64_t n_total,
+                             int64_t m, int32_t kind, uint64_t seed, int32_t level, float* SA_part) {
+    if (n < 1 || d < 1 || m < 1 || level < 0 || m > ((int64_t)1 << 31)) return IHS_EINVAL;
+    if (row0 < 0 || n_total < row0 + n || n_total > ((int64_t)1 << 32)) return IHS_EINVAL;
+    if (kind == IHS_SKETCH_SRHT) {
+        // whole transform blocks: the shard starts on a block, and ends on one
+        // unless it holds the last rows
+        if (row0 % 1024 || (n % 1024 && row0 + n != n_total)) return IHS_EINVAL;
+        return srht_enqueue(ctx, A, n, d, m, seed, level, SA_part, row0, n_total);
+    }
+    if (kind == IHS_SKETCH_GAUSS) {
+        if (m > n_total) return IHS_EINVAL;
+        if (ctx->p.precision == IHS_PREC_BF16)
+            return ihs_gauss_tc_enqueue(ctx, A, n, d, m, seed, level, SA_part, 0, 0, 0, row0);
+        if (ctx->p.precision == IHS_PREC_FP8)
+            return ihs_gauss_tc_enqueue(ctx, A, n, d, m, seed, level, SA_part, 1, 0, 0, row0);
+        return gauss_enqueue(ctx, A, n, d, m, seed, level, SA_part, 0, 0, row0);
+    }
+    return IHS_EINVAL;
+}
+
+extern "C" int ihs_sketch_shard(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t row0, int64_t n_total,
+                                int64_t m, int32_t kind, uint64_t seed, int32_t level, float* SA_part) {
+    IhsRange range("ihs_sketch_shard");
+    if (!ctx || !A || !SA_part) return IHS_EINVAL;
+    IHS_TRY(ihs_sketch_shard_enqueue(ctx, A, n, d, row0, n_total, m, kind, seed, level, SA_part));
+    return IHS_OK;
 }
 
 int ihs_sketch_rows_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,

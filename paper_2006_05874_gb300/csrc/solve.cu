@@ -289,7 +289,23 @@ struct Solver {
     int64_t m;
     int level;
     float ms_sketch, ms_iter, ms_grad;
+    // row-sharded solve: A holds rows [row0, row0 + n) of n_total; the sketch
+    // and the gradient's partial sums are summed over ranks by `ar`
+    int64_t row0, n_total;
+    ihs_allreduce_fn ar;
+    void* ar_user;
+    double* gp;           // d + 1 FP64 gradient partials (sharded solves)
 };
+
+// Sum a device buffer over the ranks of a sharded solve, in place.
+int shard_sum(Solver& S, void* buf, int64_t count, int32_t dtype) {
+    const int st = S.ar(S.ar_user, buf, count, dtype, (void*)S.ctx->stream);
+    if (st != 0) {
+        ihs_set_error("the all-reduce callback of a sharded solve failed");
+        return IHS_ECUDA;
+    }
+    return IHS_OK;
+}
 
 // old rows of a nested Gaussian sketch: dst = src * scale
 __global__ void k_scale_copy(const float* __restrict__ src, int64_t count, float scale, float* __restrict__ dst) {
@@ -313,7 +329,11 @@ int sketch_level(Solver& S, int64_t m, int level) {
     S.SA = static_cast<float*>(ws);
     S.sa_slot = slot;
     IHS_CUDA_TRY(cudaEventRecord(ctx->ev[0], ctx->stream));
-    if (reuse) {
+    if (S.ar) {
+        IHS_TRY(ihs_sketch_shard_enqueue(ctx, S.A, S.n, S.d, S.row0, S.n_total, m, ctx->p.kind, ctx->p.seed, draw,
+                                         S.SA));
+        IHS_TRY(shard_sum(S, S.SA, m * S.d, IHS_DTYPE_F32));
+    } else if (reuse) {
         const int64_t count = old_m * S.d;
         const unsigned grid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
         k_scale_copy<<<grid, 256, 0, ctx->stream>>>(old_SA, count, (float)sqrt((double)old_m / (double)m), S.SA);
@@ -350,6 +370,10 @@ int evaluate(Solver& S, int ix, int ig, int igt, double* r, double* ax2, double*
             S.ds.part, S.ds.G, (int)S.d, S.nu * S.nu, S.vec[ix], S.vlo[ix], S.bsub, S.vec[ig], S.ds.rpart, (int)nrb,
             S.dsc + 1);
         IHS_LAUNCH_CHECK();
+    } else if (S.ar) {
+        IHS_TRY(ihs_grad_partial_enqueue(ctx, S.A, S.b, S.n, S.d, S.vec[ix], S.gp));
+        IHS_TRY(shard_sum(S, S.gp, S.d + 1, IHS_DTYPE_F64));
+        IHS_TRY(ihs_grad_finish_enqueue(ctx, S.gp, S.d, S.nu, S.vec[ix], S.vec[ig], S.dsc + 1));
     } else {
         IHS_TRY(ihs_grad_enqueue(ctx, S.A, S.b, S.n, S.d, S.nu, S.vec[ix], S.vec[ig], S.dsc + 1));
     }
@@ -411,7 +435,8 @@ int solve_impl(Solver& S, double tol, ihs_report* rep, ihs_state* st = nullptr, 
     ihs_ctx* ctx = S.ctx;
     const ihs_params& p = ctx->p;
     const Params prm = make_params(p.kind, p.rho, p.eta);
-    const int64_t m_cap = p.kind == IHS_SKETCH_SRHT ? next_pow2_64(S.n) : S.n;
+    const int64_t n_all = S.n_total > 0 ? S.n_total : S.n;   // rows of the whole matrix
+    const int64_t m_cap = p.kind == IHS_SKETCH_SRHT ? next_pow2_64(n_all) : n_all;
     const bool resume = st && st->t > 0;
     int64_t m = resume ? st->m : std::min<int64_t>(p.m_init, m_cap);
     int level = 0;
@@ -608,6 +633,48 @@ extern "C" int ihs_solve_resume(ihs_ctx* ctx, const float* A, const float* b, in
     if (rep_h) *rep_h = rep;
     if (st == IHS_OK || st == IHS_EMAXITER || st == IHS_ENONFINITE) {
         // a device wait that gave up poisons r (non-finite): report the cause
+        const int s2 = ihs_check_status(ctx);
+        if (s2 != IHS_OK) return s2;
+    }
+    return st;
+}
+
+extern "C" int ihs_solve_sharded(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, int64_t row0,
+                                 int64_t n_total, double nu, double tol, float* x, ihs_report* rep_h,
+                                 ihs_allreduce_fn allreduce, void* user) {
+    if (!ctx || !A || !b || !x || !allreduce) return IHS_EINVAL;
+    if (n < 1 || d < 1 || row0 < 0 || n_total < row0 + n || n_total < d || !(nu > 0.0) || !isfinite(nu))
+        return IHS_EINVAL;
+    if (ctx->p.nested) return IHS_EINVAL;
+    if (ctx->p.kind == IHS_SKETCH_SRHT && (row0 % 1024 || (n % 1024 && row0 + n != n_total))) return IHS_EINVAL;
+    if (!(tol > 0.0)) tol = ctx->p.tol;
+    IhsRange range("ihs_solve_sharded");
+    ihs_report rep;
+    memset(&rep, 0, sizeof(rep));
+    Solver S;
+    memset(&S, 0, sizeof(S));
+    S.ctx = ctx;
+    S.A = A;
+    S.b = b;
+    S.n = n;
+    S.d = d;
+    S.nu = nu;
+    S.row0 = row0;
+    S.n_total = n_total;
+    S.ar = allreduce;
+    S.ar_user = user;
+    void* ws = nullptr;
+    const size_t vb = ((size_t)d * sizeof(float) + 255) & ~(size_t)255;
+    const size_t gb = ((size_t)(d + 1) * sizeof(double) + 255) & ~(size_t)255;
+    IHS_TRY(ihs_scratch(ctx, SLOT_SOLVE, 7 * vb + gb + 8192 * sizeof(double), &ws));
+    char* base = static_cast<char*>(ws);
+    S.vec[0] = x;
+    for (int i = 1; i < 7; ++i) S.vec[i] = reinterpret_cast<float*>(base + i * vb);
+    S.gp = reinterpret_cast<double*>(base + 7 * vb);
+    S.dsc = reinterpret_cast<double*>(base + 7 * vb + gb);
+    const int st = solve_impl(S, tol, &rep);
+    if (rep_h) *rep_h = rep;
+    if (st == IHS_OK || st == IHS_EMAXITER || st == IHS_ENONFINITE) {
         const int s2 = ihs_check_status(ctx);
         if (s2 != IHS_OK) return s2;
     }

@@ -67,6 +67,10 @@ class State(ctypes.Structure):
                 ("grad_passes", ctypes.c_int32), ("n_levels", ctypes.c_int32)]
 
 
+# ihs_allreduce_fn: int (*)(void* user, void* buf, int64_t count, int32_t dtype, void* stream)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_void_p)
+
 _vp, _i64, _i32, _u64, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
 _SIGNATURES = {
     "ihs_version": ([], ctypes.c_char_p),
@@ -87,6 +91,10 @@ _SIGNATURES = {
     "ihs_solve": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_solve_resume": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, _vp, ctypes.POINTER(State),
                           ctypes.POINTER(Report)], ctypes.c_int),
+    "ihs_sketch_shard": ([_vp, _vp, _i64, _i64, _i64, _i64, _i64, _i32, _u64, _i32, _vp], ctypes.c_int),
+    "ihs_grad_shard": ([_vp, _vp, _vp, _i64, _i64, _vp, _vp], ctypes.c_int),
+    "ihs_solve_sharded": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report),
+                           ALLREDUCE_FN, _vp], ctypes.c_int),
     "ihs_trace_events": ([_vp, ctypes.POINTER(Event), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
     "ihs_ctx_set_trace_file": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "ihs_solve_dual": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
@@ -297,6 +305,28 @@ class Context:
         if st not in (IHS_OK, IHS_EMAXITER):
             _check("ihs_solve_resume", st)
         return rep, state
+
+    def sketch_shard(self, A_local, row0, n_total, m, kind, seed, level, SA_part):
+        """This shard's term of the sketch of the whole matrix (ihs_sketch_shard)."""
+        n, d = A_local.shape
+        _check("ihs_sketch_shard", _lib.ihs_sketch_shard(self.handle, _ptr(A_local), n, d, row0, n_total, m,
+                                                         KINDS.get(kind, kind), seed, level, _ptr(SA_part)))
+
+    def grad_shard(self, A_local, b_local, x, gp):
+        """This shard's FP64 gradient terms, d + 1 doubles (ihs_grad_shard)."""
+        n, d = A_local.shape
+        _check("ihs_grad_shard", _lib.ihs_grad_shard(self.handle, _ptr(A_local), _ptr(b_local), n, d, _ptr(x),
+                                                     _ptr(gp)))
+
+    def solve_sharded(self, A_local, b_local, row0, n_total, nu, x, allreduce_cb, tol=0.0):
+        """ihs_solve_sharded with an ALLREDUCE_FN callback (see shard.make_allreduce)."""
+        n, d = A_local.shape
+        rep = Report()
+        st = _lib.ihs_solve_sharded(self.handle, _ptr(A_local), _ptr(b_local), n, d, row0, n_total, float(nu),
+                                    float(tol), _ptr(x), ctypes.byref(rep), allreduce_cb, None)
+        if st not in (IHS_OK, IHS_EMAXITER):
+            _check("ihs_solve_sharded", st)
+        return rep
 
     def trace(self):
         """Decisions of the last solve as (event, t, m, ratio) tuples."""
