@@ -1,5 +1,6 @@
 // Context, scratch arena, parameters and status plumbing of the C ABI.
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <cudaTypedefs.h>
@@ -74,6 +75,13 @@ extern "C" int ihs_ctx_create(ihs_ctx** out, void* stream, const ihs_params* p) 
     memset(c, 0, sizeof(*c));
     c->p = prm;
     c->stream = static_cast<cudaStream_t>(stream);
+    {
+        const char* e = getenv("IHS_TEST_BARRIER_UNREACHABLE");
+        c->test_bar_unreachable = (e && e[0] == '1') ? 1 : 0;
+        const char* l = getenv("IHS_BARRIER_LIMIT_MS");
+        const long ms = l ? strtol(l, nullptr, 10) : 0;
+        c->bar_limit_ns = (ms >= 1 && ms <= 60000) ? (uint64_t)ms * 1000000ull : 1000000000ull;
+    }
     int st = IHS_OK;
     do {
         if (cudaGetDevice(&c->device) != cudaSuccess) { st = IHS_ECUDA; break; }

@@ -74,6 +74,14 @@ struct ihs_ctx {
     int no_coop;             // 1: factorisations use the multi-launch form (many run side by side)
     void* trace;             // decision log of the last solve (api.cu), NULL until first use
     uint64_t apply_epoch;    // arrivals so far on the fused apply's grid-barrier counter
+    // Test-only fault injection on the host side, read from the environment at
+    // creation and off by default: IHS_TEST_BARRIER_UNREACHABLE=1 makes the
+    // first grid barrier of this context's first persistent Cholesky ask for one
+    // arrival more than the grid can give (a wait that nothing completes);
+    // IHS_BARRIER_LIMIT_MS (default 1000) bounds the persistent Cholesky's
+    // barrier waits.
+    int test_bar_unreachable;
+    uint64_t bar_limit_ns;
 };
 
 // Decision log of the controller (api.cu): cleared at the start of a solve,

@@ -387,19 +387,20 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     return v;
 }
 
-__device__ __forceinline__ bool grid_sync_bounded(unsigned* cnt, unsigned& nbar, unsigned* status) {
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* cnt, unsigned& nbar, unsigned* status,
+                                                  unsigned extra, uint64_t limit_ns) {
     __shared__ int gs_ok;
     __syncthreads();
     ++nbar;
     if (threadIdx.x == 0) {
         gs_ok = 1;
-        const unsigned target = nbar * gridDim.x;
+        const unsigned target = nbar * gridDim.x + extra;
         __threadfence();   // the whole CTA's writes (ordered by the barrier above) before the arrival
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(cnt) : "memory");
         if (ld_acquire_gpu(cnt) < target) {
             const uint64_t t0 = global_timer_ns();
             while (ld_acquire_gpu(cnt) < target) {
-                if (global_timer_ns() - t0 > 1000000000ull) {
+                if (global_timer_ns() - t0 > limit_ns) {
                     atomicOr(status, IHS_DEV_TIMEOUT);
                     gs_ok = 0;
                     break;
@@ -566,7 +567,8 @@ __device__ void chol_potrf_df(CholSmemDf& S, double* __restrict__ Kmat, int64_t 
 
 __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Kmat, int64_t k,
                                                          double* __restrict__ Wall, unsigned* bar,
-                                                         unsigned* status) {
+                                                         unsigned* status, unsigned bar_extra,
+                                                         uint64_t bar_limit_ns) {
     __shared__ CholSmemDf S;
     // operands of the panel, column and trailing products as double-float pairs
     __shared__ float2 fa[CB][CB + 1];
@@ -696,7 +698,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 it = nx;
             }
         }
-        if (!grid_sync_bounded(bar, nbar, status)) return;
+        if (!grid_sync_bounded(bar, nbar, status, nbar == 0 ? bar_extra : 0u, bar_limit_ns)) return;
         const int64_t rest = k - j0 - nb;
         if (rest <= 0) break;
         // ---- phase N: panel jb = K L_jj^{-T} by forward substitution, 16 rows per
@@ -746,7 +748,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 if (rb < k) Pdf[rb * CB + lane] = xb;
             }
         }
-        if (!grid_sync_bounded(bar, nbar, status)) return;
+        if (!grid_sync_bounded(bar, nbar, status, nbar == 0 ? bar_extra : 0u, bar_limit_ns)) return;
         // ---- phase S: column block jb+1 updated by panel jb, 16 rows per work
         // item (thread (ty, tx) takes rows ty and ty + 8 of the item, column tx)
         {
@@ -785,7 +787,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                                        (((double)b0.hi + (double)b0.lo) + ((double)b1.hi + (double)b1.lo));
             }
         }
-        if (!grid_sync_bounded(bar, nbar, status)) return;
+        if (!grid_sync_bounded(bar, nbar, status, nbar == 0 ? bar_extra : 0u, bar_limit_ns)) return;
     }
 }
 
@@ -1116,7 +1118,12 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
             unsigned* bar = ctx->d_status + 16;
             IHS_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
             int64_t kk = k;
-            void* args[] = {&Kmat, &kk, &Wall, &bar, &ctx->d_status};
+            // test-only: the first launch of a context with the knob set gets an
+            // unreachable first barrier (see ihs_ctx)
+            unsigned extra = ctx->test_bar_unreachable ? 1u : 0u;
+            ctx->test_bar_unreachable = 0;
+            uint64_t limit = ctx->bar_limit_ns;
+            void* args[] = {&Kmat, &kk, &Wall, &bar, &ctx->d_status, &extra, &limit};
             IHS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_chol_persistent, dim3((unsigned)G), dim3(256),
                                                      args, 0, s));
             ihs_count_launch();
