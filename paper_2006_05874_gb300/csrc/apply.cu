@@ -4,19 +4,18 @@
 //
 // H_S = (SA)^T SA + nu^2 I (Eq. 3).  With X = L^{-1} (FP32, from the FP64
 // Cholesky K = L L^T of factor.cu) every application is a sequence of
-// matrix-vector products, with one step of iterative refinement against the
-// exact K in double-float:
+// matrix-vector products, with one step of iterative refinement whose
+// residual applies the exact operator K from the FP32 sketch in double-float:
 //   Woodbury form (m < d, App. B.4), K = nu^2 I_m + SA SA^T:
-//     t = SA g, u0 = X^T X t, res = t - K u0, u1 = u0 + X^T X res,
-//     gt = nu^-2 (g - SA^T u1)
+//     t = SA g, u0 = X^T X t, res = t - (nu^2 u0 + SA (SA^T u0)),
+//     u1 = u0 + X^T X res, gt = nu^-2 (g - SA^T u1)
 //   direct form (m >= d), K = SA^T SA + nu^2 I_d:
-//     u0 = X^T X g, res = g - K u0, gt = u1 = u0 + X^T X res.
-// K is kept as a double-float copy (both triangles) made before the Cholesky
-// overwrites it, and SA^T as an FP32 copy (Woodbury form), so that every stage
-// is a row-parallel product: a warp takes one (row, segment) item at a time,
-// a segment being 1024 FP32 or 512 double-float entries (eight 16-byte loads
-// per lane); the segment sums go to partial vectors that the next stage adds
-// up in a fixed order while it copies its input vector into shared memory.
+//     u0 = X^T X g, res = g - (nu^2 u0 + SA^T (SA u0)), gt = u1 = u0 + X^T X res.
+// SA^T is kept as an FP32 copy made with the factor, so that every stage is a
+// row-parallel product: a warp takes one (row, segment) item at a time, a
+// segment being 1024 entries (eight 16-byte loads per lane); the segment sums
+// go to partial vectors that the next stage adds up in a fixed order while it
+// copies its input vector into shared memory.
 // The stages are separated by grid barriers on a monotonic 64-bit arrival
 // counter (bounded waits: a wait that exceeds one second sets IHS_DEV_TIMEOUT
 // and the CTAs leave); each warp loads the matrix rows of its first two items
@@ -236,7 +235,6 @@ struct ApplyArgs {
     const float* SAT;    // d x m (Woodbury form)
     const float* X;      // k x k lower, L^{-1}
     const float* XT;     // k x k upper, its transpose
-    const float2* Kdf;   // k x k, K in double-float
     const float* g;      // d
     float* gt;           // d
     double* r_out;       // device scalar or NULL
@@ -248,6 +246,7 @@ struct ApplyArgs {
     int64_t m, d, k;
     int woodbury;
     double inv_nu2;
+    double nu2;
     unsigned long long* bar;
     unsigned long long base;
     unsigned* done;      // last-CTA ticket of the decrement (left at 0)
@@ -292,6 +291,15 @@ __device__ __forceinline__ void finish_decrement(const ApplyArgs& a, double prod
         }                                                                             \
     } while (0)
 
+// res = t - (nu^2 u + w) in double-float, nu^2 split into a binary32 pair.
+__device__ __forceinline__ float2 df_residual(float2 t, float2 u, double nu2, float2 w) {
+    const float sh = (float)nu2, sl = (float)(nu2 - (double)sh);
+    float p, e;
+    two_prod(u.x, sh, p, e);
+    const float2 nu2u = df_norm(p, __fadd_rn(e, __fmaf_rn(u.x, sl, __fmul_rn(u.y, sh))));
+    return df_sub(t, df_add(nu2u, w));
+}
+
 __global__ void __launch_bounds__(kApplyThreads, 1) k_apply_fused(const ApplyArgs a) {
     extern __shared__ float4 apply_smem[];
     float2* vd = reinterpret_cast<float2*>(apply_smem);   // stage input, double-float
@@ -302,17 +310,14 @@ __global__ void __launch_bounds__(kApplyThreads, 1) k_apply_fused(const ApplyArg
     const int64_t k = a.k, m = a.m, d = a.d;
     const Mat mX{a.X, k, k, 1, 0};
     const Mat mXT{a.XT, k, k, 2, 0};
-    const Mat mK{reinterpret_cast<const float*>(a.Kdf), k, k, 0, 1};
+    const Mat mSA{a.SA, m, d, 0, 0};
+    const Mat mSAT{a.SAT, d, m, 0, 0};
     const int64_t segX = kSegFloats, PX = (k + segX - 1) / segX;   // segments of X / X^T rows
-    const int64_t PK = (2 * k + kSegFloats - 1) / kSegFloats;       // segments of K rows
+    const int64_t PSA = (d + kSegFloats - 1) / kSegFloats;          // of SA rows
+    const int64_t PSAT = (m + kSegFloats - 1) / kSegFloats;         // of SA^T rows
     Pref P;
     int nb = 0;
-    // v = X w for the staged w, then u = X^T v: the two stages of X^T X w,
-    // results as segment sums in Yv and Yu.
     if (a.woodbury) {
-        const Mat mSA{a.SA, m, d, 0, 0};
-        const Mat mSAT{a.SAT, d, m, 0, 0};
-        const int64_t PSA = (d + kSegFloats - 1) / kSegFloats, PSAT = (m + kSegFloats - 1) / kSegFloats;
         // 1: t = SA g
         prefetch(mSA, gw, W, P);
         for (int64_t e = tid; e < d; e += kApplyThreads) vf[e] = __ldg(a.g + e);
@@ -330,37 +335,44 @@ __global__ void __launch_bounds__(kApplyThreads, 1) k_apply_fused(const ApplyArg
         for (int64_t i = tid; i < k; i += kApplyThreads) vd[i] = sum_parts(a.Y1, k, i, 0, i / segX + 1);
         __syncthreads();
         run_stage(mXT, gw, W, P, nullptr, vd, a.Y2);
-        prefetch(mK, gw, W, P);
-        IHS_APPLY_SYNC();
-        // 4: K u0
-        for (int64_t i = tid; i < k; i += kApplyThreads) vd[i] = sum_parts(a.Y2, k, i, i / segX, PX);
-        __syncthreads();
-        run_stage(mK, gw, W, P, nullptr, vd, a.Y3);
-        prefetch(mX, gw, W, P);
-        IHS_APPLY_SYNC();
-        // 5: v = X res, res = t - K u0
-        for (int64_t i = tid; i < k; i += kApplyThreads)
-            vd[i] = df_sub(sum_parts(a.Y0, m, i, 0, PSA), sum_parts(a.Y3, k, i, 0, PK));
-        __syncthreads();
-        run_stage(mX, gw, W, P, nullptr, vd, a.Y1);
-        prefetch(mXT, gw, W, P);
-        IHS_APPLY_SYNC();
-        // 6: X^T v
-        for (int64_t i = tid; i < k; i += kApplyThreads) vd[i] = sum_parts(a.Y1, k, i, 0, i / segX + 1);
-        __syncthreads();
-        run_stage(mXT, gw, W, P, nullptr, vd, a.Y3);
         prefetch(mSAT, gw, W, P);
         IHS_APPLY_SYNC();
-        // 7: w = SA^T u1, u1 = u0 + X^T v
-        for (int64_t i = tid; i < k; i += kApplyThreads)
-            vd[i] = df_add(sum_parts(a.Y2, k, i, i / segX, PX), sum_parts(a.Y3, k, i, i / segX, PX));
+        // 4: w = SA^T u0
+        for (int64_t i = tid; i < k; i += kApplyThreads) vd[i] = sum_parts(a.Y2, k, i, i / segX, PX);
         __syncthreads();
-        run_stage(mSAT, gw, W, P, nullptr, vd, a.Y1);
+        run_stage(mSAT, gw, W, P, nullptr, vd, a.Y3);
+        prefetch(mSA, gw, W, P);
         IHS_APPLY_SYNC();
-        // 8: gt = (g - w) / nu^2 and the decrement
+        // 5: w2 = SA w
+        for (int64_t c = tid; c < d; c += kApplyThreads) vd[c] = sum_parts(a.Y3, d, c, 0, PSAT);
+        __syncthreads();
+        run_stage(mSA, gw, W, P, nullptr, vd, a.Y1);
+        prefetch(mX, gw, W, P);
+        IHS_APPLY_SYNC();
+        // 6: v = X res, res = t - K u0 = t - (nu^2 u0 + w2)
+        for (int64_t i = tid; i < k; i += kApplyThreads)
+            vd[i] = df_residual(sum_parts(a.Y0, m, i, 0, PSA), sum_parts(a.Y2, k, i, i / segX, PX), a.nu2,
+                                sum_parts(a.Y1, m, i, 0, PSA));
+        __syncthreads();
+        run_stage(mX, gw, W, P, nullptr, vd, a.Y3);
+        prefetch(mXT, gw, W, P);
+        IHS_APPLY_SYNC();
+        // 7: X^T v
+        for (int64_t i = tid; i < k; i += kApplyThreads) vd[i] = sum_parts(a.Y3, k, i, 0, i / segX + 1);
+        __syncthreads();
+        run_stage(mXT, gw, W, P, nullptr, vd, a.Y1);
+        prefetch(mSAT, gw, W, P);
+        IHS_APPLY_SYNC();
+        // 8: w = SA^T u1, u1 = u0 + X^T v
+        for (int64_t i = tid; i < k; i += kApplyThreads)
+            vd[i] = df_add(sum_parts(a.Y2, k, i, i / segX, PX), sum_parts(a.Y1, k, i, i / segX, PX));
+        __syncthreads();
+        run_stage(mSAT, gw, W, P, nullptr, vd, a.Y3);
+        IHS_APPLY_SYNC();
+        // gt = (g - w) / nu^2 and the decrement
         double prod = 0.0;
         for (int64_t c = (int64_t)blockIdx.x * kApplyThreads + tid; c < d; c += (int64_t)gridDim.x * kApplyThreads) {
-            const float2 w = sum_parts(a.Y1, d, c, 0, PSAT);
+            const float2 w = sum_parts(a.Y3, d, c, 0, PSAT);
             const double gc = (double)__ldg(a.g + c);
             const double v = (gc - ((double)w.x + (double)w.y)) * a.inv_nu2;
             a.gt[c] = (float)v;
@@ -379,27 +391,34 @@ __global__ void __launch_bounds__(kApplyThreads, 1) k_apply_fused(const ApplyArg
         for (int64_t i = tid; i < k; i += kApplyThreads) vd[i] = sum_parts(a.Y1, k, i, 0, i / segX + 1);
         __syncthreads();
         run_stage(mXT, gw, W, P, nullptr, vd, a.Y2);
-        prefetch(mK, gw, W, P);
+        prefetch(mSA, gw, W, P);
         IHS_APPLY_SYNC();
-        // 3: K u0
+        // 3: w = SA u0
         for (int64_t i = tid; i < k; i += kApplyThreads) vd[i] = sum_parts(a.Y2, k, i, i / segX, PX);
         __syncthreads();
-        run_stage(mK, gw, W, P, nullptr, vd, a.Y3);
+        run_stage(mSA, gw, W, P, nullptr, vd, a.Y0);
+        prefetch(mSAT, gw, W, P);
+        IHS_APPLY_SYNC();
+        // 4: w2 = SA^T w
+        for (int64_t j = tid; j < m; j += kApplyThreads) vd[j] = sum_parts(a.Y0, m, j, 0, PSA);
+        __syncthreads();
+        run_stage(mSAT, gw, W, P, nullptr, vd, a.Y3);
         prefetch(mX, gw, W, P);
         IHS_APPLY_SYNC();
-        // 4: v = X res, res = g - K u0
+        // 5: v = X res, res = g - K u0 = g - (nu^2 u0 + w2)
         for (int64_t i = tid; i < k; i += kApplyThreads)
-            vd[i] = df_sub(make_float2(__ldg(a.g + i), 0.f), sum_parts(a.Y3, k, i, 0, PK));
+            vd[i] = df_residual(make_float2(__ldg(a.g + i), 0.f), sum_parts(a.Y2, k, i, i / segX, PX), a.nu2,
+                                sum_parts(a.Y3, d, i, 0, PSAT));
         __syncthreads();
         run_stage(mX, gw, W, P, nullptr, vd, a.Y1);
         prefetch(mXT, gw, W, P);
         IHS_APPLY_SYNC();
-        // 5: X^T v
+        // 6: X^T v
         for (int64_t i = tid; i < k; i += kApplyThreads) vd[i] = sum_parts(a.Y1, k, i, 0, i / segX + 1);
         __syncthreads();
         run_stage(mXT, gw, W, P, nullptr, vd, a.Y3);
         IHS_APPLY_SYNC();
-        // 6: gt = u1 = u0 + X^T v and the decrement
+        // gt = u1 = u0 + X^T v and the decrement
         double prod = 0.0;
         for (int64_t c = (int64_t)blockIdx.x * kApplyThreads + tid; c < d; c += (int64_t)gridDim.x * kApplyThreads) {
             const float2 u1 = df_add(sum_parts(a.Y2, k, c, c / segX, PX), sum_parts(a.Y3, k, c, c / segX, PX));
@@ -412,34 +431,8 @@ __global__ void __launch_bounds__(kApplyThreads, 1) k_apply_fused(const ApplyArg
 }
 
 // Barriers per launch of k_apply_fused.
-constexpr int kBarriersWoodbury = 7;
-constexpr int kBarriersDirect = 5;
-
-// Kdf = K in double-float, both triangles, from the lower triangle of K
-// (FP64, row-major k x k, nu^2 already on the diagonal): one 32 x 32 tile
-// (I, J), J <= I, per CTA, written at (I, J) and, transposed through shared
-// memory, at (J, I).
-__global__ void __launch_bounds__(256) k_kdf(const double* __restrict__ K, int64_t k, float2* __restrict__ Kdf) {
-    __shared__ float2 tile[32][33];
-    const int64_t t = blockIdx.x;
-    int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while (I * (I + 1) / 2 > t) --I;
-    while ((I + 1) * (I + 2) / 2 <= t) ++I;
-    const int64_t J = t - I * (I + 1) / 2;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t gr = I * 32 + r, gc = J * 32 + tx;
-        float2 v = make_float2(0.f, 0.f);
-        if (gr < k && gc <= gr) v = df_split(K[gr * k + gc]);
-        tile[r][tx] = v;
-        if (gr < k && gc <= gr) Kdf[gr * k + gc] = v;
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t gr = J * 32 + r, gc = I * 32 + tx;   // entry (gr, gc) = K(gc, gr), lower when gc >= gr
-        if (gr < k && gc < k && gc > gr) Kdf[gr * k + gc] = tile[tx][r];
-    }
-}
+constexpr int kBarriersWoodbury = 8;
+constexpr int kBarriersDirect = 6;
 
 // SAT = SA^T (SA: m x d row-major), 32 x 32 tiles.
 __global__ void __launch_bounds__(256) k_sat(const float* __restrict__ SA, int64_t m, int64_t d,
@@ -458,50 +451,38 @@ __global__ void __launch_bounds__(256) k_sat(const float* __restrict__ SA, int64
     }
 }
 
-size_t fused_smem_bytes(int64_t k, int64_t m, int64_t d, int woodbury) {
-    const size_t v = (size_t)k * sizeof(float2);
-    const size_t g = woodbury ? (size_t)d * sizeof(float) : 0;
-    return v > g ? v : g;
+size_t fused_smem_bytes(int64_t m, int64_t d) {
+    // the largest stage vector: max(m, d) double-float entries
+    return (size_t)std::max(m, d) * sizeof(float2);
 }
 
 }  // namespace
 
-// The fused apply needs 16-byte rows (k, d and, for the Woodbury form, m
-// multiples of 4) and its stage vector in shared memory (at most 16384
-// double-float entries, 128 KB).
+// The fused apply needs 16-byte rows (k, m and d multiples of 4) and its
+// stage vectors in shared memory (at most 16384 double-float entries, 128 KB).
 bool ihs_apply_fused_ok(int64_t k, int64_t m, int64_t d) {
-    const bool woodbury = m < d;
-    if (k < 4 || k % 4 || d % 4 || (woodbury && m % 4)) return false;
-    return fused_smem_bytes(k, m, d, woodbury) <= 128 * 1024 && d <= 32768;
+    if (k < 4 || k % 4 || d % 4 || m % 4) return false;
+    return fused_smem_bytes(m, d) <= 128 * 1024;
 }
 
 size_t ihs_apply_partials(int64_t k, int64_t m, int64_t d) {
     auto seg = [](int64_t floats) { return (floats + kSegFloats - 1) / kSegFloats; };
-    size_t n = (size_t)(seg(2 * k) * k);                  // K rows
-    n = std::max(n, (size_t)(seg(k) * k));                 // X, X^T rows
-    if (m < d) {
-        n = std::max(n, (size_t)(seg(d) * m));             // SA rows
-        n = std::max(n, (size_t)(seg(m) * d));             // SA^T rows
-    }
+    size_t n = (size_t)(seg(k) * k);                       // X, X^T rows
+    n = std::max(n, (size_t)(seg(d) * m));                 // SA rows
+    n = std::max(n, (size_t)(seg(m) * d));                 // SA^T rows
     return n;
 }
 
 int ihs_apply_prepare(ihs_ctx* ctx, ihs_factor_t* F) {
     if (!F->fused) return IHS_OK;
-    const int64_t k = F->k;
-    const int64_t T = (k + 31) / 32;
-    k_kdf<<<(unsigned)(T * (T + 1) / 2), 256, 0, ctx->stream>>>(F->L, k, F->Kdf);
+    dim3 grid((unsigned)ceil_div64(F->d, 32), (unsigned)ceil_div64(F->m, 32));
+    k_sat<<<grid, 256, 0, ctx->stream>>>(F->SA, F->m, F->d, F->SAT);
     IHS_LAUNCH_CHECK();
-    if (F->woodbury) {
-        dim3 grid((unsigned)ceil_div64(F->d, 32), (unsigned)ceil_div64(F->m, 32));
-        k_sat<<<grid, 256, 0, ctx->stream>>>(F->SA, F->m, F->d, F->SAT);
-        IHS_LAUNCH_CHECK();
-    }
     return IHS_OK;
 }
 
 int ihs_apply_fused(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt, double* d_r) {
-    const size_t smem = fused_smem_bytes(F->k, F->m, F->d, F->woodbury);
+    const size_t smem = fused_smem_bytes(F->m, F->d);
     // one fixed limit for every launch (the kernel also holds 4 KB of static
     // shared memory, so the device's whole opt-in maximum cannot be granted)
     IHS_CUDA_TRY(cudaFuncSetAttribute(k_apply_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
@@ -515,7 +496,6 @@ int ihs_apply_fused(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* 
     a.SAT = F->SAT;
     a.X = F->X;
     a.XT = F->XT;
-    a.Kdf = F->Kdf;
     a.g = g;
     a.gt = gt;
     a.r_out = d_r;
@@ -529,6 +509,7 @@ int ihs_apply_fused(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* 
     a.k = F->k;
     a.woodbury = F->woodbury;
     a.inv_nu2 = 1.0 / (F->nu * F->nu);
+    a.nu2 = F->nu * F->nu;
     a.bar = reinterpret_cast<unsigned long long*>(ctx->d_status + 32);
     a.base = ctx->apply_epoch;
     a.done = ctx->d_status + 40;

@@ -114,17 +114,16 @@ struct ihs_factor {
     double* work;         // apply scratch vectors and reduction slots
     int owned;            // 1: the buffers above are this handle's own allocations
     // fused apply (one cooperative launch, apply.cu); fused == 0 takes the
-    // multi-launch apply and leaves the three buffers below unset
+    // multi-launch apply and leaves the two buffers below unset
     int fused;
-    float2* Kdf;          // K = nu^2 I + SA SA^T (or SA^T SA + nu^2 I), k x k, both triangles, double-float
-    float* SAT;           // (SA)^T, d x m FP32 (Woodbury form only)
-    float2* Y;            // four partial-sum buffers of apply_partials(k, m, d) pairs each
+    float* SAT;           // (SA)^T, d x m FP32
+    float2* Y;            // four partial-sum buffers of ihs_apply_partials(k, m, d) pairs each
 };
 
 // Fused apply (apply.cu).
 bool ihs_apply_fused_ok(int64_t k, int64_t m, int64_t d);
 size_t ihs_apply_partials(int64_t k, int64_t m, int64_t d);   // float2 entries per partial buffer
-int ihs_apply_prepare(ihs_ctx* ctx, ihs_factor_t* F);          // Kdf (before the Cholesky) and SAT
+int ihs_apply_prepare(ihs_ctx* ctx, ihs_factor_t* F);          // SA^T
 int ihs_apply_fused(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt, double* d_r);
 
 int ihs_scratch(ihs_ctx* ctx, int slot, size_t bytes, void** out);

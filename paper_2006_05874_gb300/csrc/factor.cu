@@ -1097,7 +1097,7 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
             IHS_LAUNCH_CHECK();
         }
     }
-    // the fused apply's copies of K (before the Cholesky overwrites it) and SA^T
+    // the fused apply's copy of SA^T
     IHS_TRY(ihs_apply_prepare(ctx, F));
     // Blocked right-looking Cholesky with one step of look-ahead: on the main
     // stream, diagonal block jb, its panel and the update of block column jb+1;
@@ -1276,10 +1276,10 @@ static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Byte offsets of a factor's buffers in one block: K/L (FP64 k x k), the
 // diagonal-block inverses W, X = L^{-1} and X^T (FP32), the multi-launch
-// apply's work area, and for the fused apply the double-float K, SA^T and
-// four partial-sum buffers (+ one FP64 slot per CTA).
+// apply's work area, and for the fused apply SA^T and four partial-sum
+// buffers (+ one FP64 slot per CTA).
 struct FactorLayout {
-    size_t L, W, X, XT, work, Kdf, SAT, Y, total;
+    size_t L, W, X, XT, work, SAT, Y, total;
 };
 
 static FactorLayout factor_layout(int64_t k, int64_t m, int64_t d, bool fused, int sm_count) {
@@ -1297,14 +1297,10 @@ static FactorLayout factor_layout(int64_t k, int64_t m, int64_t d, bool fused, i
     o += align256(kk * sizeof(float));
     l.work = o;
     o += align256(factor_work_doubles(k, m, d) * sizeof(double));
-    l.Kdf = l.SAT = l.Y = 0;
+    l.SAT = l.Y = 0;
     if (fused) {
-        l.Kdf = o;
-        o += align256(kk * sizeof(float2));
-        if (m < d) {
-            l.SAT = o;
-            o += align256((size_t)m * d * sizeof(float));
-        }
+        l.SAT = o;
+        o += align256((size_t)m * d * sizeof(float));
         l.Y = o;
         o += align256((4 * ihs_apply_partials(k, m, d)) * sizeof(float2) + (size_t)sm_count * sizeof(double));
     }
@@ -1333,8 +1329,7 @@ static void factor_bind(ihs_factor_t* F, char* base, const FactorLayout& l) {
     F->XT = reinterpret_cast<float*>(base + l.XT);
     F->work = reinterpret_cast<double*>(base + l.work);
     if (F->fused) {
-        F->Kdf = reinterpret_cast<float2*>(base + l.Kdf);
-        F->SAT = F->woodbury ? reinterpret_cast<float*>(base + l.SAT) : nullptr;
+        F->SAT = reinterpret_cast<float*>(base + l.SAT);
         F->Y = reinterpret_cast<float2*>(base + l.Y);
     }
 }
