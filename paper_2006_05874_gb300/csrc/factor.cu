@@ -873,6 +873,117 @@ __global__ void __launch_bounds__(256) k_pair_gemm(const float* __restrict__ Xf,
         }
 }
 
+// The same pair products for blocks of s >= 128 (s a multiple of 128, k a
+// multiple of 8): 128 x 128 output tiles, 8 x 8 per thread, the inner
+// dimension in double-buffered chunks of 16 staged through shared memory with
+// 16-byte global loads (A from L is converted from FP64 on the fly).  tri
+// skips the inner range where a triangular operand is zero: 1 = B lower
+// (B[q][c] = 0 for q < c: q starts at the tile's first column), 2 = A lower
+// (A[r][q] = 0 for q > r: q ends after the tile's last row).
+constexpr int PGT = 128, PGK = 16;
+__global__ void __launch_bounds__(256) k_pair_sgemm(const float* __restrict__ Xf, const double* __restrict__ Ld,
+                                                    int a_is_l, int64_t k, int64_t s, int64_t pstride, int64_t ra,
+                                                    int64_t ca, int64_t rb, int64_t cb, const float* Bsrc,
+                                                    float* __restrict__ C, int64_t rc, int64_t cc, float alpha,
+                                                    int tri) {
+    __shared__ __align__(16) float As[2][PGK][PGT + 4];   // As[q][r]
+    __shared__ __align__(16) float Bs[2][PGK][PGT + 4];   // Bs[q][c]
+    const int tid = threadIdx.x;
+    const int64_t off = (int64_t)blockIdx.z * pstride;
+    const int64_t tr = (int64_t)blockIdx.y * PGT, tc = (int64_t)blockIdx.x * PGT;
+    int64_t q0 = 0, q1 = s;
+    if (tri == 1) q0 = tc;
+    if (tri == 2) q1 = min(s, tr + PGT);
+    // loaders: A row ar, inner elements [ak, ak + 8); B inner row bq, columns [bc, bc + 8)
+    const int ar = tid >> 1, ak = (tid & 1) * 8;
+    const int bq = tid >> 4, bc = (tid & 15) * 8;
+    const int64_t ga_r = ra + off + tr + ar;        // global row of A
+    const int64_t gb_c = cb + off + tc + bc;        // global column of B
+    float la[8], lb[8];
+    auto load = [&](int64_t q) {
+        const int64_t ga_c = ca + off + q + ak;     // global column of A
+        if (ga_r < k && ga_c < k) {
+            if (a_is_l) {
+                const double2* src = reinterpret_cast<const double2*>(Ld + ga_r * k + ga_c);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const double2 v = src[u];
+                    la[2 * u] = (float)v.x;
+                    la[2 * u + 1] = (float)v.y;
+                }
+            } else {
+                const float4* src = reinterpret_cast<const float4*>(Xf + ga_r * k + ga_c);
+                const float4 v0 = src[0], v1 = src[1];
+                la[0] = v0.x; la[1] = v0.y; la[2] = v0.z; la[3] = v0.w;
+                la[4] = v1.x; la[5] = v1.y; la[6] = v1.z; la[7] = v1.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) la[u] = 0.f;
+        }
+        const int64_t gb_r = rb + off + q + bq;     // global row of B
+        if (gb_r < k && gb_c < k) {
+            const float4* src = reinterpret_cast<const float4*>(Bsrc + gb_r * k + gb_c);
+            const float4 v0 = src[0], v1 = src[1];
+            lb[0] = v0.x; lb[1] = v0.y; lb[2] = v0.z; lb[3] = v0.w;
+            lb[4] = v1.x; lb[5] = v1.y; lb[6] = v1.z; lb[7] = v1.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) lb[u] = 0.f;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) As[buf][ak + u][ar] = la[u];
+        *reinterpret_cast<float4*>(&Bs[buf][bq][bc]) = make_float4(lb[0], lb[1], lb[2], lb[3]);
+        *reinterpret_cast<float4*>(&Bs[buf][bq][bc + 4]) = make_float4(lb[4], lb[5], lb[6], lb[7]);
+    };
+    const int ty = tid >> 4, tx = tid & 15;   // rows ty*4 + {0..3, 64..67}, columns tx*4 + {0..3, 64..67}
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    int buf = 0;
+    if (q0 < q1) {
+        load(q0);
+        store(0);
+    }
+    __syncthreads();
+    for (int64_t q = q0; q < q1; q += PGK) {
+        const bool more = q + PGK < q1;
+        if (more) load(q + PGK);
+#pragma unroll
+        for (int kk = 0; kk < PGK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = __fmaf_rn(av[i], bv[j], acc[i][j]);
+        }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = tr + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        const int64_t gr = rc + off + r;
+        if (r >= s || gr >= k) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t c = tc + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+            const int64_t gc = cc + off + c;
+            if (c < s && gc < k) C[gr * k + gc] = alpha * acc[i][j];
+        }
+    }
+}
+
 // XT = X^T for FP32 lower-triangular X.
 __global__ void k_transpose_f32(const float* __restrict__ X, int64_t k, float* __restrict__ XT) {
     __shared__ float tile[32][33];
@@ -1176,6 +1287,16 @@ inverse:
         const int64_t pairs = ceil_div64(k, 2 * sz);
         const int64_t tiles = ceil_div64(sz, FB);
         dim3 grid((unsigned)tiles, (unsigned)tiles, (unsigned)pairs);
+        if (sz % PGT == 0 && k % 8 == 0) {
+            const int64_t t2 = sz / PGT;
+            dim3 g2((unsigned)t2, (unsigned)t2, (unsigned)pairs);
+            // tmp21 = L21 X11 (X11 lower), X21 = -X22 tmp21 (X22 lower)
+            k_pair_sgemm<<<g2, 256, 0, s>>>(X, F->L, 1, k, sz, 2 * sz, sz, 0, 0, 0, X, tmp, sz, 0, 1.0f, 1);
+            IHS_LAUNCH_CHECK();
+            k_pair_sgemm<<<g2, 256, 0, s>>>(X, nullptr, 0, k, sz, 2 * sz, sz, sz, sz, 0, tmp, X, sz, 0, -1.0f, 2);
+            IHS_LAUNCH_CHECK();
+            continue;
+        }
         // tmp21 = L21 X11   (L21 at rows [sz, 2sz), cols [0, sz) of the pair)
         k_pair_gemm<<<grid, 256, 0, s>>>(X, F->L, 1, k, sz, 2 * sz, sz, 0, 0, 0, X, tmp, sz, 0, 1.0f);
         IHS_LAUNCH_CHECK();

@@ -592,10 +592,10 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
     CUtensorMap amap;
     const bool tma = Q == 1024 && ihs_tensor_map_f32(&amap, A, n, d, d, kR32C, 256) == IHS_OK;
     if (tma) {
-        // Selected rows go in chunks of at most 1024 (32 register accumulators
+        // Selected rows go in chunks of at most 2048 (64 register accumulators
         // per thread); each chunk re-reads A.  Chunks of <= 256 rows run the
         // 512-row-block kernel at two CTAs per SM, larger ones the 1024-row one.
-        const int64_t chunk = std::min<int64_t>(m, 1024);
+        const int64_t chunk = std::min<int64_t>(m, 2048);
         const int64_t CT32 = ceil_div64(d, kR32C);
         const bool small = m <= 256;
         // a grid of CT32 x PG32 CTAs in whole waves when the block ranges allow
@@ -624,7 +624,8 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
             else if (mc <= 128) st = launch_q512<8>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, gblk, part);
             else if (mc <= 256) st = launch_q512<16>(ctx, amap, (int)d, mc, m, c0, 2 * P, (int)PG, rows + c0, level, seed, gblk, part);
             else if (mc <= 32 * 16) st = launch_r32<16>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, gblk, part);
-            else st = launch_r32<32>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, gblk, part);
+            else if (mc <= 32 * 32) st = launch_r32<32>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, gblk, part);
+            else st = launch_r32<64>(ctx, amap, (int)d, mc, m, c0, P, (int)PG, rows + c0, level, seed, gblk, part);
             IHS_TRY(st);
         }
     } else {

@@ -56,10 +56,11 @@ def test_srht_full_size_sampled_rows(ctx, torch_cuda):
         assert _relfro(got[j], ref[k]) <= TOL
 
 
-@pytest.mark.parametrize("m,which", [(16, [0, 7, 15]), (200, [0, 99, 199])])
+@pytest.mark.parametrize("m,which", [(16, [0, 7, 15]), (200, [0, 99, 199]), (2048, [0, 1023, 1024, 1500, 2047])])
 def test_srht_full_size_small_m_sampled_rows(ctx, torch_cuda, m, which):
-    """131072 x 2048 at the small sketch sizes of the first levels (512-row
-    block kernel): sampled rows against explicit +-1 sums."""
+    """131072 x 2048 at the sketch sizes of the first levels (512-row block
+    kernel) and of the last one (m = 2048, one pass with 64 accumulators per
+    thread): sampled rows against explicit +-1 sums."""
     A = problems.random_matrix(131072, 2048, seed=14, scale=1.0 / 45.0)
     got = _sketch(torch_cuda, ctx, A, m, "srht", 0, 4)
     ref = sketch.srht_rows_explicit(A, m, 0, 4, which=which)
