@@ -107,7 +107,9 @@ struct ihs_factor {
     int64_t m, d, k;      // k = m (Woodbury) or d (direct)
     double nu;
     int woodbury;
-    double* L;            // k x k: K, then its lower Cholesky factor (row-major, FP64)
+    double* L;            // k x k: K, then its lower Cholesky factor (row-major; FP64, or
+                          // double-float pairs in the same 8 bytes when l_df)
+    int l_df;             // 1: L holds (hi, lo) binary32 pairs (persistent Cholesky)
     double* W;            // inverses of the 64 x 64 diagonal blocks of L (FP64)
     float* X;             // k x k lower inverse L^{-1} (FP32)
     float* XT;            // its transpose (upper)

@@ -41,7 +41,8 @@ constexpr int FB = 64;   // block size of the FP64 Cholesky and of the inverse
 // tile of float2 per (split, tile)) for k_gram_reduce, else straight to G.
 __global__ void __launch_bounds__(256) k_gram_c32(const float* __restrict__ SA, int64_t d, int woodbury,
                                                   int64_t kdim, int64_t K, int64_t kchunk, double nu2,
-                                                  double* __restrict__ G, float2* __restrict__ part) {
+                                                  float2 nu2df, int out_df, double* __restrict__ G,
+                                                  float2* __restrict__ part) {
     __shared__ float xa[32][FB + 4];
     __shared__ float xb[32][FB + 4];
     const int64_t t = blockIdx.x;
@@ -113,14 +114,29 @@ __global__ void __launch_bounds__(256) k_gram_c32(const float* __restrict__ SA, 
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int64_t r = I * FB + ty + 16 * a, c = J * FB + tx + 16 * b;
-            if (r < kdim && c < kdim && c <= r)
-                G[r * kdim + c] = (double)hi[a][b] + (double)lo[a][b] + (r == c ? nu2 : 0.0);
+            if (r < kdim && c < kdim && c <= r) {
+                if (out_df) {   // double-float pairs, the FP32 pipes only
+                    float s, e;
+                    two_sum(hi[a][b], lo[a][b], s, e);
+                    float2 v = make_float2(s, e);
+                    if (r == c) {
+                        float s2, e2;
+                        two_sum(v.x, nu2df.x, s2, e2);
+                        const float l2 = __fadd_rn(e2, __fadd_rn(v.y, nu2df.y));
+                        const float s3 = __fadd_rn(s2, l2);
+                        v = make_float2(s3, __fsub_rn(l2, __fsub_rn(s3, s2)));
+                    }
+                    reinterpret_cast<float2*>(G)[r * kdim + c] = v;
+                } else {
+                    G[r * kdim + c] = (double)hi[a][b] + (double)lo[a][b] + (r == c ? nu2 : 0.0);
+                }
+            }
         }
 }
 
 // G tile t = sum over the KS splits (fixed order, FP64) of hi + lo, + nu^2 I.
 __global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ part, int KS, int64_t ntiles,
-                                                     int64_t kdim, double nu2, double* __restrict__ G) {
+                                                     int64_t kdim, double nu2, int out_df, double* __restrict__ G) {
     const int64_t t = blockIdx.x;
     int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
     while (I * (I + 1) / 2 > t) --I;
@@ -135,7 +151,9 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ 
             const float2 v = part[((size_t)y * ntiles + t) * FB * FB + e];
             acc += (double)v.x + (double)v.y;
         }
-        G[r * kdim + c] = acc + (r == c ? nu2 : 0.0);
+        const double v = acc + (r == c ? nu2 : 0.0);
+        if (out_df) reinterpret_cast<float2*>(G)[r * kdim + c] = df_split(v);
+        else G[r * kdim + c] = v;
     }
 }
 
@@ -445,6 +463,29 @@ __device__ __forceinline__ float2 df_fnms(float2 k, float2 x, float2 y) {
     return make_float2(t, __fsub_rn(e, __fsub_rn(t, s)));
 }
 
+// Sums of double-float pairs (binary32 hi + lo): the result renormalised.
+__device__ __forceinline__ float2 pair_norm(float hi, float lo) {   // |hi| >= |lo|
+    const float s = __fadd_rn(hi, lo);
+    return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
+}
+
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    return pair_norm(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+
+__device__ __forceinline__ float2 pair_sub(float2 a, float2 b) { return pair_add(a, make_float2(-b.x, -b.y)); }
+
+// Lower-triangle tile (I, J), J <= I, of linear index t = I (I + 1) / 2 + J
+// (binary32 square root, corrected exactly in integers).
+__device__ __forceinline__ void tri_tile(int64_t t, int64_t& I, int64_t& J) {
+    I = (int64_t)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while (I * (I + 1) / 2 > t) --I;
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    J = t - I * (I + 1) / 2;
+}
+
 // 1 / sqrt(p) for a positive double-float p: the single-precision estimate
 // rsqrtf(p.hi) refined by two Newton-Raphson steps for f(y) = 1/y^2 - p,
 // y <- y + y (1 - p y^2) / 2, with the residual 1 - p y^2 formed in
@@ -474,7 +515,7 @@ __device__ __forceinline__ float2 df_rsqrt(float2 p) {
 // thread 0 runs the pivot chain with one column of look-ahead while threads
 // 32..255 apply column j to the packed trailing entries; columns stay
 // unscaled until a final pass forms L_rc = a_rc / sqrt(p_c).  L goes back to
-// Kmat in FP64, 1 / L_cc to Wd[0..CB).  Rows and columns >= nb are padded with
+// Kmat as double-float pairs, 1 / L_cc to Wd[0..CB) in FP64.  Rows and columns >= nb are padded with
 // the identity; a non-positive or non-finite pivot sets IHS_DEV_NOTPD (and is
 // replaced by 1).
 struct CholSmemDf {
@@ -483,7 +524,7 @@ struct CholSmemDf {
     int bad;
 };
 
-__device__ void chol_potrf_df(CholSmemDf& S, double* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
+__device__ void chol_potrf_df(CholSmemDf& S, float2* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
                               double* __restrict__ Wd, unsigned* status) {
     static_assert(CB == 32, "the packed entry mapping assumes CB = 32 and 256 threads");
     const int tid = threadIdx.x;
@@ -492,7 +533,7 @@ __device__ void chol_potrf_df(CholSmemDf& S, double* __restrict__ Kmat, int64_t 
         const int r = e / CB, c = e % CB;
         float2 v = make_float2(0.f, 0.f);
         if (c <= r) {
-            if (r < nb) v = c < nb ? df_split(__ldcg(Kmat + (j0 + r) * k + j0 + c)) : make_float2(0.f, 0.f);
+            if (r < nb) v = c < nb ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : make_float2(0.f, 0.f);
             else v = make_float2(r == c ? 1.f : 0.f, 0.f);
         }
         S.a[r][c] = v;
@@ -556,16 +597,13 @@ __device__ void chol_potrf_df(CholSmemDf& S, double* __restrict__ Kmat, int64_t 
     }
     for (int e = tid; e < CB * CB; e += 256) {
         const int r = e / CB, c = e % CB;
-        if (c <= r && r < nb && c < nb) {
-            const float2 l = df_mul2(S.a[r][c], S.dinv[c]);
-            Kmat[(j0 + r) * k + j0 + c] = (double)l.x + (double)l.y;
-        }
+        if (c <= r && r < nb && c < nb) Kmat[(j0 + r) * k + j0 + c] = df_mul2(S.a[r][c], S.dinv[c]);
     }
     if (tid < CB) Wd[tid] = tid < nb ? (double)S.dinv[tid].x + (double)S.dinv[tid].y : 0.0;   // 1 / L_cc
     if (tid == 0 && S.bad) atomicOr(status, IHS_DEV_NOTPD);
 }
 
-__global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Kmat, int64_t k,
+__global__ void __launch_bounds__(256) k_chol_persistent(float2* __restrict__ Kmat, int64_t k,
                                                          double* __restrict__ Wall, unsigned* bar,
                                                          unsigned* status, unsigned bar_extra,
                                                          uint64_t bar_limit_ns) {
@@ -596,13 +634,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
             // 16-row halves so that the short last steps spread wider
             const int H = (Tr * (Tr - 1) / 2 < 2 * (int64_t)workers) ? 2 : 1;
             const int64_t total = ntile * H;
-            auto tile_of = [&](int64_t it, int64_t& I, int64_t& J) {
-                const int64_t t = it / H;
-                I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-                while (I * (I + 1) / 2 > t) --I;
-                while ((I + 1) * (I + 2) / 2 <= t) ++I;
-                J = t - I * (I + 1) / 2;
-            };
+            auto tile_of = [&](int64_t it, int64_t& I, int64_t& J) { tri_tile(it / H, I, J); };
             // column block jb (J = 0) was done in phase S of step jb-1
             auto next_item = [&](int64_t it) -> int64_t {
                 for (; it < total; it += workers) {
@@ -644,16 +676,16 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 __syncthreads();
                 const int64_t nx = next_item(it + workers);
                 if (nx < total) fetch(nx);
-                // the rank-32 product in double-float on the FP32 pipes, the
-                // subtraction from K in FP64
+                // the rank-32 product and the subtraction from K in double-float
+                // on the FP32 pipes
                 if (H == 1) {
-                    double kold[2][2];
+                    float2 kold[2][2];
 #pragma unroll
                     for (int a = 0; a < 2; ++a)
 #pragma unroll
                         for (int b = 0; b < 2; ++b) {
                             const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
-                            kold[a][b] = (r < k && c <= r) ? __ldcg(Kmat + r * k + c) : 0.0;
+                            kold[a][b] = (r < k && c <= r) ? __ldcg(Kmat + r * k + c) : make_float2(0.f, 0.f);
                         }
                     Acc2 acc[2][2] = {};
 #pragma unroll 4
@@ -671,16 +703,16 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                         for (int b = 0; b < 2; ++b) {
                             const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
                             if (r < k && c <= r)
-                                Kmat[r * k + c] = kold[a][b] - ((double)acc[a][b].hi + (double)acc[a][b].lo);
+                                Kmat[r * k + c] = pair_sub(kold[a][b], pair_norm(acc[a][b].hi, acc[a][b].lo));
                         }
                 } else {
                     // rows ty + 16 hsel only
                     const int ra = ty + 16 * hsel;
-                    double kold[2];
+                    float2 kold[2];
 #pragma unroll
                     for (int b = 0; b < 2; ++b) {
                         const int64_t r = j1 + I * CB + ra, c = j1 + J * CB + tx + 16 * b;
-                        kold[b] = (r < k && c <= r) ? __ldcg(Kmat + r * k + c) : 0.0;
+                        kold[b] = (r < k && c <= r) ? __ldcg(Kmat + r * k + c) : make_float2(0.f, 0.f);
                     }
                     Acc2 acc[2] = {};
 #pragma unroll 4
@@ -692,7 +724,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
 #pragma unroll
                     for (int b = 0; b < 2; ++b) {
                         const int64_t r = j1 + I * CB + ra, c = j1 + J * CB + tx + 16 * b;
-                        if (r < k && c <= r) Kmat[r * k + c] = kold[b] - ((double)acc[b].hi + (double)acc[b].lo);
+                        if (r < k && c <= r) Kmat[r * k + c] = pair_sub(kold[b], pair_norm(acc[b].hi, acc[b].lo));
                     }
                 }
                 it = nx;
@@ -715,7 +747,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                     // L_jj and 1 / L_cc as double-float pairs, once per step
                     for (int e = tid; e < CB * CB; e += 256) {
                         const int r = e / CB, c = e % CB;
-                        fa[r][c] = df_split((c <= r && r < nb) ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : 0.0);
+                        fa[r][c] = (c <= r && r < nb) ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : make_float2(0.f, 0.f);
                     }
                     if (tid < CB) fb[0][tid] = df_split(__ldcg(dinv + tid));
                     __syncthreads();
@@ -723,8 +755,8 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 }
                 // substitution in double-float (FP32 latencies on the dependent chains)
                 const int64_t ra = r0 + wq, rb = r0 + 8 + wq;
-                float2 ka = df_split((ra < k && lane < nb) ? __ldcg(Kmat + ra * k + j0 + lane) : 0.0);
-                float2 kb = df_split((rb < k && lane < nb) ? __ldcg(Kmat + rb * k + j0 + lane) : 0.0);
+                float2 ka = (ra < k && lane < nb) ? __ldcg(Kmat + ra * k + j0 + lane) : make_float2(0.f, 0.f);
+                float2 kb = (rb < k && lane < nb) ? __ldcg(Kmat + rb * k + j0 + lane) : make_float2(0.f, 0.f);
                 float2 xa = make_float2(0.f, 0.f), xb = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < CB; ++c) {
@@ -742,9 +774,9 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                         kb = df_fnms(kb, xcb, lc);
                     }
                 }
-                if (ra < k && lane < nb) Kmat[ra * k + j0 + lane] = (double)xa.x + (double)xa.y;
+                if (ra < k && lane < nb) Kmat[ra * k + j0 + lane] = xa;
                 if (ra < k) Pdf[ra * CB + lane] = xa;   // 0 for lanes >= nb
-                if (rb < k && lane < nb) Kmat[rb * k + j0 + lane] = (double)xb.x + (double)xb.y;
+                if (rb < k && lane < nb) Kmat[rb * k + j0 + lane] = xb;
                 if (rb < k) Pdf[rb * CB + lane] = xb;
             }
         }
@@ -780,11 +812,11 @@ __global__ void __launch_bounds__(256) k_chol_persistent(double* __restrict__ Km
                 const int64_t c = j1 + tx;
                 const int64_t ra = r0 + ty, rb = r0 + 8 + ty;
                 if (ra < k && tx < ncol && c <= ra)
-                    Kmat[ra * k + c] = __ldcg(Kmat + ra * k + c) -
-                                       (((double)a0.hi + (double)a0.lo) + ((double)a1.hi + (double)a1.lo));
+                    Kmat[ra * k + c] = pair_sub(__ldcg(Kmat + ra * k + c),
+                                                pair_add(pair_norm(a0.hi, a0.lo), pair_norm(a1.hi, a1.lo)));
                 if (rb < k && tx < ncol && c <= rb)
-                    Kmat[rb * k + c] = __ldcg(Kmat + rb * k + c) -
-                                       (((double)b0.hi + (double)b0.lo) + ((double)b1.hi + (double)b1.lo));
+                    Kmat[rb * k + c] = pair_sub(__ldcg(Kmat + rb * k + c),
+                                                pair_add(pair_norm(b0.hi, b0.lo), pair_norm(b1.hi, b1.lo)));
             }
         }
         if (!grid_sync_bounded(bar, nbar, status, nbar == 0 ? bar_extra : 0u, bar_limit_ns)) return;
@@ -799,14 +831,24 @@ __global__ void k_zero_f32(float* __restrict__ X, int64_t count) {
     if (idx < count) X[idx] = 0.f;
 }
 
-__global__ void __launch_bounds__(FB) k_blockinv32(const double* __restrict__ L, int64_t k, float* __restrict__ X) {
+// L as FP64 (l_df = 0) or as double-float pairs (l_df = 1): its value in FP32.
+__device__ __forceinline__ float l_entry(const double* L, int l_df, int64_t idx) {
+    if (l_df) {
+        const float2 v = reinterpret_cast<const float2*>(L)[idx];
+        return __fadd_rn(v.x, v.y);
+    }
+    return (float)L[idx];
+}
+
+__global__ void __launch_bounds__(FB) k_blockinv32(const double* __restrict__ L, int l_df, int64_t k,
+                                                   float* __restrict__ X) {
     __shared__ float l[FB][FB + 1];
     __shared__ float w[FB][FB + 1];
     const int64_t b0 = (int64_t)blockIdx.x * FB;
     const int nb = (int)(k - b0 < FB ? k - b0 : FB);
     for (int e = threadIdx.x; e < FB * FB; e += FB) {
         const int r = e / FB, c = e % FB;
-        l[r][c] = (r < nb && c < nb && c <= r) ? (float)L[(b0 + r) * k + b0 + c] : 0.f;
+        l[r][c] = (r < nb && c < nb && c <= r) ? l_entry(L, l_df, (b0 + r) * k + b0 + c) : 0.f;
     }
     __syncthreads();
     const int c = threadIdx.x;
@@ -826,7 +868,7 @@ __global__ void __launch_bounds__(FB) k_blockinv32(const double* __restrict__ L,
 //   A_p at (ra + p*pstride, ca + p*pstride), B_p at (rb + p*pstride, cb + p*pstride), ...
 // Size s x s x s.  A is float (X) or double (L) by `a_is_l`.
 __global__ void __launch_bounds__(256) k_pair_gemm(const float* __restrict__ Xf, const double* __restrict__ Ld,
-                                                   int a_is_l, int64_t k, int64_t s, int64_t pstride,
+                                                   int a_is_l, int l_df, int64_t k, int64_t s, int64_t pstride,
                                                    int64_t ra, int64_t ca, int64_t rb, int64_t cb, const float* Bsrc,
                                                    float* __restrict__ C, int64_t rc, int64_t cc, float alpha) {
     __shared__ float as[32][FB + 4];
@@ -843,7 +885,7 @@ __global__ void __launch_bounds__(256) k_pair_gemm(const float* __restrict__ Xf,
             const int64_t gr = ra + off + tr + rr, gq = ca + off + q0 + qq;
             float v = 0.f;
             if (tr + rr < s && q0 + qq < s && gr < k && gq < k)
-                v = a_is_l ? (float)Ld[gr * k + gq] : Xf[gr * k + gq];
+                v = a_is_l ? l_entry(Ld, l_df, gr * k + gq) : Xf[gr * k + gq];
             as[qq][rr] = v;
             const int qq2 = e / FB, cc2 = e % FB;
             const int64_t br = rb + off + q0 + qq2, bc = cb + off + tc + cc2;
@@ -882,7 +924,8 @@ __global__ void __launch_bounds__(256) k_pair_gemm(const float* __restrict__ Xf,
 // (A[r][q] = 0 for q > r: q ends after the tile's last row).
 constexpr int PGT = 128, PGK = 16;
 __global__ void __launch_bounds__(256) k_pair_sgemm(const float* __restrict__ Xf, const double* __restrict__ Ld,
-                                                    int a_is_l, int64_t k, int64_t s, int64_t pstride, int64_t ra,
+                                                    int a_is_l, int l_df, int64_t k, int64_t s, int64_t pstride,
+                                                    int64_t ra,
                                                     int64_t ca, int64_t rb, int64_t cb, const float* Bsrc,
                                                     float* __restrict__ C, int64_t rc, int64_t cc, float alpha,
                                                     int tri) {
@@ -903,7 +946,15 @@ __global__ void __launch_bounds__(256) k_pair_sgemm(const float* __restrict__ Xf
     auto load = [&](int64_t q) {
         const int64_t ga_c = ca + off + q + ak;     // global column of A
         if (ga_r < k && ga_c < k) {
-            if (a_is_l) {
+            if (a_is_l && l_df) {
+                const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(Ld) + ga_r * k + ga_c);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float4 v = src[u];   // two (hi, lo) pairs
+                    la[2 * u] = __fadd_rn(v.x, v.y);
+                    la[2 * u + 1] = __fadd_rn(v.z, v.w);
+                }
+            } else if (a_is_l) {
                 const double2* src = reinterpret_cast<const double2*>(Ld + ga_r * k + ga_c);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -1186,6 +1237,23 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
     double* Kmat = F->L;
     double* Wall = F->W;
     const int64_t K = F->woodbury ? F->d : F->m;
+    // One cooperative launch of the Cholesky when the context allows it
+    // (contexts that run many factorisations side by side take the stream
+    // version); that path keeps K and L as double-float pairs (the FP32 pipes
+    // only), the stream version in FP64.
+    const int64_t TC = ceil_div64(k, CB);
+    int Gcoop = 0;
+    if (!ctx->no_coop && TC > 1) {
+        int per_sm = 0;
+        IHS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_persistent, 256, 0));
+        const int64_t first_tiles = (TC - 1) * TC / 2;
+        Gcoop = (int)std::min<int64_t>(ctx->sm_count, std::max<int64_t>(1, (first_tiles + 1) / 2));
+        Gcoop = std::min(Gcoop, per_sm * ctx->sm_count);
+    }
+    F->l_df = Gcoop >= 1 ? 1 : 0;
+    const double nu2 = F->nu * F->nu;
+    const float nu2_hi = (float)nu2;
+    const float2 nu2df = make_float2(nu2_hi, (float)(nu2 - (double)nu2_hi));
     {
         // split the inner dimension so that at least two CTAs per SM work on
         // the Gram, with at least 256 inner rows per split
@@ -1201,10 +1269,10 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
             gpart = static_cast<float2*>(ws);
         }
         k_gram_c32<<<dim3((unsigned)ntiles, (unsigned)KS), 256, 0, s>>>(F->SA, F->d, F->woodbury, k, K, kchunk,
-                                                                        F->nu * F->nu, Kmat, gpart);
+                                                                        nu2, nu2df, F->l_df, Kmat, gpart);
         IHS_LAUNCH_CHECK();
         if (KS > 1) {
-            k_gram_reduce<<<(unsigned)ntiles, 256, 0, s>>>(gpart, (int)KS, ntiles, k, F->nu * F->nu, Kmat);
+            k_gram_reduce<<<(unsigned)ntiles, 256, 0, s>>>(gpart, (int)KS, ntiles, k, nu2, F->l_df, Kmat);
             IHS_LAUNCH_CHECK();
         }
     }
@@ -1216,16 +1284,9 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
     // which overlaps the factorisation of block jb+1.  Events order the
     // writes: the update of column jb+1 (main) follows the previous rest
     // update (aux), and each rest update follows its panel.
-    const int64_t TC = ceil_div64(k, CB);
-    // One cooperative launch when the context allows it (contexts that run many
-    // factorisations side by side take the stream version below).
-    if (!ctx->no_coop && TC > 1) {
-        int per_sm = 0;
-        IHS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_persistent, 256, 0));
-        const int64_t first_tiles = (TC - 1) * TC / 2;
-        int G = (int)std::min<int64_t>(ctx->sm_count, std::max<int64_t>(1, (first_tiles + 1) / 2));
-        G = std::min(G, per_sm * ctx->sm_count);
-        if (G >= 1) {
+    if (F->l_df) {
+        const int G = Gcoop;
+        {
             unsigned* bar = ctx->d_status + 16;
             IHS_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
             int64_t kk = k;
@@ -1234,7 +1295,8 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
             unsigned extra = ctx->test_bar_unreachable ? 1u : 0u;
             ctx->test_bar_unreachable = 0;
             uint64_t limit = ctx->bar_limit_ns;
-            void* args[] = {&Kmat, &kk, &Wall, &bar, &ctx->d_status, &extra, &limit};
+            float2* Kdf = reinterpret_cast<float2*>(Kmat);
+            void* args[] = {&Kdf, &kk, &Wall, &bar, &ctx->d_status, &extra, &limit};
             IHS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_chol_persistent, dim3((unsigned)G), dim3(256),
                                                      args, 0, s));
             ihs_count_launch();
@@ -1281,7 +1343,7 @@ inverse:
     float* tmp = F->XT;   // scratch for L21 X11 (overwritten by X^T at the end)
     k_zero_f32<<<(unsigned)ceil_div64(k * k, 256), 256, 0, s>>>(X, k * k);
     IHS_LAUNCH_CHECK();
-    k_blockinv32<<<(unsigned)T, FB, 0, s>>>(F->L, k, X);
+    k_blockinv32<<<(unsigned)T, FB, 0, s>>>(F->L, F->l_df, k, X);
     IHS_LAUNCH_CHECK();
     for (int64_t sz = FB; sz < k; sz *= 2) {
         const int64_t pairs = ceil_div64(k, 2 * sz);
@@ -1291,18 +1353,18 @@ inverse:
             const int64_t t2 = sz / PGT;
             dim3 g2((unsigned)t2, (unsigned)t2, (unsigned)pairs);
             // tmp21 = L21 X11 (X11 lower), X21 = -X22 tmp21 (X22 lower)
-            k_pair_sgemm<<<g2, 256, 0, s>>>(X, F->L, 1, k, sz, 2 * sz, sz, 0, 0, 0, X, tmp, sz, 0, 1.0f, 1);
+            k_pair_sgemm<<<g2, 256, 0, s>>>(X, F->L, 1, F->l_df, k, sz, 2 * sz, sz, 0, 0, 0, X, tmp, sz, 0, 1.0f, 1);
             IHS_LAUNCH_CHECK();
-            k_pair_sgemm<<<g2, 256, 0, s>>>(X, nullptr, 0, k, sz, 2 * sz, sz, sz, sz, 0, tmp, X, sz, 0, -1.0f, 2);
+            k_pair_sgemm<<<g2, 256, 0, s>>>(X, nullptr, 0, 0, k, sz, 2 * sz, sz, sz, sz, 0, tmp, X, sz, 0, -1.0f, 2);
             IHS_LAUNCH_CHECK();
             continue;
         }
         // tmp21 = L21 X11   (L21 at rows [sz, 2sz), cols [0, sz) of the pair)
-        k_pair_gemm<<<grid, 256, 0, s>>>(X, F->L, 1, k, sz, 2 * sz, sz, 0, 0, 0, X, tmp, sz, 0, 1.0f);
+        k_pair_gemm<<<grid, 256, 0, s>>>(X, F->L, 1, F->l_df, k, sz, 2 * sz, sz, 0, 0, 0, X, tmp, sz, 0, 1.0f);
         IHS_LAUNCH_CHECK();
         // X21 = -X22 tmp21 (X is both the A operand and C: X22 is read, the
         // disjoint block X21 written)
-        k_pair_gemm<<<grid, 256, 0, s>>>(X, nullptr, 0, k, sz, 2 * sz, sz, sz, sz, 0, tmp, X, sz, 0, -1.0f);
+        k_pair_gemm<<<grid, 256, 0, s>>>(X, nullptr, 0, 0, k, sz, 2 * sz, sz, sz, sz, 0, tmp, X, sz, 0, -1.0f);
         IHS_LAUNCH_CHECK();
     }
     dim3 tg((unsigned)ceil_div64(k, 32), (unsigned)ceil_div64(k, 32));

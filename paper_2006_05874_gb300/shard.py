@@ -74,7 +74,8 @@ def make_allreduce(reduce_fn):
     def cb(user, buf, count, dtype, stream):
         try:
             t = torch.as_tensor(_DeviceBuffer(buf, count, dtype), device="cuda")
-            with torch.cuda.stream(torch.cuda.ExternalStream(stream or 0)):
+            s = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(s):
                 reduce_fn(t)
             return 0
         except Exception:   # reported to the caller as IHS_ECUDA

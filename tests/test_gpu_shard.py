@@ -112,14 +112,14 @@ def _emulated_ranks(torch, ihs, A, b, nu, parts, kind, variant, tol):
 
     def make_cb(rank):
         def reduce_fn(t):
-            torch.cuda.current_stream().synchronize()
-            slots[rank] = t.cpu()
+            torch.cuda.synchronize()          # every rank's work on the shared stream is done
+            slots[rank] = t.cpu().numpy().copy()
             barrier.wait(timeout=60)
-            total = slots[0].clone()
-            for r in range(1, world):
+            total = slots[0].copy()
+            for r in range(1, world):         # rank order: every rank forms the same sums
                 total += slots[r]
-            t.copy_(total.to(t.device))
-            torch.cuda.current_stream().synchronize()
+            t.copy_(torch.from_numpy(total).to(t.device))
+            torch.cuda.synchronize()
             barrier.wait(timeout=60)
         return shard.make_allreduce(reduce_fn)
 
