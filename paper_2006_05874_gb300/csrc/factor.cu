@@ -487,14 +487,14 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t& I, int64_t& J) {
 }
 
 // 1 / sqrt(p) for a positive double-float p: the single-precision estimate
-// rsqrtf(p.hi) refined by two Newton-Raphson steps for f(y) = 1/y^2 - p,
+// rsqrtf(p.hi) refined by one Newton-Raphson step for f(y) = 1/y^2 - p,
 // y <- y + y (1 - p y^2) / 2, with the residual 1 - p y^2 formed in
-// double-float (each step squares the relative error: 2^-23 -> 2^-45 ->
-// the double-float rounding level).
+// double-float (the step squares the estimate's relative error, about 2^-22,
+// to about 2^-44 plus the rounding of the pair arithmetic).
 __device__ __forceinline__ float2 df_rsqrt(float2 p) {
     float2 y = make_float2(rsqrtf(p.x), 0.f);
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < 1; ++it) {
         const float2 q = df_mul2(p, df_mul2(y, y));   // p y^2, close to 1
         float s, e;
         two_sum(1.0f, -q.x, s, e);
