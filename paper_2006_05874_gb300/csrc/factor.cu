@@ -603,237 +603,6 @@ __device__ void chol_potrf_df(CholSmemDf& S, float2* __restrict__ Kmat, int64_t 
     if (tid == 0 && S.bad) atomicOr(status, IHS_DEV_NOTPD);
 }
 
-// Flag wait of the persistent Cholesky: thread 0 polls a monotonic counter
-// with acquire loads until it reaches `target` (bounded like the grid barrier);
-// the CTA then reads what the flag's writer stored before its release.
-__device__ __forceinline__ bool wait_flag_bounded(const unsigned* flag, unsigned target, unsigned* status,
-                                                  uint64_t limit_ns) {
-    __shared__ int wf_ok;
-    if (threadIdx.x == 0) {
-        wf_ok = 1;
-        if (ld_acquire_gpu(flag) < target) {
-            const uint64_t t0 = global_timer_ns();
-            while (ld_acquire_gpu(flag) < target) {
-                if (global_timer_ns() - t0 > limit_ns) {
-                    atomicOr(status, IHS_DEV_TIMEOUT);
-                    wf_ok = 0;
-                    break;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    return wf_ok != 0;
-}
-
-// Trailing update by the panel stored in Pdf (rows >= j1) of the lower tiles of
-// column blocks >= 1 of the region that starts at row and column j1; this CTA
-// takes items me, me + workers, ...
-__device__ void chol_trailing(float2* __restrict__ Kmat, int64_t k, const float2* __restrict__ Pdf, int64_t j1,
-                              int workers, int me, float2 (&fa)[CB][CB + 1], float2 (&fb)[CB][CB + 1]) {
-    const int tid = threadIdx.x;
-    const int64_t Tr = ceil_div64(k - j1, CB);
-    const int64_t ntile = Tr * (Tr + 1) / 2;
-    // tiles of column blocks >= 1 of the trailing region: Tr (Tr - 1) / 2;
-    // when they are fewer than two per worker, split each into two
-    // 16-row halves so that the short last steps spread wider
-    const int H = (Tr * (Tr - 1) / 2 < 2 * (int64_t)workers) ? 2 : 1;
-    const int64_t total = ntile * H;
-    auto tile_of = [&](int64_t it, int64_t& I, int64_t& J) { tri_tile(it / H, I, J); };
-    // column block 0 of the region (J = 0) was updated in the previous phase B
-    auto next_item = [&](int64_t it) -> int64_t {
-        for (; it < total; it += workers) {
-            int64_t I, J;
-            tile_of(it, I, J);
-            if (J >= 1) return it;
-        }
-        return total;
-    };
-    // operands of the next item are loaded into registers while the
-    // current one computes
-    float2 va[4], vb[4];
-    auto fetch = [&](int64_t it) {
-        int64_t I, J;
-        tile_of(it, I, J);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int e = tid + 256 * i;
-            const int rr = e / CB, q = e % CB;
-            const int64_t ra = j1 + I * CB + rr, rb = j1 + J * CB + rr;
-            va[i] = ra < k ? __ldcg(Pdf + ra * CB + q) : make_float2(0.f, 0.f);
-            vb[i] = rb < k ? __ldcg(Pdf + rb * CB + q) : make_float2(0.f, 0.f);
-        }
-    };
-    int64_t it = next_item(me);
-    if (it < total) fetch(it);
-    const int tx = tid % 16, ty = tid / 16;
-    while (it < total) {
-        int64_t I, J;
-        tile_of(it, I, J);
-        const int hsel = (int)(it % H);
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int e = tid + 256 * i;
-            fa[e / CB][e % CB] = va[i];
-            fb[e / CB][e % CB] = vb[i];
-        }
-        __syncthreads();
-        const int64_t nx = next_item(it + workers);
-        if (nx < total) fetch(nx);
-        // the rank-32 product and the subtraction from K in double-float
-        // on the FP32 pipes
-        if (H == 1) {
-            float2 kold[2][2];
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
-                    kold[a][b] = (r < k && c <= r) ? __ldcg(Kmat + r * k + c) : make_float2(0.f, 0.f);
-                }
-            Acc2 acc[2][2] = {};
-#pragma unroll 4
-            for (int q = 0; q < CB; ++q) {
-                const float2 a0 = fa[ty][q], a1 = fa[ty + 16][q];
-                const float2 b0 = fb[tx][q], b1 = fb[tx + 16][q];
-                df_fma_acc(acc[0][0], a0, b0);
-                df_fma_acc(acc[0][1], a0, b1);
-                df_fma_acc(acc[1][0], a1, b0);
-                df_fma_acc(acc[1][1], a1, b1);
-            }
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
-                    if (r < k && c <= r)
-                        Kmat[r * k + c] = pair_sub(kold[a][b], pair_norm(acc[a][b].hi, acc[a][b].lo));
-                }
-        } else {
-            // rows ty + 16 hsel only
-            const int ra = ty + 16 * hsel;
-            float2 kold[2];
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const int64_t r = j1 + I * CB + ra, c = j1 + J * CB + tx + 16 * b;
-                kold[b] = (r < k && c <= r) ? __ldcg(Kmat + r * k + c) : make_float2(0.f, 0.f);
-            }
-            Acc2 acc[2] = {};
-#pragma unroll 4
-            for (int q = 0; q < CB; ++q) {
-                const float2 a0 = fa[ra][q];
-                df_fma_acc(acc[0], a0, fb[tx][q]);
-                df_fma_acc(acc[1], a0, fb[tx + 16][q]);
-            }
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const int64_t r = j1 + I * CB + ra, c = j1 + J * CB + tx + 16 * b;
-                if (r < k && c <= r) Kmat[r * k + c] = pair_sub(kold[b], pair_norm(acc[b].hi, acc[b].lo));
-            }
-        }
-        it = nx;
-    }
-}
-
-// L_jj (double-float) into fa and 1 / L_cc into fb[0] for the panel of block
-// [j0, j0 + nb).
-__device__ __forceinline__ void chol_panel_load(const float2* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
-                                                const double* __restrict__ dinv, float2 (&fa)[CB][CB + 1],
-                                                float2 (&fb)[CB][CB + 1]) {
-    const int tid = threadIdx.x;
-    for (int e = tid; e < CB * CB; e += 256) {
-        const int r = e / CB, c = e % CB;
-        fa[r][c] = (c <= r && r < nb) ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : make_float2(0.f, 0.f);
-    }
-    if (tid < CB) fb[0][tid] = df_split(__ldcg(dinv + tid));
-    __syncthreads();
-}
-
-// Panel rows [r0, r0 + 16) of block column j0 (L_rj = K_rj L_jj^{-T}) by
-// forward substitution in double-float: warp w solves rows r0 + w and
-// r0 + 8 + w side by side (two independent chains), lane c holds column c;
-// stored in Kmat and, as the next steps' operand, in Pdf.
-__device__ __forceinline__ void chol_panel_item(float2* __restrict__ Kmat, int64_t k, int64_t j0, int nb,
-                                                int64_t r0, const float2 (&fa)[CB][CB + 1],
-                                                const float2 (&fb)[CB][CB + 1], float2* __restrict__ Pdf) {
-    const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
-    const int64_t ra = r0 + wq, rb = r0 + 8 + wq;
-    float2 ka = (ra < k && lane < nb) ? __ldcg(Kmat + ra * k + j0 + lane) : make_float2(0.f, 0.f);
-    float2 kb = (rb < k && lane < nb) ? __ldcg(Kmat + rb * k + j0 + lane) : make_float2(0.f, 0.f);
-    float2 xa = make_float2(0.f, 0.f), xb = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int c = 0; c < CB; ++c) {
-        const float2 kca = make_float2(__shfl_sync(0xffffffffu, ka.x, c), __shfl_sync(0xffffffffu, ka.y, c));
-        const float2 kcb = make_float2(__shfl_sync(0xffffffffu, kb.x, c), __shfl_sync(0xffffffffu, kb.y, c));
-        const float2 dc = fb[0][c];
-        const float2 xca = df_mul2(kca, dc);
-        const float2 xcb = df_mul2(kcb, dc);
-        if (lane == c) {
-            xa = xca;
-            xb = xcb;
-        } else if (lane > c) {
-            const float2 lc = fa[lane][c];
-            ka = df_fnms(ka, xca, lc);
-            kb = df_fnms(kb, xcb, lc);
-        }
-    }
-    if (ra < k && lane < nb) Kmat[ra * k + j0 + lane] = xa;
-    if (ra < k) Pdf[ra * CB + lane] = xa;   // 0 for lanes >= nb
-    if (rb < k && lane < nb) Kmat[rb * k + j0 + lane] = xb;
-    if (rb < k) Pdf[rb * CB + lane] = xb;
-}
-
-// Column block [j1, j1 + ncol) of rows [r0, r0 + 16) updated by the panel in
-// Pdf: K_rc -= P_r . P_c for c <= r (thread (ty, tx) takes rows ty and ty + 8,
-// column tx).  Leaves fa and fb overwritten.
-__device__ __forceinline__ void chol_column_item(float2* __restrict__ Kmat, int64_t k, const float2* __restrict__ Pdf,
-                                                 int64_t j1, int ncol, int64_t r0, float2 (&fa)[CB][CB + 1],
-                                                 float2 (&fb)[CB][CB + 1]) {
-    const int tid = threadIdx.x;
-    __syncthreads();
-    for (int e = tid; e < CB * CB; e += 256) {
-        const int c = e / CB, q = e % CB;
-        fb[c][q] = c < ncol ? __ldcg(Pdf + (j1 + c) * CB + q) : make_float2(0.f, 0.f);
-    }
-    for (int e = tid; e < 16 * CB; e += 256) {
-        const int r = e / CB, q = e % CB;
-        fa[r][q] = r0 + r < k ? __ldcg(Pdf + (r0 + r) * CB + q) : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const int tx = tid % CB, ty = tid / CB;
-    Acc2 a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < CB; q += 2) {
-        const float2 f0 = fb[tx][q], f1 = fb[tx][q + 1];
-        df_fma_acc(a0, fa[ty][q], f0);
-        df_fma_acc(a1, fa[ty][q + 1], f1);
-        df_fma_acc(b0, fa[ty + 8][q], f0);
-        df_fma_acc(b1, fa[ty + 8][q + 1], f1);
-    }
-    const int64_t c = j1 + tx;
-    const int64_t ra = r0 + ty, rb = r0 + 8 + ty;
-    if (ra < k && tx < ncol && c <= ra)
-        Kmat[ra * k + c] = pair_sub(__ldcg(Kmat + ra * k + c), pair_add(pair_norm(a0.hi, a0.lo), pair_norm(a1.hi, a1.lo)));
-    if (rb < k && tx < ncol && c <= rb)
-        Kmat[rb * k + c] = pair_sub(__ldcg(Kmat + rb * k + c), pair_add(pair_norm(b0.hi, b0.lo), pair_norm(b1.hi, b1.lo)));
-}
-
-// The blocked Cholesky as one cooperative launch on double-float storage,
-// with the diagonal blocks one step ahead.  Before the loop CTA 0 factors
-// diagonal block 0.  Step jb (column block [j0, j0 + nb), next block
-// [j1, j1 + nb1), j1 = j0 + nb):
-//   phase A (jb >= 1): every CTA applies panel jb-1 to the lower tiles of
-//            column blocks >= jb+1 (the trailing update);  grid barrier;
-//   phase B: CTA 0 forms the panel rows of block jb+1, raises the flag,
-//            applies them to diagonal tile jb+1 and factors diagonal block jb+1
-//            (next step's), while the other CTAs form the panel rows below
-//            block jb+1, wait for the flag (they need block jb+1's panel rows)
-//            and update column block jb+1 below its diagonal tile;  grid
-//            barrier.
-// So the factorisation of block jb+1 overlaps the panel and column work of
-// step jb, and a step takes two grid barriers.  Every wait is bounded; a wait
-// that gives up sets IHS_DEV_TIMEOUT and the CTAs leave.
 __global__ void __launch_bounds__(256) k_chol_persistent(float2* __restrict__ Kmat, int64_t k,
                                                          double* __restrict__ Wall, unsigned* bar,
                                                          unsigned* status, unsigned bar_extra,
@@ -845,52 +614,212 @@ __global__ void __launch_bounds__(256) k_chol_persistent(float2* __restrict__ Km
     const int tid = threadIdx.x;
     const int G = gridDim.x, cta = blockIdx.x;
     const int64_t T = ceil_div64(k, CB);
-    unsigned* flag = bar + 2;   // panel rows of block jb+1 stored: raised to jb + 1
     // Wall: 1 / L_cc of every block step (T x CB), then the current panel as
-    // double-float pairs, row r at Pdf + r * CB
+    // double-float pairs, row r at Pdf + r * CB (written once per element in
+    // phase N, read by phase S and by the next step's trailing tiles)
     float2* Pdf = reinterpret_cast<float2*>(Wall + T * CB);
     unsigned nbar = 0;   // grid barriers passed
-    if (cta == 0) chol_potrf_df(S, Kmat, k, 0, (int)min((int64_t)CB, k), Wall, status);
-    if (!grid_sync_bounded(bar, nbar, status, bar_extra, bar_limit_ns)) return;
     for (int64_t jb = 0; jb < T; ++jb) {
         const int64_t j0 = jb * CB;
         const int nb = (int)min((int64_t)CB, k - j0);
-        const int64_t j1 = j0 + nb;
-        if (k - j1 <= 0) break;
-        const int nb1 = (int)min((int64_t)CB, k - j1);
-        // ---- phase A: trailing update by panel jb-1 (column blocks >= jb+1)
-        if (jb > 0) {
-            chol_trailing(Kmat, k, Pdf, j0, G, cta, fa, fb);
-            if (!grid_sync_bounded(bar, nbar, status, 0u, bar_limit_ns)) return;
-        }
-        // ---- phase B
-        const double* dinv = Wall + jb * CB;   // 1 / L_cc of block jb
-        const int64_t below = k - j1 - nb1;    // panel rows below block jb+1
-        const int64_t items = ceil_div64(below, 16);
-        if (cta == 0) {
-            chol_panel_load(Kmat, k, j0, nb, dinv, fa, fb);
-            for (int64_t r0 = j1; r0 < j1 + nb1; r0 += 16) chol_panel_item(Kmat, k, j0, nb, r0, fa, fb, Pdf);
-            __syncthreads();
-            if (tid == 0) {
-                __threadfence();
-                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(flag) : "memory");
-            }
-            for (int64_t r0 = j1; r0 < j1 + nb1; r0 += 16) chol_column_item(Kmat, k, Pdf, j1, nb1, r0, fa, fb);
-            __syncthreads();
-            chol_potrf_df(S, Kmat, k, j1, nb1, Wall + (jb + 1) * CB, status);
-        }
-        if (cta > 0 || G == 1) {
+        // ---- phase P: diagonal block jb | rest of the update by panel jb-1
+        if (cta == 0) chol_potrf_df(S, Kmat, k, j0, nb, Wall + jb * CB, status);
+        if (jb > 0 && (cta > 0 || G == 1)) {
+            const int64_t j1 = j0;                 // trailing region starts at block jb
+            const int64_t Tr = ceil_div64(k - j1, CB);
+            const int64_t ntile = Tr * (Tr + 1) / 2;
             const int workers = G > 1 ? G - 1 : 1, me = G > 1 ? cta - 1 : 0;
-            if (me < items) {
-                chol_panel_load(Kmat, k, j0, nb, dinv, fa, fb);
-                for (int64_t it = me; it < items; it += workers)
-                    chol_panel_item(Kmat, k, j0, nb, j1 + nb1 + it * 16, fa, fb, Pdf);
-                if (G > 1 && !wait_flag_bounded(flag, (unsigned)(jb + 1), status, bar_limit_ns)) return;
-                for (int64_t it = me; it < items; it += workers)
-                    chol_column_item(Kmat, k, Pdf, j1, nb1, j1 + nb1 + it * 16, fa, fb);
+            // tiles of column blocks >= 1 of the trailing region: Tr (Tr - 1) / 2;
+            // when they are fewer than two per worker, split each into two
+            // 16-row halves so that the short last steps spread wider
+            const int H = (Tr * (Tr - 1) / 2 < 2 * (int64_t)workers) ? 2 : 1;
+            const int64_t total = ntile * H;
+            auto tile_of = [&](int64_t it, int64_t& I, int64_t& J) { tri_tile(it / H, I, J); };
+            // column block jb (J = 0) was done in phase S of step jb-1
+            auto next_item = [&](int64_t it) -> int64_t {
+                for (; it < total; it += workers) {
+                    int64_t I, J;
+                    tile_of(it, I, J);
+                    if (J >= 1) return it;
+                }
+                return total;
+            };
+            // operands of the next item are loaded into registers while the
+            // current one computes
+            float2 va[4], vb[4];
+            auto fetch = [&](int64_t it) {
+                int64_t I, J;
+                tile_of(it, I, J);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int e = tid + 256 * i;
+                    const int rr = e / CB, q = e % CB;
+                    const int64_t ra = j1 + I * CB + rr, rb = j1 + J * CB + rr;
+                    va[i] = ra < k ? __ldcg(Pdf + ra * CB + q) : make_float2(0.f, 0.f);
+                    vb[i] = rb < k ? __ldcg(Pdf + rb * CB + q) : make_float2(0.f, 0.f);
+                }
+            };
+            int64_t it = next_item(me);
+            if (it < total) fetch(it);
+            const int tx = tid % 16, ty = tid / 16;
+            while (it < total) {
+                int64_t I, J;
+                tile_of(it, I, J);
+                const int hsel = (int)(it % H);
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int e = tid + 256 * i;
+                    fa[e / CB][e % CB] = va[i];
+                    fb[e / CB][e % CB] = vb[i];
+                }
+                __syncthreads();
+                const int64_t nx = next_item(it + workers);
+                if (nx < total) fetch(nx);
+                // the rank-32 product and the subtraction from K in double-float
+                // on the FP32 pipes
+                if (H == 1) {
+                    float2 kold[2][2];
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) {
+                            const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
+                            kold[a][b] = (r < k && c <= r) ? __ldcg(Kmat + r * k + c) : make_float2(0.f, 0.f);
+                        }
+                    Acc2 acc[2][2] = {};
+#pragma unroll 4
+                    for (int q = 0; q < CB; ++q) {
+                        const float2 a0 = fa[ty][q], a1 = fa[ty + 16][q];
+                        const float2 b0 = fb[tx][q], b1 = fb[tx + 16][q];
+                        df_fma_acc(acc[0][0], a0, b0);
+                        df_fma_acc(acc[0][1], a0, b1);
+                        df_fma_acc(acc[1][0], a1, b0);
+                        df_fma_acc(acc[1][1], a1, b1);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) {
+                            const int64_t r = j1 + I * CB + ty + 16 * a, c = j1 + J * CB + tx + 16 * b;
+                            if (r < k && c <= r)
+                                Kmat[r * k + c] = pair_sub(kold[a][b], pair_norm(acc[a][b].hi, acc[a][b].lo));
+                        }
+                } else {
+                    // rows ty + 16 hsel only
+                    const int ra = ty + 16 * hsel;
+                    float2 kold[2];
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int64_t r = j1 + I * CB + ra, c = j1 + J * CB + tx + 16 * b;
+                        kold[b] = (r < k && c <= r) ? __ldcg(Kmat + r * k + c) : make_float2(0.f, 0.f);
+                    }
+                    Acc2 acc[2] = {};
+#pragma unroll 4
+                    for (int q = 0; q < CB; ++q) {
+                        const float2 a0 = fa[ra][q];
+                        df_fma_acc(acc[0], a0, fb[tx][q]);
+                        df_fma_acc(acc[1], a0, fb[tx + 16][q]);
+                    }
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int64_t r = j1 + I * CB + ra, c = j1 + J * CB + tx + 16 * b;
+                        if (r < k && c <= r) Kmat[r * k + c] = pair_sub(kold[b], pair_norm(acc[b].hi, acc[b].lo));
+                    }
+                }
+                it = nx;
             }
         }
-        if (!grid_sync_bounded(bar, nbar, status, 0u, bar_limit_ns)) return;
+        if (!grid_sync_bounded(bar, nbar, status, nbar == 0 ? bar_extra : 0u, bar_limit_ns)) return;
+        const int64_t rest = k - j0 - nb;
+        if (rest <= 0) break;
+        // ---- phase N: panel jb = K L_jj^{-T} by forward substitution, 16 rows per
+        // work item: warp w solves rows r0 + w and r0 + 8 + w side by side (two
+        // independent chains), lane c holds column c
+        {
+            const double* dinv = Wall + jb * CB;   // 1 / L_cc
+            const int64_t items = ceil_div64(rest, 16);
+            const int lane = tid & 31, wq = tid >> 5;
+            bool loaded = false;
+            for (int64_t it = cta; it < items; it += G) {
+                const int64_t r0 = j0 + nb + it * 16;
+                if (!loaded) {
+                    // L_jj and 1 / L_cc as double-float pairs, once per step
+                    for (int e = tid; e < CB * CB; e += 256) {
+                        const int r = e / CB, c = e % CB;
+                        fa[r][c] = (c <= r && r < nb) ? __ldcg(Kmat + (j0 + r) * k + j0 + c) : make_float2(0.f, 0.f);
+                    }
+                    if (tid < CB) fb[0][tid] = df_split(__ldcg(dinv + tid));
+                    __syncthreads();
+                    loaded = true;
+                }
+                // substitution in double-float (FP32 latencies on the dependent chains)
+                const int64_t ra = r0 + wq, rb = r0 + 8 + wq;
+                float2 ka = (ra < k && lane < nb) ? __ldcg(Kmat + ra * k + j0 + lane) : make_float2(0.f, 0.f);
+                float2 kb = (rb < k && lane < nb) ? __ldcg(Kmat + rb * k + j0 + lane) : make_float2(0.f, 0.f);
+                float2 xa = make_float2(0.f, 0.f), xb = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    const float2 kca = make_float2(__shfl_sync(0xffffffffu, ka.x, c), __shfl_sync(0xffffffffu, ka.y, c));
+                    const float2 kcb = make_float2(__shfl_sync(0xffffffffu, kb.x, c), __shfl_sync(0xffffffffu, kb.y, c));
+                    const float2 dc = fb[0][c];
+                    const float2 xca = df_mul2(kca, dc);
+                    const float2 xcb = df_mul2(kcb, dc);
+                    if (lane == c) {
+                        xa = xca;
+                        xb = xcb;
+                    } else if (lane > c) {
+                        const float2 lc = fa[lane][c];
+                        ka = df_fnms(ka, xca, lc);
+                        kb = df_fnms(kb, xcb, lc);
+                    }
+                }
+                if (ra < k && lane < nb) Kmat[ra * k + j0 + lane] = xa;
+                if (ra < k) Pdf[ra * CB + lane] = xa;   // 0 for lanes >= nb
+                if (rb < k && lane < nb) Kmat[rb * k + j0 + lane] = xb;
+                if (rb < k) Pdf[rb * CB + lane] = xb;
+            }
+        }
+        if (!grid_sync_bounded(bar, nbar, status, nbar == 0 ? bar_extra : 0u, bar_limit_ns)) return;
+        // ---- phase S: column block jb+1 updated by panel jb, 16 rows per work
+        // item (thread (ty, tx) takes rows ty and ty + 8 of the item, column tx)
+        {
+            const int64_t j1 = j0 + nb;
+            const int ncol = (int)min((int64_t)CB, k - j1);
+            const int64_t items = ceil_div64(k - j1, 16);
+            for (int64_t it = cta; it < items; it += G) {
+                const int64_t r0 = j1 + it * 16;
+                __syncthreads();
+                for (int e = tid; e < CB * CB; e += 256) {
+                    const int c = e / CB, q = e % CB;
+                    fb[c][q] = c < ncol ? __ldcg(Pdf + (j1 + c) * CB + q) : make_float2(0.f, 0.f);
+                }
+                for (int e = tid; e < 16 * CB; e += 256) {
+                    const int r = e / CB, q = e % CB;
+                    fa[r][q] = r0 + r < k ? __ldcg(Pdf + (r0 + r) * CB + q) : make_float2(0.f, 0.f);
+                }
+                __syncthreads();
+                const int tx = tid % CB, ty = tid / CB;
+                Acc2 a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f};
+#pragma unroll
+                for (int q = 0; q < CB; q += 2) {
+                    const float2 f0 = fb[tx][q], f1 = fb[tx][q + 1];
+                    df_fma_acc(a0, fa[ty][q], f0);
+                    df_fma_acc(a1, fa[ty][q + 1], f1);
+                    df_fma_acc(b0, fa[ty + 8][q], f0);
+                    df_fma_acc(b1, fa[ty + 8][q + 1], f1);
+                }
+                const int64_t c = j1 + tx;
+                const int64_t ra = r0 + ty, rb = r0 + 8 + ty;
+                if (ra < k && tx < ncol && c <= ra)
+                    Kmat[ra * k + c] = pair_sub(__ldcg(Kmat + ra * k + c),
+                                                pair_add(pair_norm(a0.hi, a0.lo), pair_norm(a1.hi, a1.lo)));
+                if (rb < k && tx < ncol && c <= rb)
+                    Kmat[rb * k + c] = pair_sub(__ldcg(Kmat + rb * k + c),
+                                                pair_add(pair_norm(b0.hi, b0.lo), pair_norm(b1.hi, b1.lo)));
+            }
+        }
+        if (!grid_sync_bounded(bar, nbar, status, nbar == 0 ? bar_extra : 0u, bar_limit_ns)) return;
     }
 }
 
@@ -1358,8 +1287,8 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
     if (F->l_df) {
         const int G = Gcoop;
         {
-            unsigned* bar = ctx->d_status + 16;   // barrier counter; word 18: the panel flag
-            IHS_CUDA_TRY(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), s));
+            unsigned* bar = ctx->d_status + 16;
+            IHS_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
             int64_t kk = k;
             // test-only: the first launch of a context with the knob set gets an
             // unreachable first barrier (see ihs_ctx)
