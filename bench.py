@@ -14,7 +14,7 @@ from CUDA events recorded around every gradient pass inside the timed solves;
 an end-to-end time through host buffers; the CPU oracle on a bounded sample.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       python bench.py --profile solve|grad|srht|gauss   (one NVTX-marked run for ncu)
+       python bench.py --profile solve|grad|srht|gauss|factor   (one NVTX-marked run for ncu)
 """
 import argparse
 import hashlib
@@ -356,6 +356,15 @@ def run_profile(what, rows=N_ROWS, m=1024):
             x = torch.randn(D_COLS, device="cuda", generator=gen)
             g = torch.empty(D_COLS, device="cuda")
             fn = lambda: ctx.grad(A, b, 0.015, x, g, want_axnorm2=False)
+        elif what == "factor":
+            # the top level of the spectral solve: SRHT sketch of size m = d, then
+            # the d x d factorisation (persistent Cholesky at k = 2048)
+            SA = torch.empty(D_COLS, D_COLS, device="cuda")
+            ctx.sketch(A, D_COLS, "srht", 0, 11, SA)
+
+            def fn():
+                F = ctx.factor(SA, 0.015)
+                F.destroy()
         else:
             # default m = 1024: the sketch size the solves settle at (SRHT level 10; BF16 Gaussian warm start)
             SA = torch.empty(m, D_COLS, device="cuda")
@@ -698,7 +707,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["solve", "grad", "srht", "gauss"], default=None)
+    ap.add_argument("--profile", choices=["solve", "grad", "srht", "gauss", "factor"], default=None)
     ap.add_argument("--profile-rows", type=int, default=N_ROWS,
                     help="rows of A for --profile grad|srht|gauss (a smaller case for ncu captures)")
     ap.add_argument("--profile-m", type=int, default=1024, help="sketch size for --profile srht|gauss")
