@@ -337,6 +337,10 @@ __device__ __forceinline__ void st_cluster_u16(uint32_t addr, uint16_t v) {
     asm volatile("st.shared::cluster.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_cluster_u8(uint32_t addr, uint8_t v) {
+    asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(addr), "h"((uint16_t)v) : "memory");
+}
+
 __device__ __forceinline__ void arrive_cluster(uint32_t bar_addr_cluster) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_addr_cluster) : "memory");
 }
@@ -443,44 +447,34 @@ k_gauss_tc_cl(const __grid_constant__ CUtensorMap amap, int64_t n, int d, int64_
         if (c >= 2) {
             // every CTA's MMAs of chunk c-2 are done with stage s
             const bool w = mbar_wait_cluster_bounded(&bar_free[s], (uint32_t)(((c - 2) >> 1) & 1), status);
-            if (__syncthreads_or(!w)) {
+            if (__syncthreads_or(!w || !ok)) {   // thread 0's waits fold in here
                 ok = false;
                 break;
             }
         }
         const int64_t i0 = i_begin + c * TC_KE;
-        // this CTA's share of the Z tile: quads [rank QPC, (rank + 1) QPC), into every CTA's stage
-        if (tid < QPC * 16) {
-            const int q = (int)rank * QPC + (tid >> 4), ig = tid & 15;
-            float zv[4][2];
-            if (q < nq) {
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const float4 z = gauss4_fast(ibase + (uint32_t)(i0 + 2 * ig + t), zq0 + (uint32_t)((j0 >> 2) + q),
-                                                 level, k0, k1);
-                    zv[0][t] = z.x;
-                    zv[1][t] = z.y;
-                    zv[2][t] = z.z;
-                    zv[3][t] = z.w;
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) zv[r][0] = zv[r][1] = 0.f;
-            }
+        // this CTA's share of the Z tile: quads [rank QPC, (rank + 1) QPC) of four
+        // sketch rows, one (quad, column) Philox draw per thread, stored into every
+        // CTA's stage
+        if (tid < QPC * TC_KE) {
+            const int q = (int)rank * QPC + tid / TC_KE, i = tid % TC_KE;
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < nq) z = gauss4_fast(ibase + (uint32_t)(i0 + i), zq0 + (uint32_t)((j0 >> 2) + q), level, k0, k1);
+            const float zr[4] = {z.x, z.y, z.z, z.w};
             const uint32_t zbase = smem_u32(zt);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 if (FMT == 0) {
-                    const uint32_t off = kmaj<RB>(4 * q + r, 4 * ig);
-                    const uint32_t v = pack_bf16(zv[r][0], zv[r][1]);
-#pragma unroll
-                    for (int p = 0; p < CL; ++p) st_cluster_u32(mapa_shared(zbase + off, (uint32_t)p), v);
-                } else {
-                    const uint32_t off = kmaj<RB>(4 * q + r, 2 * ig);
-                    const uint16_t v = (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(zv[r][0], zv[r][1]),
-                                                                            __NV_SATFINITE, __NV_E4M3);
+                    const uint32_t off = kmaj<RB>(4 * q + r, 2 * i);
+                    const __nv_bfloat16 h = __float2bfloat16_rn(zr[r]);
+                    const uint16_t v = *reinterpret_cast<const uint16_t*>(&h);
 #pragma unroll
                     for (int p = 0; p < CL; ++p) st_cluster_u16(mapa_shared(zbase + off, (uint32_t)p), v);
+                } else {
+                    const uint32_t off = kmaj<RB>(4 * q + r, i);
+                    const uint8_t v = (uint8_t)__nv_cvt_float_to_fp8(zr[r], __NV_SATFINITE, __NV_E4M3);
+#pragma unroll
+                    for (int p = 0; p < CL; ++p) st_cluster_u8(mapa_shared(zbase + off, (uint32_t)p), v);
                 }
             }
             // the stores above are read by the peers' tensor cores (async proxy)
@@ -489,7 +483,7 @@ k_gauss_tc_cl(const __grid_constant__ CUtensorMap amap, int64_t n, int d, int64_
         // A tile from the staging buffer: thread = one column, all 32 rows
         {
             const bool w = mbar_wait_bounded(&bar_tma[s], (uint32_t)((c >> 1) & 1), status);
-            if (__syncthreads_or(!w)) {
+            if (__syncthreads_or(!w || !ok)) {
                 ok = false;
                 break;
             }
@@ -569,10 +563,6 @@ k_gauss_tc_cl(const __grid_constant__ CUtensorMap amap, int64_t n, int d, int64_
                 "h"(cmask)
                 : "memory");
             committed = c;
-        }
-        if (__syncthreads_or(!ok)) {
-            ok = false;
-            break;
         }
     }
     if (ok && nchunks > 0) {
