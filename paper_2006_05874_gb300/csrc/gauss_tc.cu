@@ -299,327 +299,6 @@ k_gauss_tc(const __grid_constant__ CUtensorMap amap, const float* __restrict__ A
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_N));
 }
 
-// ---------------------------------------------------------------------------
-// Cluster form: the CL CTAs that compute the CL column tiles (512 columns
-// each) of the same 128 sketch rows and the same rows of A form one cluster
-// and share the Z tile of every chunk.  Each CTA draws 128 / CL of its rows
-// (Philox + Box-Muller are most of the instructions of the single-CTA form,
-// which draws each z once per column tile) and stores them, rounded, into the
-// Z stage of every CTA of the cluster through distributed shared memory.
-// Per operand stage s, in every CTA:
-//   zfull[s]  (CL arrivals): every CTA's share of the chunk's Z is in place
-//             (remote release-arrive after the stores);
-//   free[s]   (CL arrivals): every CTA's MMAs of the chunk that last used
-//             stage s are done (tcgen05.commit multicast to the cluster),
-//             so no CTA overwrites a stage a peer is still reading.
-// A (FP32, by TMA into local staging) is converted by each CTA for its own
-// columns, as in the single-CTA form.  A cluster barrier before the TMEM is
-// freed and the CTA exits covers the remote stores and arrivals.  Every
-// mbarrier wait is bounded; a wait that gives up sets IHS_DEV_TIMEOUT.
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
-    return r;
-}
-
-__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
-    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void st_cluster_u16(uint32_t addr, uint16_t v) {
-    asm volatile("st.shared::cluster.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
-}
-
-__device__ __forceinline__ void st_cluster_u8(uint32_t addr, uint8_t v) {
-    asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(addr), "h"((uint16_t)v) : "memory");
-}
-
-__device__ __forceinline__ void arrive_cluster(uint32_t bar_addr_cluster) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_addr_cluster) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait with cluster-scope acquire (the barrier is completed by peers).
-__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity, unsigned* status) {
-    if (mbar_try_wait_cluster(bar, parity)) return true;
-    const uint64_t t0 = global_timer_ns();
-    while (!mbar_try_wait_cluster(bar, parity)) {
-        if (global_timer_ns() - t0 > 1000000000ull) {
-            atomicOr(status, IHS_DEV_TIMEOUT);
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-template <int FMT, int CL>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-k_gauss_tc_cl(const __grid_constant__ CUtensorMap amap, int64_t n, int d, int64_t m, int64_t rows_per_split,
-              uint32_t level, uint32_t k0, uint32_t k1, uint32_t zq0 /* first z row / 4 */,
-              uint32_t ibase /* global row of A's row 0 */, const float* __restrict__ col_recip, unsigned* status,
-              float* __restrict__ part /* KS x m x d */) {
-    constexpr int RB = (int)tc_rb(FMT);
-    constexpr uint32_t ZB = TC_M * RB, STAGE = tc_stage(FMT);
-    constexpr int KSTEPS = RB / 32;
-    constexpr int QPC = (TC_M / 4) / CL;   // quads of four sketch rows drawn by each CTA
-    extern __shared__ __align__(1024) unsigned char sm[];
-    float* stg = reinterpret_cast<float*>(sm);                                   // 2 x [32][512] FP32
-    unsigned char* ops = sm + 2 * TC_STG;                                        // 2 operand stages
-    uint64_t* bar = reinterpret_cast<uint64_t*>(ops + 2 * STAGE);                // tma[2], free[2], zfull[2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 6);
-    uint64_t* bar_tma = bar;
-    uint64_t* bar_free = bar + 2;
-    uint64_t* bar_zfull = bar + 4;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t rank = cluster_rank();
-    const int64_t j0 = (int64_t)blockIdx.x * TC_M;
-    const int c0 = blockIdx.y * TC_N;
-    const int64_t i_begin = (int64_t)blockIdx.z * rows_per_split;
-    const int64_t i_end = min(n, i_begin + rows_per_split);
-    const int64_t nchunks = i_end > i_begin ? ceil_div64(i_end - i_begin, TC_KE) : 0;
-    const int mrows = (int)min((int64_t)TC_M, m - j0);
-    const int nq = (mrows + 3) >> 2;
-
-    if (tid == 0) {
-        mbar_init(&bar_tma[0], 1);
-        mbar_init(&bar_tma[1], 1);
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&bar_free[i], CL);
-            mbar_init(&bar_zfull[i], CL);
-        }
-        fence_mbar_init();
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(TC_N));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
-    // every CTA's barriers are initialised before any peer arrives on them
-    cluster_sync_all();
-    tc_fence_after();
-    const uint32_t taddr = *tslot;
-    int64_t issued = 0;
-    auto issue_tma = [&](int64_t c) {
-        issued = c + 1;
-        const int b = (int)(c & 1);
-        mbar_arrive_expect_tx(&bar_tma[b], TC_STG);
-        const int y = (int)(i_begin + c * TC_KE);
-        tma_load_2d(stg + (size_t)b * TC_KE * TC_N, &amap, c0, y, &bar_tma[b]);
-        tma_load_2d(stg + (size_t)b * TC_KE * TC_N + TC_KE * 256, &amap, c0 + 256, y, &bar_tma[b]);
-    };
-    if (tid == 0) {
-        for (int64_t c = 0; c < min((int64_t)2, nchunks); ++c) issue_tma(c);
-    }
-    const uint32_t fmtbits = FMT == 0 ? ((1u << 7) | (1u << 10)) : 0u;
-    const uint32_t idesc = (1u << 4) | fmtbits | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
-    const int nc = tid;
-    const float crec0 = (FMT == 1 && c0 + nc < d) ? col_recip[c0 + nc] : 1.f;
-    const uint16_t cmask = (uint16_t)((1u << CL) - 1u);
-    int64_t committed = -1;   // thread 0: the last chunk whose MMAs were committed
-    bool ok = true;
-    for (int64_t c = 0; c < nchunks; ++c) {
-        const int s = (int)(c & 1);
-        unsigned char* zt = ops + s * STAGE;
-        unsigned char* at = zt + ZB;
-        if (c >= 2) {
-            // every CTA's MMAs of chunk c-2 are done with stage s
-            const bool w = mbar_wait_cluster_bounded(&bar_free[s], (uint32_t)(((c - 2) >> 1) & 1), status);
-            if (__syncthreads_or(!w || !ok)) {   // thread 0's waits fold in here
-                ok = false;
-                break;
-            }
-        }
-        const int64_t i0 = i_begin + c * TC_KE;
-        // this CTA's share of the Z tile: quads [rank QPC, (rank + 1) QPC) of four
-        // sketch rows, one (quad, column) Philox draw per thread, stored into every
-        // CTA's stage
-        if (tid < QPC * TC_KE) {
-            const int q = (int)rank * QPC + tid / TC_KE, i = tid % TC_KE;
-            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q < nq) z = gauss4_fast(ibase + (uint32_t)(i0 + i), zq0 + (uint32_t)((j0 >> 2) + q), level, k0, k1);
-            const float zr[4] = {z.x, z.y, z.z, z.w};
-            const uint32_t zbase = smem_u32(zt);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                if (FMT == 0) {
-                    const uint32_t off = kmaj<RB>(4 * q + r, 2 * i);
-                    const __nv_bfloat16 h = __float2bfloat16_rn(zr[r]);
-                    const uint16_t v = *reinterpret_cast<const uint16_t*>(&h);
-#pragma unroll
-                    for (int p = 0; p < CL; ++p) st_cluster_u16(mapa_shared(zbase + off, (uint32_t)p), v);
-                } else {
-                    const uint32_t off = kmaj<RB>(4 * q + r, i);
-                    const uint8_t v = (uint8_t)__nv_cvt_float_to_fp8(zr[r], __NV_SATFINITE, __NV_E4M3);
-#pragma unroll
-                    for (int p = 0; p < CL; ++p) st_cluster_u8(mapa_shared(zbase + off, (uint32_t)p), v);
-                }
-            }
-            // the stores above are read by the peers' tensor cores (async proxy)
-            asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
-        }
-        // A tile from the staging buffer: thread = one column, all 32 rows
-        {
-            const bool w = mbar_wait_bounded(&bar_tma[s], (uint32_t)((c >> 1) & 1), status);
-            if (__syncthreads_or(!w || !ok)) {
-                ok = false;
-                break;
-            }
-            const float* sb = stg + (size_t)s * TC_KE * TC_N;
-            const int rvalid = (int)min((int64_t)TC_KE, i_end - i0);
-            constexpr int G = FMT == 0 ? 8 : 16;
-#pragma unroll
-            for (int g = 0; g < TC_KE / G; ++g) {
-                float v0[G];
-#pragma unroll
-                for (int t = 0; t < G; ++t) {
-                    const int r = G * g + t;
-                    const bool rv = r < rvalid;
-                    const int half = nc >= 256;
-                    const float a = sb[half * TC_KE * 256 + r * 256 + (nc & 255)];
-                    v0[t] = rv ? (FMT == 1 ? __fmul_rn(a, crec0) : a) : 0.f;
-                }
-                uint4 p0;
-                if (FMT == 0) {
-                    p0 = make_uint4(pack_bf16(v0[0], v0[1]), pack_bf16(v0[2], v0[3]), pack_bf16(v0[4], v0[5]),
-                                    pack_bf16(v0[6], v0[7]));
-                } else {
-                    p0 = make_uint4(pack_e4m3(v0[0], v0[1], v0[2 % G], v0[3 % G]),
-                                    pack_e4m3(v0[4 % G], v0[5 % G], v0[6 % G], v0[7 % G]),
-                                    pack_e4m3(v0[8 % G], v0[9 % G], v0[10 % G], v0[11 % G]),
-                                    pack_e4m3(v0[12 % G], v0[13 % G], v0[14 % G], v0[15 % G]));
-                }
-                *reinterpret_cast<uint4*>(at + kmaj<RB>(nc, 16 * g)) = p0;
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {
-            // this CTA's share of chunk c is in every CTA's stage s
-            const uint32_t zf = smem_u32(&bar_zfull[s]);
-#pragma unroll
-            for (int p = 0; p < CL; ++p) arrive_cluster(mapa_shared(zf, (uint32_t)p));
-            // the staging buffer of chunk c is free again: fetch chunk c + 2 into it
-            if (c + 2 < nchunks) issue_tma(c + 2);
-            // every share of the Z tile has arrived
-            if (!mbar_wait_cluster_bounded(&bar_zfull[s], (uint32_t)((c >> 1) & 1), status)) {
-                ok = false;
-            } else {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tc_fence_after();
-                const uint32_t za = smem_u32(zt), aa = smem_u32(at);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-#pragma unroll
-                    for (int ks = 0; ks < KSTEPS; ++ks) {
-                        const uint64_t ad = umma_desc(za + ks * 256, 128, (RB / 16) * 128);
-                        const uint64_t bd = umma_desc(aa + (uint32_t)h * (256 / 8) * (RB / 16) * 128 + ks * 256, 128,
-                                                      (RB / 16) * 128);
-                        const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
-                        const uint32_t tacc = taddr + (uint32_t)(h * 256);
-                        if (FMT == 0) {
-                            asm volatile(
-                                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tacc),
-                                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-                        } else {
-                            asm volatile(
-                                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tacc),
-                                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-                        }
-                    }
-                }
-            }
-            // completion of these MMAs frees stage s in every CTA of the cluster
-            // (also after a failed wait: the commit tracks whatever was issued)
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                    smem_u32(&bar_free[s])),
-                "h"(cmask)
-                : "memory");
-            committed = c;
-        }
-    }
-    if (ok && nchunks > 0) {
-        const int64_t last = nchunks - 1;
-        if (tid == 0) {
-            if (!mbar_wait_cluster_bounded(&bar_free[last & 1], (uint32_t)((last >> 1) & 1), status)) ok = false;
-        }
-    }
-    ok = !__syncthreads_or(!ok);
-    if (!ok && tid == 0) {
-        // let the (at most two) staging loads still in flight land, and this
-        // CTA's MMAs finish, before the tensor memory is freed
-        for (int64_t cc = max((int64_t)0, issued - 2); cc < issued; ++cc)
-            mbar_wait_bounded(&bar_tma[cc & 1], (uint32_t)((cc >> 1) & 1), status);
-        if (committed >= 0)
-            mbar_wait_cluster_bounded(&bar_free[committed & 1], (uint32_t)((committed >> 1) & 1), status);
-    }
-    tc_fence_after();
-    if (ok) {
-        const int quad = warp & 3, cpart = warp >> 2;
-        float* tile = stg + warp * (32 * 33);
-#pragma unroll 1
-        for (int cc = 0; cc < TC_N / 4; cc += 32) {
-            const int colb = cpart * (TC_N / 4) + cc;
-            uint32_t v[32];
-            const uint32_t a = taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)colb;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(a));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int t = 0; t < 32; ++t) tile[lane * 33 + t] = nchunks > 0 ? __uint_as_float(v[t]) : 0.f;
-            __syncwarp();
-            const int cidx = c0 + colb + lane;
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-                const int grow = 32 * quad + rr;
-                if (grow < mrows && cidx < d)
-                    part[((size_t)blockIdx.z * m + j0 + grow) * d + cidx] = tile[rr * 33 + lane];
-            }
-            __syncwarp();
-        }
-    }
-    tc_fence_before();
-    // no peer stores into this CTA's shared memory or arrives on its barriers
-    // after this point
-    cluster_sync_all();
-    tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_N));
-}
-
 // Column maxima of |A| (as ordered uint bits of non-negative floats).
 __global__ void k_col_amax(const float* __restrict__ A, int64_t n, int d, int64_t rows_per_block,
                            unsigned* __restrict__ amax) {
@@ -707,56 +386,6 @@ int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int
     }
     dim3 grid((unsigned)MT, (unsigned)NT, (unsigned)KS);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    // the cluster form when the column tiles group into clusters of 8, 4 or 2
-    // CTAs that the device can hold at once
-    auto launch_cl = [&](auto kern, int fmt, int cl, const float* crec) -> int {
-        IHS_CUDA_TRY(ihs_allow_smem(kern, tc_smem(fmt)));
-        cudaLaunchConfig_t cfg;
-        memset(&cfg, 0, sizeof(cfg));
-        cfg.gridDim = grid;
-        cfg.blockDim = dim3(TC_THREADS);
-        cfg.dynamicSmemBytes = tc_smem(fmt);
-        cfg.stream = ctx->stream;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 1;
-        attr[0].val.clusterDim.y = (unsigned)cl;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
-            cudaGetLastError();
-            return IHS_EINVAL;   // not resident as a cluster: the caller takes the single-CTA form
-        }
-        IHS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, amap, n, (int)d, m, rows_per_split, (uint32_t)level, k0, k1,
-                                        (uint32_t)(zrow0 >> 2), (uint32_t)grow0, crec, ctx->d_status, part));
-        ihs_count_launch();
-        return IHS_OK;
-    };
-    int cl = 0;
-    if (tma) {
-        for (int c : {8, 4, 2})
-            if (NT % c == 0) {
-                cl = c;
-                break;
-            }
-    }
-    bool done = false;
-    if (cl) {
-        int st = IHS_EINVAL;
-        if (fp8) {
-            st = cl == 8 ? launch_cl(k_gauss_tc_cl<1, 8>, 1, 8, crecip)
-               : cl == 4 ? launch_cl(k_gauss_tc_cl<1, 4>, 1, 4, crecip)
-                         : launch_cl(k_gauss_tc_cl<1, 2>, 1, 2, crecip);
-        } else {
-            st = cl == 8 ? launch_cl(k_gauss_tc_cl<0, 8>, 0, 8, nullptr)
-               : cl == 4 ? launch_cl(k_gauss_tc_cl<0, 4>, 0, 4, nullptr)
-                         : launch_cl(k_gauss_tc_cl<0, 2>, 0, 2, nullptr);
-        }
-        if (st == IHS_OK) done = true;
-        else if (st != IHS_EINVAL) return st;
-    }
     auto launch = [&](auto kern, int fmt, const float* crec) -> int {
         IHS_CUDA_TRY(ihs_allow_smem(kern, tc_smem(fmt)));
         kern<<<grid, TC_THREADS, tc_smem(fmt), ctx->stream>>>(amap, A, n, (int)d, m, rows_per_split, (uint32_t)level,
@@ -764,11 +393,9 @@ int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int
                                                               ctx->d_status, part);
         return IHS_OK;
     };
-    if (!done) {
-        if (fp8) IHS_TRY(tma ? launch(k_gauss_tc<1, true>, 1, crecip) : launch(k_gauss_tc<1, false>, 1, crecip));
-        else IHS_TRY(tma ? launch(k_gauss_tc<0, true>, 0, nullptr) : launch(k_gauss_tc<0, false>, 0, nullptr));
-        IHS_LAUNCH_CHECK();
-    }
+    if (fp8) IHS_TRY(tma ? launch(k_gauss_tc<1, true>, 1, crecip) : launch(k_gauss_tc<1, false>, 1, crecip));
+    else IHS_TRY(tma ? launch(k_gauss_tc<0, true>, 0, nullptr) : launch(k_gauss_tc<0, false>, 0, nullptr));
+    IHS_LAUNCH_CHECK();
     const int64_t count = m * d;
     const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
     if (fp8) {

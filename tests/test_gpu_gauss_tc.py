@@ -48,10 +48,10 @@ def test_gauss_bf16_parity(torch_cuda, n, d, m):
 @pytest.mark.parametrize("n,d,m,precision", [(4096, 1024, 200, "bf16"), (3000, 4096, 64, "bf16"),
                                              (2048, 2048, 130, "bf16"), (4096, 1024, 128, "fp8"),
                                              (1500, 4096, 20, "fp8")])
-def test_gauss_cluster_parity(torch_cuda, n, d, m, precision):
-    """Widths of 2, 4 or 8 column tiles take the cluster form, in which the CTAs
-    of a cluster share each Z tile (clusters of 2, 4 and 8; a partial last row
-    tile; a ragged last chunk of rows)."""
+def test_gauss_wide_parity(torch_cuda, n, d, m, precision):
+    """Widths of 2, 4 and 8 column tiles of 512, a partial last tile of sketch
+    rows and a ragged last chunk of rows of A, against the oracle's rounded
+    sketch."""
     A = problems.random_matrix(n, d, seed=n + 5 * d + m)
     if precision == "fp8":
         A[:, 3] *= 50.0
