@@ -92,7 +92,7 @@ extern "C" int ihs_ctx_create(ihs_ctx** out, void* stream, const ihs_params* p) 
         if (cudaMallocHost(&c->pinned, 64 * sizeof(double)) != cudaSuccess) { st = IHS_ENOMEM; break; }
         if (cudaMalloc(&c->d_status, 256) != cudaSuccess) { st = IHS_ENOMEM; break; }
         if (cudaMemsetAsync(c->d_status, 0, 256, c->stream) != cudaSuccess) { st = IHS_ECUDA; break; }
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 6; ++i)
             if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { st = IHS_ECUDA; break; }
         if (st != IHS_OK) break;
         if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess) { st = IHS_ECUDA; break; }
@@ -115,7 +115,7 @@ extern "C" int ihs_ctx_destroy(ihs_ctx* c) {
         if (c->buf[i]) cudaFree(c->buf[i]);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->d_status) cudaFree(c->d_status);
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 6; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     for (int i = 0; i < 8; ++i)
         if (c->fev[i]) cudaEventDestroy(c->fev[i]);

@@ -67,7 +67,7 @@ struct ihs_ctx {
     size_t buf_bytes[SLOT_COUNT];
     double* pinned;          // host pinned scratch (64 doubles)
     unsigned* d_status;      // device status word (IHS_DEV_*)
-    cudaEvent_t ev[4];
+    cudaEvent_t ev[6];       // [4], [5]: the solver's sketch + factor interval
     cudaStream_t aux;        // private stream for the look-ahead Cholesky (joined back before return)
     cudaEvent_t fev[8];      // fork/join events of the look-ahead Cholesky
     void* lanes;             // batched solves: sub-contexts, streams and memory pool kept across calls
@@ -175,7 +175,8 @@ int ihs_factor_alloc_pool(ihs_ctx* ctx, cudaMemPool_t pool, const float* SA, int
 void ihs_factor_release_pool(ihs_factor_t* F, cudaStream_t s);
 // Factor into the context's scratch (no allocation once the slot is large
 // enough); F is caller storage, valid until the next call with the same ctx.
-int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t* F);
+int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t* F,
+                       bool check = true);   // check = false: enqueue only, the caller reads the status word later
 int ihs_apply_enqueue(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* gt,
                       double* d_r);
 

@@ -1517,14 +1517,15 @@ static void factor_bind(ihs_factor_t* F, char* base, const FactorLayout& l) {
     }
 }
 
-int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t* F) {
+int ihs_factor_scratch(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t* F,
+                       bool check) {
     if (!ctx || !SA || !F || m < 1 || d < 1 || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
     factor_init(F, ctx, SA, m, d, nu, 0, true);
     const FactorLayout l = factor_layout(F->k, m, d, F->fused, ctx->sm_count);
     void* ws = nullptr;
     IHS_TRY(ihs_scratch(ctx, SLOT_FACTOR, l.total, &ws));
     factor_bind(F, static_cast<char*>(ws), l);
-    return ihs_factor_build(ctx, F);
+    return check ? ihs_factor_build(ctx, F) : ihs_factor_enqueue(ctx, F);
 }
 
 int ihs_factor_alloc(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** out) {

@@ -295,7 +295,31 @@ struct Solver {
     ihs_allreduce_fn ar;
     void* ar_user;
     double* gp;           // d + 1 FP64 gradient partials (sharded solves)
+    bool sketch_pending;  // a level's sketch + factor awaits its status check and timing
 };
+
+// Enqueue the copy of the device status word next to the scalars a caller is
+// about to read back (the factor of a new level is checked there instead of
+// with a synchronisation of its own).
+int status_copy(Solver& S) {
+    unsigned* hs = reinterpret_cast<unsigned*>(S.ctx->pinned + 16);
+    IHS_CUDA_TRY(cudaMemcpyAsync(hs, S.ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, S.ctx->stream));
+    return IHS_OK;
+}
+
+// After the synchronisation: the pending level's timing, and any device error
+// (a non-positive pivot, a wait that gave up) as its status code.
+int status_after_sync(Solver& S) {
+    if (S.sketch_pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, S.ctx->ev[4], S.ctx->ev[5]);
+        S.ms_sketch += ms;
+        S.sketch_pending = false;
+    }
+    const unsigned hs = *reinterpret_cast<const unsigned*>(S.ctx->pinned + 16);
+    if (hs != 0u) return ihs_check_status(S.ctx);
+    return IHS_OK;
+}
 
 // Sum a device buffer over the ranks of a sharded solve, in place.
 int shard_sum(Solver& S, void* buf, int64_t count, int32_t dtype) {
@@ -328,7 +352,7 @@ int sketch_level(Solver& S, int64_t m, int level) {
     IHS_TRY(ihs_scratch(ctx, slot, (size_t)m * S.d * sizeof(float), &ws));
     S.SA = static_cast<float*>(ws);
     S.sa_slot = slot;
-    IHS_CUDA_TRY(cudaEventRecord(ctx->ev[0], ctx->stream));
+    IHS_CUDA_TRY(cudaEventRecord(ctx->ev[4], ctx->stream));
     if (S.ar) {
         IHS_TRY(ihs_sketch_shard_enqueue(ctx, S.A, S.n, S.d, S.row0, S.n_total, m, ctx->p.kind, ctx->p.seed, draw,
                                          S.SA));
@@ -343,13 +367,12 @@ int sketch_level(Solver& S, int64_t m, int level) {
     } else {
         IHS_TRY(ihs_sketch_enqueue(ctx, S.A, S.n, S.d, m, ctx->p.kind, ctx->p.seed, draw, S.SA));
     }
-    IHS_TRY(ihs_factor_scratch(ctx, S.SA, m, S.d, S.nu, &S.Fs));   // synchronises (pivot check)
+    // enqueue only: the pivot check (status word) and the interval's timing are
+    // read after the next synchronisation, in evaluate() or reapply()
+    IHS_TRY(ihs_factor_scratch(ctx, S.SA, m, S.d, S.nu, &S.Fs, false));
     S.F = &S.Fs;
-    IHS_CUDA_TRY(cudaEventRecord(ctx->ev[1], ctx->stream));
-    IHS_CUDA_TRY(cudaEventSynchronize(ctx->ev[1]));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
-    S.ms_sketch += ms;
+    IHS_CUDA_TRY(cudaEventRecord(ctx->ev[5], ctx->stream));
+    S.sketch_pending = true;
     S.m = m;
     S.level = level;
     return IHS_OK;
@@ -388,7 +411,9 @@ int evaluate(Solver& S, int ix, int ig, int igt, double* r, double* ax2, double*
     }
     IHS_CUDA_TRY(cudaEventRecord(ctx->ev[3], ctx->stream));
     IHS_CUDA_TRY(cudaMemcpyAsync(ctx->pinned, S.dsc, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    IHS_TRY(status_copy(S));
     IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    IHS_TRY(status_after_sync(S));
     float ms = 0.f, msg = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
     cudaEventElapsedTime(&msg, ctx->ev[2], ctx->ev[0]);
@@ -405,7 +430,9 @@ int reapply(Solver& S, int ig, int igt, double* r) {
     ihs_ctx* ctx = S.ctx;
     IHS_TRY(ihs_apply_enqueue(ctx, S.F, S.vec[ig], S.vec[igt], S.dsc + 0));
     IHS_CUDA_TRY(cudaMemcpyAsync(ctx->pinned, S.dsc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    IHS_TRY(status_copy(S));
     IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    IHS_TRY(status_after_sync(S));
     *r = ctx->pinned[0];
     return IHS_OK;
 }
