@@ -223,6 +223,15 @@ int ihs_grad_noalloc(void* stream, const float* A, const float* b, int64_t n, in
 int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d,
               double nu, double tol, float* x, ihs_report* rep_h);
 
+/* ihs_solve with HOST buffers, end to end: A_h (n x d), b_h (n) and x_h (d,
+ * x_1 on entry, the last iterate on exit) are host FP32 arrays; the call copies
+ * them into device memory the context owns (grown as needed, kept for the next
+ * call), solves, copies x back and synchronises.  Page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister) gives the copies the full host-device
+ * bandwidth; pageable memory works but is staged.  Errors as ihs_solve. */
+int ihs_solve_host(ihs_ctx* ctx, const float* A_h, const float* b_h, int64_t n, int64_t d,
+                   double nu, double tol, float* x_h, ihs_report* rep_h);
+
 /* Underdetermined case, n <= d (App. A.2): the same controller on the dual
  * z* = argmin 1/2 ||A^T z||^2 + nu^2/2 ||z||^2 - b^T z, whose data matrix is A^T
  * (d x n) and whose gradient is A A^T z - b + nu^2 z; sketches are drawn over

@@ -51,6 +51,7 @@ enum ScratchSlot {
     SLOT_FACTOR,          // the solver's factor (K/L, block inverses, X, X^T, apply scratch)
     SLOT_DUAL,            // underdetermined solves: A^T and the dual gradient's scratch
     SLOT_SOLVE_SA2,       // nested sketches: the previous level's SA while the next one is formed
+    SLOT_HOST_IN,         // ihs_solve_host: device copies of the caller's A, b and x
     SLOT_COUNT
 };
 

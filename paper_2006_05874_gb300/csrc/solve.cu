@@ -626,6 +626,39 @@ extern "C" int ihs_solve(ihs_ctx* ctx, const float* A, const float* b, int64_t n
     return st;
 }
 
+extern "C" int ihs_solve_host(ihs_ctx* ctx, const float* A_h, const float* b_h, int64_t n, int64_t d, double nu,
+                              double tol, float* x_h, ihs_report* rep_h) {
+    if (!ctx || !A_h || !b_h || !x_h) return IHS_EINVAL;
+    if (n < 1 || d < 1 || n < d || !(nu > 0.0) || !isfinite(nu)) return IHS_EINVAL;
+    IhsRange range("ihs_solve_host");
+    // A, b, x in one context-owned block (each piece 256-byte aligned)
+    const size_t bA = ((size_t)n * d * sizeof(float) + 255) & ~(size_t)255;
+    const size_t bb = ((size_t)n * sizeof(float) + 255) & ~(size_t)255;
+    const size_t bx = ((size_t)d * sizeof(float) + 255) & ~(size_t)255;
+    void* ws = nullptr;
+    IHS_TRY(ihs_scratch(ctx, SLOT_HOST_IN, bA + bb + bx, &ws));
+    char* base = static_cast<char*>(ws);
+    float* A = reinterpret_cast<float*>(base);
+    float* b = reinterpret_cast<float*>(base + bA);
+    float* x = reinterpret_cast<float*>(base + bA + bb);
+    // one copy per piece, A in 256 MiB pieces so that the first ones can start
+    // the DMA engines while the next are issued
+    const size_t total = (size_t)n * d * sizeof(float), piece = (size_t)256 << 20;
+    for (size_t o = 0; o < total; o += piece) {
+        const size_t len = total - o < piece ? total - o : piece;
+        IHS_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(A) + o, reinterpret_cast<const char*>(A_h) + o, len,
+                                     cudaMemcpyHostToDevice, ctx->stream));
+    }
+    IHS_CUDA_TRY(cudaMemcpyAsync(b, b_h, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    IHS_CUDA_TRY(cudaMemcpyAsync(x, x_h, (size_t)d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    const int st = ihs_solve(ctx, A, b, n, d, nu, tol, x, rep_h);
+    if (st == IHS_OK || st == IHS_EMAXITER) {
+        IHS_CUDA_TRY(cudaMemcpyAsync(x_h, x, (size_t)d * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        IHS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    return st;
+}
+
 extern "C" int ihs_solve_resume(ihs_ctx* ctx, const float* A, const float* b, int64_t n, int64_t d, double nu,
                                 double tol, float* x, float* x_prev, ihs_state* st_h, ihs_report* rep_h) {
     if (!ctx || !A || !b || !x || !x_prev || !st_h) return IHS_EINVAL;

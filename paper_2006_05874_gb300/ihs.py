@@ -89,6 +89,7 @@ _SIGNATURES = {
     "ihs_apply_hinv": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
     "ihs_grad": ([_vp, _vp, _vp, _i64, _i64, _dbl, _vp, _vp, ctypes.POINTER(_dbl)], ctypes.c_int),
     "ihs_solve": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
+    "ihs_solve_host": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_solve_resume": ([_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, _vp, ctypes.POINTER(State),
                           ctypes.POINTER(Report)], ctypes.c_int),
     "ihs_sketch_shard": ([_vp, _vp, _i64, _i64, _i64, _i64, _i64, _i32, _u64, _i32, _vp], ctypes.c_int),
@@ -292,6 +293,20 @@ class Context:
         st = _lib.ihs_solve(self.handle, _ptr(A), _ptr(b), n, d, float(nu), float(tol), _ptr(x), ctypes.byref(rep))
         if st != IHS_OK and (st != IHS_EMAXITER or raise_on_maxiter):
             _check("ihs_solve", st)
+        return rep
+
+    def solve_host(self, A_h, b_h, nu, x_h, tol=0.0, raise_on_maxiter=False):
+        """ihs_solve_host: A_h, b_h, x_h are contiguous float32 CPU tensors (pinned
+        for full copy bandwidth); x_h is updated in place."""
+        for t in (A_h, b_h, x_h):
+            if t.is_cuda or not t.is_contiguous() or t.dtype != __import__("torch").float32:
+                raise ValueError("expected contiguous float32 host tensors")
+        n, d = A_h.shape
+        rep = Report()
+        st = _lib.ihs_solve_host(self.handle, ctypes.c_void_p(A_h.data_ptr()), ctypes.c_void_p(b_h.data_ptr()), n, d,
+                                 float(nu), float(tol), ctypes.c_void_p(x_h.data_ptr()), ctypes.byref(rep))
+        if st != IHS_OK and (st != IHS_EMAXITER or raise_on_maxiter):
+            _check("ihs_solve_host", st)
         return rep
 
     def solve_resume(self, A, b, nu, x, x_prev, state=None, tol=0.0):

@@ -149,3 +149,22 @@ def test_solve_spectral_full_size_schedule(ctx, torch_cuda):
     ref = oracle_ihs.adaptive_ihs(p.A, p.b, p.nu, kind="srht", variant="gd", tol=1e-5)
     assert ref.levels[-1] >= 1024
     assert_same_schedule(events, ref.trace, "srht")
+
+
+def test_solve_host_buffers_match_device_solve(ctx, torch_cuda, exp_problem):
+    """ihs_solve_host (host A, b, x; the copies inside the call) returns the
+    device-buffer solve's bits, with page-locked and with pageable memory."""
+    torch = torch_cuda
+    p, xs = exp_problem
+    ctx.set_params(kind="srht", variant="gd", tol=1e-5, m_init=1, max_iter=500)
+    x_d = torch.zeros(p.d, device="cuda")
+    rep_d = ctx.solve(torch.from_numpy(p.A).cuda(), torch.from_numpy(p.b).cuda(), p.nu, x_d)
+    for pinned in (True, False):
+        A_h, b_h = torch.from_numpy(p.A.copy()), torch.from_numpy(p.b.copy())
+        x_h = torch.zeros(p.d)
+        if pinned:
+            A_h, b_h, x_h = A_h.pin_memory(), b_h.pin_memory(), x_h.pin_memory()
+        rep = ctx.solve_host(A_h, b_h, p.nu, x_h)
+        assert rep.status == 0 and rep.levels() == rep_d.levels()
+        assert torch.equal(x_h, x_d.cpu())
+    assert linalg.relative_error(p.A, p.nu, x_h.numpy(), xs) <= 1e-5
