@@ -81,6 +81,10 @@ extern "C" int ihs_ctx_create(ihs_ctx** out, void* stream, const ihs_params* p) 
         const char* l = getenv("IHS_BARRIER_LIMIT_MS");
         const long ms = l ? strtol(l, nullptr, 10) : 0;
         c->bar_limit_ns = (ms >= 1 && ms <= 60000) ? (uint64_t)ms * 1000000ull : 1000000000ull;
+        const char* cp = getenv("IHS_CHOL_CTAS_PER_SM");
+        c->chol_per_sm = (cp && cp[0] == '1') ? 1 : 2;
+        const char* ac = getenv("IHS_APPLY_CTAS");
+        c->apply_ctas = ac ? (int)strtol(ac, nullptr, 10) : 0;
     }
     int st = IHS_OK;
     do {

@@ -489,7 +489,8 @@ int ihs_apply_fused(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* 
     int per_sm = 0;
     IHS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_fused, kApplyThreads, smem));
     if (per_sm < 1) return IHS_EINVAL;
-    const int G = ctx->sm_count;   // one CTA per SM, all resident (cooperative launch)
+    // one CTA per SM, all resident (cooperative launch), unless set lower
+    const int G = (ctx->apply_ctas >= 1 && ctx->apply_ctas < ctx->sm_count) ? ctx->apply_ctas : ctx->sm_count;
     const size_t np = ihs_apply_partials(F->k, F->m, F->d);
     ApplyArgs a;
     a.SA = F->SA;

@@ -140,8 +140,8 @@ __device__ __forceinline__ float2 df_scale(float2 a, double sc) {
 
 // commit (x, g, gt <- xc, gc, gtc for accepted problems), then the candidate
 // xc = x - mu gt with per-block partials of ||xc||^2.  grid (blocks, P).
-__global__ void kb_candidate(BVec* __restrict__ V) {
-    __shared__ double sm[256];
+__global__ void __launch_bounds__(256) kb_candidate(BVec* __restrict__ V) {
+    __shared__ double sm[8];
     BVec& v = V[blockIdx.y];
     if (!v.active && !v.commit) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -162,11 +162,13 @@ __global__ void kb_candidate(BVec* __restrict__ V) {
         }
     }
     if (!v.active || (int64_t)blockIdx.x * blockDim.x >= v.d) return;
-    sm[threadIdx.x] = sq;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = sq;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int k = 0; k < 256; ++k) s += sm[k];
+        for (int k = 0; k < 8; ++k) s += sm[k];
         v.xpart[blockIdx.x] = s;
     }
 }
@@ -244,7 +246,9 @@ __global__ void __launch_bounds__(256) kb_grad_tiles(const BVec* __restrict__ V,
     }
 }
 
-// gc = sum of the problem's tile partials (fixed order, FP64) + nu^2 xc; sc[1] = sum pax2.
+// gc = sum of the problem's tile partials + nu^2 xc, in a fixed order as a
+// compensated binary32 pair (FP64 runs at a small fraction of the FP32 rate);
+// sc[1] = sum pax2 (FP64, lane strides and a butterfly in warp 0).
 // grid (ceil(dmax / 256), P).
 __global__ void kb_grad_reduce(BVec* __restrict__ V, const int* __restrict__ tbeg, const int* __restrict__ tcnt,
                                const int64_t* __restrict__ poff, const float2* __restrict__ part,
@@ -255,17 +259,22 @@ __global__ void kb_grad_reduce(BVec* __restrict__ V, const int* __restrict__ tbe
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int t0 = tbeg[p], nt = tcnt[p];
     if (c < v.d) {
-        double s = 0.0;
+        Acc2 a{0.f, 0.f};
         for (int t = 0; t < nt; ++t) {
             const float2 q = part[poff[t0 + t] + c];
-            s += (double)q.x + (double)q.y;
+            a.add_pair(q.x, q.y);
         }
-        v.gc[c] = (float)(s + v.nu2 * (double)v.xc[c]);
+        const float nh = (float)v.nu2;
+        const float2 e = df_mul(v.xc[c], 0.f, nh, (float)(v.nu2 - (double)nh));
+        a.add_pair(e.x, e.y);
+        v.gc[c] = __fadd_rn(a.hi, a.lo);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
         double s = 0.0;
-        for (int t = 0; t < nt; ++t) s += pax2[t0 + t];
-        v.sc[1] = s;
+        for (int t = threadIdx.x; t < nt; t += 32) s += pax2[t0 + t];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) v.sc[1] = s;
     }
 }
 
@@ -412,7 +421,8 @@ __global__ void __launch_bounds__(256) kb_mrhs_atr(const float* __restrict__ A, 
     }
 }
 
-// gc of member k = sum over splits (fixed order, FP64) + nu_k^2 xc; sc[1] from the residual tiles.
+// gc of member k = sum over splits + nu_k^2 xc (fixed order, compensated
+// binary32 pair); sc[1] from the residual tiles (FP64, warp 0).
 __global__ void kb_mrhs_reduce(BVec* __restrict__ V, const int* __restrict__ members, int K, int64_t d, int splits,
                                const float2* __restrict__ Gpart, int rtiles, const double* __restrict__ pax2) {
     const int k = blockIdx.y;
@@ -420,17 +430,22 @@ __global__ void kb_mrhs_reduce(BVec* __restrict__ V, const int* __restrict__ mem
     if (!v.active) return;
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c < d) {
-        double s = 0.0;
+        Acc2 a{0.f, 0.f};
         for (int sp = 0; sp < splits; ++sp) {
             const float2 q = Gpart[((size_t)sp * d + c) * K + k];
-            s += (double)q.x + (double)q.y;
+            a.add_pair(q.x, q.y);
         }
-        v.gc[c] = (float)(s + v.nu2 * (double)v.xc[c]);
+        const float nh = (float)v.nu2;
+        const float2 e = df_mul(v.xc[c], 0.f, nh, (float)(v.nu2 - (double)nh));
+        a.add_pair(e.x, e.y);
+        v.gc[c] = __fadd_rn(a.hi, a.lo);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
         double s = 0.0;
-        for (int t = 0; t < rtiles; ++t) s += pax2[(size_t)t * MR_K + k];
-        v.sc[1] = s;
+        for (int t = threadIdx.x; t < rtiles; t += 32) s += pax2[(size_t)t * MR_K + k];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) v.sc[1] = s;
     }
 }
 

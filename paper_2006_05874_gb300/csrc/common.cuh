@@ -83,6 +83,12 @@ struct ihs_ctx {
     // barrier waits.
     int test_bar_unreachable;
     uint64_t bar_limit_ns;
+    // CTAs per SM of the persistent Cholesky: 2 (default; the second CTA's
+    // warps hide the latencies of the double-float tile updates) or 1
+    // (IHS_CHOL_CTAS_PER_SM=1, a launch-shape setting read at creation)
+    int chol_per_sm;
+    // CTAs of the fused apply (IHS_APPLY_CTAS, 1 .. SM count; 0: one per SM)
+    int apply_ctas;
 };
 
 // Decision log of the controller (api.cu): cleared at the start of a solve,
@@ -158,6 +164,11 @@ int ihs_gauss_fp32_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, i
 int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
                          int32_t level, float* SA, int fp8, int64_t zrow0 = 0, int64_t m_scale = 0,
                          int64_t grow0 = 0);   // rows [zrow0, zrow0 + m) of the sketch of size m_scale; A's row 0 is global row grow0
+// out[e] = fl32(scale * colscale[e % d] * sum_k part_k[e]) over K partials of
+// `count` elements (float, or hi + lo float2 pairs when `pairs`), summed in a
+// fixed order; colscale may be NULL.
+int ihs_reduce_parts_enqueue(ihs_ctx* ctx, const float* part, bool pairs, int K, int64_t count, int64_t d,
+                             double scale, const float* colscale, float* out);
 // A row shard's term of the sketch (rows [row0, row0 + n) of n_total) and of
 // the gradient (FP64 partial sums, d + 1 doubles: A^T (A x - b) and ||A x||^2).
 int ihs_sketch_shard_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t row0, int64_t n_total,
@@ -307,6 +318,25 @@ struct Acc2 {
         lo = __fadd_rn(lo, __fadd_rn(e, l2));
     }
 };
+
+// A double as an unevaluated binary32 pair (hi + lo), on the host.
+struct DfConst {
+    float hi, lo;
+};
+inline DfConst df_const(double v) {
+    const float hi = (float)v;
+    return DfConst{hi, (float)(v - (double)hi)};
+}
+
+// (hi + lo) * (sh + sl) as a normalised pair: the product of two double-float
+// numbers with the lo * sl term dropped (below 2^-46 relative).
+__device__ __forceinline__ float2 df_mul(float hi, float lo, float sh, float sl) {
+    float p, e;
+    two_prod(hi, sh, p, e);
+    e = __fmaf_rn(hi, sl, __fmaf_rn(lo, sh, e));
+    const float s = __fadd_rn(p, e);
+    return make_float2(s, __fsub_rn(e, __fsub_rn(s, p)));
+}
 
 // v as hi + lo with integer operations (no FP64 instruction: conversions from
 // double run at the FP64 rate): hi keeps the sign, the exponent and the top 23

@@ -134,26 +134,40 @@ __global__ void __launch_bounds__(256) k_gram_c32(const float* __restrict__ SA, 
         }
 }
 
-// G tile t = sum over the KS splits (fixed order, FP64) of hi + lo, + nu^2 I.
+// G tile t = sum over the KS splits of hi + lo, + nu^2 I: the pairs summed in
+// a fixed order as a compensated binary32 pair (FP64 runs at a small fraction
+// of the FP32 rate), then stored as a normalised pair (out_df) or widened to
+// FP64.  Grid (tiles, FB * FB / 256): one entry per thread, its KS loads in
+// batches of eight ahead of the dependent additions.
 __global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ part, int KS, int64_t ntiles,
-                                                     int64_t kdim, double nu2, int out_df, double* __restrict__ G) {
+                                                     int64_t kdim, float2 nu2df, int out_df, double* __restrict__ G) {
     const int64_t t = blockIdx.x;
     int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
     while (I * (I + 1) / 2 > t) --I;
     while ((I + 1) * (I + 2) / 2 <= t) ++I;
     const int64_t J = t - I * (I + 1) / 2;
-    for (int e = threadIdx.x; e < FB * FB; e += 256) {
-        const int rr = e / FB, cc = e % FB;
-        const int64_t r = I * FB + rr, c = J * FB + cc;
-        if (r >= kdim || c >= kdim || c > r) continue;
-        double acc = 0.0;
-        for (int y = 0; y < KS; ++y) {
-            const float2 v = part[((size_t)y * ntiles + t) * FB * FB + e];
-            acc += (double)v.x + (double)v.y;
+    const int e = blockIdx.y * 256 + threadIdx.x;
+    const int rr = e / FB, cc = e % FB;
+    const int64_t r = I * FB + rr, c = J * FB + cc;
+    if (r >= kdim || c >= kdim || c > r) return;
+    Acc2 acc{0.f, 0.f};
+    for (int y0 = 0; y0 < KS; y0 += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (y0 + u < KS) v[u] = part[((size_t)(y0 + u) * ntiles + t) * FB * FB + e];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (y0 + u >= KS) break;
+            acc.add_pair(v[u].x, v[u].y);
         }
-        const double v = acc + (r == c ? nu2 : 0.0);
-        if (out_df) reinterpret_cast<float2*>(G)[r * kdim + c] = df_split(v);
-        else G[r * kdim + c] = v;
+    }
+    if (r == c) acc.add_pair(nu2df.x, nu2df.y);
+    if (out_df) {
+        const float hi = __fadd_rn(acc.hi, acc.lo);
+        reinterpret_cast<float2*>(G)[r * kdim + c] = make_float2(hi, __fsub_rn(acc.lo, __fsub_rn(hi, acc.hi)));
+    } else {
+        G[r * kdim + c] = (double)acc.hi + (double)acc.lo;
     }
 }
 
@@ -840,25 +854,85 @@ __device__ __forceinline__ float l_entry(const double* L, int l_df, int64_t idx)
     return (float)L[idx];
 }
 
-__global__ void __launch_bounds__(FB) k_blockinv32(const double* __restrict__ L, int l_df, int64_t k,
-                                                   float* __restrict__ X) {
-    __shared__ float l[FB][FB + 1];
-    __shared__ float w[FB][FB + 1];
+// One 64 x 64 diagonal block L_b = [A 0; B C] per CTA of 256 threads, its
+// inverse in two levels: A^-1 and C^-1 (32 x 32 each) by forward substitution,
+// thread c of each half forming column c, w_r = (delta_rc - sum_{q<r} l_rq w_q)
+// / l_rr with the column in registers (rows above the diagonal give w_q = 0,
+// which adds nothing); then the lower-left block -C^-1 (B A^-1) by two 32 x 32
+// products over all threads.  The serial chains are 32 rows long and the
+// unrolled code stays small.  Padding rows of a short last block carry 1 on
+// the diagonal.
+__global__ void __launch_bounds__(256) k_blockinv32(const double* __restrict__ L, int l_df, int64_t k,
+                                                    float* __restrict__ X) {
+    constexpr int H = FB / 2;                      // 32
+    __shared__ __align__(16) float l[FB][FB + 4];  // the block of L
+    __shared__ __align__(16) float w[FB][FB + 4];  // its inverse (lower)
+    __shared__ __align__(16) float t[H][H + 4];    // B A^-1
+    const int tid = threadIdx.x;
     const int64_t b0 = (int64_t)blockIdx.x * FB;
     const int nb = (int)(k - b0 < FB ? k - b0 : FB);
-    for (int e = threadIdx.x; e < FB * FB; e += FB) {
+#pragma unroll
+    for (int i = 0; i < FB * FB / 256; ++i) {
+        const int e = tid + 256 * i;
         const int r = e / FB, c = e % FB;
-        l[r][c] = (r < nb && c < nb && c <= r) ? l_entry(L, l_df, (b0 + r) * k + b0 + c) : 0.f;
+        l[r][c] = (r < nb && c < nb && c <= r) ? l_entry(L, l_df, (b0 + r) * k + b0 + c) : (r == c ? 1.f : 0.f);
     }
     __syncthreads();
-    const int c = threadIdx.x;
-    if (c < nb) {
-        for (int r = c; r < nb; ++r) {
-            float s = (r == c) ? 1.f : 0.f;
-            for (int q = c; q < r; ++q) s = __fmaf_rn(-l[r][q], w[q][c], s);
-            w[r][c] = s / l[r][r];
+    if (tid < FB) {   // A^-1 (tid < 32) and C^-1 (32 <= tid < 64)
+        const int o = (tid / H) * H, c = tid % H;
+        float v[H];
+#pragma unroll
+        for (int r = 0; r < H; ++r) {
+            float sacc = (r == c) ? 1.f : 0.f;
+#pragma unroll
+            for (int q = 0; q < r; q += 4) {
+                const float4 lv = *reinterpret_cast<const float4*>(&l[o + r][o + q]);
+                sacc = __fmaf_rn(-lv.x, v[q], sacc);
+                if (q + 1 < r) sacc = __fmaf_rn(-lv.y, v[q + 1], sacc);
+                if (q + 2 < r) sacc = __fmaf_rn(-lv.z, v[q + 2], sacc);
+                if (q + 3 < r) sacc = __fmaf_rn(-lv.w, v[q + 3], sacc);
+            }
+            v[r] = __fdiv_rn(sacc, l[o + r][o + r]);
         }
-        for (int r = c; r < nb; ++r) X[(b0 + r) * k + b0 + c] = w[r][c];
+#pragma unroll
+        for (int r = 0; r < H; ++r) w[o + r][o + c] = v[r];
+    }
+    __syncthreads();
+    // thread: row i of the lower-left block, columns j0 .. j0 + 3
+    const int i = tid >> 3, j0 = (tid & 7) * 4;
+    {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);   // (B A^-1)[i][j0..]: A^-1[q][j] = 0 for q < j
+#pragma unroll 8
+        for (int q = 0; q < H; ++q) {
+            const float bq = l[H + i][q];
+            const float4 a = *reinterpret_cast<const float4*>(&w[q][j0]);
+            acc.x = __fmaf_rn(bq, a.x, acc.x);
+            acc.y = __fmaf_rn(bq, a.y, acc.y);
+            acc.z = __fmaf_rn(bq, a.z, acc.z);
+            acc.w = __fmaf_rn(bq, a.w, acc.w);
+        }
+        *reinterpret_cast<float4*>(&t[i][j0]) = acc;
+    }
+    __syncthreads();
+    {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);   // (C^-1 T)[i][j0..]: C^-1[i][q] = 0 for q > i
+#pragma unroll 8
+        for (int q = 0; q < H; ++q) {
+            const float cq = w[H + i][H + q];
+            const float4 tv = *reinterpret_cast<const float4*>(&t[q][j0]);
+            acc.x = __fmaf_rn(cq, tv.x, acc.x);
+            acc.y = __fmaf_rn(cq, tv.y, acc.y);
+            acc.z = __fmaf_rn(cq, tv.z, acc.z);
+            acc.w = __fmaf_rn(cq, tv.w, acc.w);
+        }
+        *reinterpret_cast<float4*>(&w[H + i][j0]) = make_float4(-acc.x, -acc.y, -acc.z, -acc.w);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < FB * FB / 256; ++u) {
+        const int e = tid + 256 * u;
+        const int r = e / FB, c = e % FB;
+        if (c <= r && r < nb) X[(b0 + r) * k + b0 + c] = w[r][c];
     }
 }
 
@@ -915,41 +989,46 @@ __global__ void __launch_bounds__(256) k_pair_gemm(const float* __restrict__ Xf,
         }
 }
 
-// The same pair products for blocks of s >= 128 (s a multiple of 128, k a
-// multiple of 8): 128 x 128 output tiles, 8 x 8 per thread, the inner
-// dimension in double-buffered chunks of 16 staged through shared memory with
-// 16-byte global loads (A from L is converted from FP64 on the fly).  tri
-// skips the inner range where a triangular operand is zero: 1 = B lower
-// (B[q][c] = 0 for q < c: q starts at the tile's first column), 2 = A lower
-// (A[r][q] = 0 for q > r: q ends after the tile's last row).
-constexpr int PGT = 128, PGK = 16;
+// The same pair products for blocks of s a multiple of TT (TT = 128 or 64, k a
+// multiple of 8): TT x TT output tiles, TT/16 x TT/16 per thread (rows and
+// columns h 64 + 4 t + {0..3}), the inner dimension in double-buffered chunks
+// of 16 staged through shared memory with 16-byte global loads (A from L is
+// converted from its FP64 or double-float storage on the fly).  The 64 tiles
+// serve the merges whose 128 tiles would leave SMs idle.  tri skips the inner
+// range where a triangular operand is zero: 1 = B lower (B[q][c] = 0 for
+// q < c: q starts at the tile's first column), 2 = A lower (A[r][q] = 0 for
+// q > r: q ends after the tile's last row).
+constexpr int PGK = 16;
+template <int TT>
 __global__ void __launch_bounds__(256) k_pair_sgemm(const float* __restrict__ Xf, const double* __restrict__ Ld,
                                                     int a_is_l, int l_df, int64_t k, int64_t s, int64_t pstride,
-                                                    int64_t ra,
-                                                    int64_t ca, int64_t rb, int64_t cb, const float* Bsrc,
+                                                    int64_t ra, int64_t ca, int64_t rb, int64_t cb, const float* Bsrc,
                                                     float* __restrict__ C, int64_t rc, int64_t cc, float alpha,
                                                     int tri) {
-    __shared__ __align__(16) float As[2][PGK][PGT + 4];   // As[q][r]
-    __shared__ __align__(16) float Bs[2][PGK][PGT + 4];   // Bs[q][c]
+    static_assert(TT == 128 || TT == 64, "tile of 128 or 64");
+    constexpr int RT = TT / 16;          // rows (and columns) of C per thread
+    constexpr int E = TT * PGK / 256;    // A (and B) elements a thread stages per chunk: 8 or 4
+    __shared__ __align__(16) float As[2][PGK][TT + 4];   // As[q][r]
+    __shared__ __align__(16) float Bs[2][PGK][TT + 4];   // Bs[q][c]
     const int tid = threadIdx.x;
     const int64_t off = (int64_t)blockIdx.z * pstride;
-    const int64_t tr = (int64_t)blockIdx.y * PGT, tc = (int64_t)blockIdx.x * PGT;
+    const int64_t tr = (int64_t)blockIdx.y * TT, tc = (int64_t)blockIdx.x * TT;
     int64_t q0 = 0, q1 = s;
     if (tri == 1) q0 = tc;
-    if (tri == 2) q1 = min(s, tr + PGT);
-    // loaders: A row ar, inner elements [ak, ak + 8); B inner row bq, columns [bc, bc + 8)
-    const int ar = tid >> 1, ak = (tid & 1) * 8;
-    const int bq = tid >> 4, bc = (tid & 15) * 8;
+    if (tri == 2) q1 = min(s, tr + TT);
+    // loaders: A row ar, inner elements [ak, ak + E); B inner row bq, columns [bc, bc + E)
+    const int ar = tid / (PGK / E), ak = (tid % (PGK / E)) * E;
+    const int bq = tid / (TT / E), bc = (tid % (TT / E)) * E;
     const int64_t ga_r = ra + off + tr + ar;        // global row of A
     const int64_t gb_c = cb + off + tc + bc;        // global column of B
-    float la[8], lb[8];
+    float la[E], lb[E];
     auto load = [&](int64_t q) {
         const int64_t ga_c = ca + off + q + ak;     // global column of A
         if (ga_r < k && ga_c < k) {
             if (a_is_l && l_df) {
                 const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(Ld) + ga_r * k + ga_c);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < E / 2; ++u) {
                     const float4 v = src[u];   // two (hi, lo) pairs
                     la[2 * u] = __fadd_rn(v.x, v.y);
                     la[2 * u + 1] = __fadd_rn(v.z, v.w);
@@ -957,44 +1036,50 @@ __global__ void __launch_bounds__(256) k_pair_sgemm(const float* __restrict__ Xf
             } else if (a_is_l) {
                 const double2* src = reinterpret_cast<const double2*>(Ld + ga_r * k + ga_c);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < E / 2; ++u) {
                     const double2 v = src[u];
                     la[2 * u] = (float)v.x;
                     la[2 * u + 1] = (float)v.y;
                 }
             } else {
                 const float4* src = reinterpret_cast<const float4*>(Xf + ga_r * k + ga_c);
-                const float4 v0 = src[0], v1 = src[1];
-                la[0] = v0.x; la[1] = v0.y; la[2] = v0.z; la[3] = v0.w;
-                la[4] = v1.x; la[5] = v1.y; la[6] = v1.z; la[7] = v1.w;
+#pragma unroll
+                for (int u = 0; u < E / 4; ++u) {
+                    const float4 v = src[u];
+                    la[4 * u] = v.x; la[4 * u + 1] = v.y; la[4 * u + 2] = v.z; la[4 * u + 3] = v.w;
+                }
             }
         } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) la[u] = 0.f;
+            for (int u = 0; u < E; ++u) la[u] = 0.f;
         }
         const int64_t gb_r = rb + off + q + bq;     // global row of B
         if (gb_r < k && gb_c < k) {
             const float4* src = reinterpret_cast<const float4*>(Bsrc + gb_r * k + gb_c);
-            const float4 v0 = src[0], v1 = src[1];
-            lb[0] = v0.x; lb[1] = v0.y; lb[2] = v0.z; lb[3] = v0.w;
-            lb[4] = v1.x; lb[5] = v1.y; lb[6] = v1.z; lb[7] = v1.w;
+#pragma unroll
+            for (int u = 0; u < E / 4; ++u) {
+                const float4 v = src[u];
+                lb[4 * u] = v.x; lb[4 * u + 1] = v.y; lb[4 * u + 2] = v.z; lb[4 * u + 3] = v.w;
+            }
         } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) lb[u] = 0.f;
+            for (int u = 0; u < E; ++u) lb[u] = 0.f;
         }
     };
     auto store = [&](int buf) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) As[buf][ak + u][ar] = la[u];
-        *reinterpret_cast<float4*>(&Bs[buf][bq][bc]) = make_float4(lb[0], lb[1], lb[2], lb[3]);
-        *reinterpret_cast<float4*>(&Bs[buf][bq][bc + 4]) = make_float4(lb[4], lb[5], lb[6], lb[7]);
+        for (int u = 0; u < E; ++u) As[buf][ak + u][ar] = la[u];
+#pragma unroll
+        for (int u = 0; u < E / 4; ++u)
+            *reinterpret_cast<float4*>(&Bs[buf][bq][bc + 4 * u]) =
+                make_float4(lb[4 * u], lb[4 * u + 1], lb[4 * u + 2], lb[4 * u + 3]);
     };
-    const int ty = tid >> 4, tx = tid & 15;   // rows ty*4 + {0..3, 64..67}, columns tx*4 + {0..3, 64..67}
-    float acc[8][8];
+    const int ty = tid >> 4, tx = tid & 15;
+    float acc[RT][RT];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < RT; ++j) acc[i][j] = 0.f;
     int buf = 0;
     if (q0 < q1) {
         load(q0);
@@ -1006,29 +1091,31 @@ __global__ void __launch_bounds__(256) k_pair_sgemm(const float* __restrict__ Xf
         if (more) load(q + PGK);
 #pragma unroll
         for (int kk = 0; kk < PGK; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            float av[RT], bv[RT];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int h = 0; h < RT / 4; ++h) {
+                const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][64 * h + ty * 4]);
+                const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 * h + tx * 4]);
+                av[4 * h] = a4.x; av[4 * h + 1] = a4.y; av[4 * h + 2] = a4.z; av[4 * h + 3] = a4.w;
+                bv[4 * h] = b4.x; bv[4 * h + 1] = b4.y; bv[4 * h + 2] = b4.z; bv[4 * h + 3] = b4.w;
+            }
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = __fmaf_rn(av[i], bv[j], acc[i][j]);
+            for (int i = 0; i < RT; ++i)
+#pragma unroll
+                for (int j = 0; j < RT; ++j) acc[i][j] = __fmaf_rn(av[i], bv[j], acc[i][j]);
         }
         if (more) store(buf ^ 1);
         __syncthreads();
         buf ^= 1;
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int64_t r = tr + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    for (int i = 0; i < RT; ++i) {
+        const int64_t r = tr + 64 * (i / 4) + ty * 4 + (i % 4);
         const int64_t gr = rc + off + r;
         if (r >= s || gr >= k) continue;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int64_t c = tc + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+        for (int j = 0; j < RT; ++j) {
+            const int64_t c = tc + 64 * (j / 4) + tx * 4 + (j % 4);
             const int64_t gc = cc + off + c;
             if (c < s && gc < k) C[gr * k + gc] = alpha * acc[i][j];
         }
@@ -1247,7 +1334,8 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
         int per_sm = 0;
         IHS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_persistent, 256, 0));
         const int64_t first_tiles = (TC - 1) * TC / 2;
-        Gcoop = (int)std::min<int64_t>(ctx->sm_count, std::max<int64_t>(1, (first_tiles + 1) / 2));
+        Gcoop = (int)std::min<int64_t>((int64_t)ctx->chol_per_sm * ctx->sm_count,
+                                       std::max<int64_t>(1, (first_tiles + 1) / 2));
         Gcoop = std::min(Gcoop, per_sm * ctx->sm_count);
     }
     F->l_df = Gcoop >= 1 ? 1 : 0;
@@ -1256,10 +1344,10 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
     const float2 nu2df = make_float2(nu2_hi, (float)(nu2 - (double)nu2_hi));
     {
         // split the inner dimension so that at least two CTAs per SM work on
-        // the Gram, with at least 256 inner rows per split
+        // the Gram, with at least 64 inner rows per split
         const int64_t ntiles = T * (T + 1) / 2;
         int64_t KS = std::max<int64_t>(1, ceil_div64(2 * (int64_t)ctx->sm_count, ntiles));
-        KS = std::min<int64_t>(KS, std::max<int64_t>(1, K / 256));
+        KS = std::min<int64_t>(KS, std::max<int64_t>(1, K / 64));
         const int64_t kchunk = ceil_div64(ceil_div64(K, KS), 32) * 32;
         KS = ceil_div64(K, kchunk);
         float2* gpart = nullptr;
@@ -1272,7 +1360,8 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
                                                                         nu2, nu2df, F->l_df, Kmat, gpart);
         IHS_LAUNCH_CHECK();
         if (KS > 1) {
-            k_gram_reduce<<<(unsigned)ntiles, 256, 0, s>>>(gpart, (int)KS, ntiles, k, nu2, F->l_df, Kmat);
+            k_gram_reduce<<<dim3((unsigned)ntiles, FB * FB / 256), 256, 0, s>>>(gpart, (int)KS, ntiles, k, nu2df, F->l_df,
+                                                                              Kmat);
             IHS_LAUNCH_CHECK();
         }
     }
@@ -1343,19 +1432,23 @@ inverse:
     float* tmp = F->XT;   // scratch for L21 X11 (overwritten by X^T at the end)
     k_zero_f32<<<(unsigned)ceil_div64(k * k, 256), 256, 0, s>>>(X, k * k);
     IHS_LAUNCH_CHECK();
-    k_blockinv32<<<(unsigned)T, FB, 0, s>>>(F->L, F->l_df, k, X);
+    k_blockinv32<<<(unsigned)T, 256, 0, s>>>(F->L, F->l_df, k, X);
     IHS_LAUNCH_CHECK();
     for (int64_t sz = FB; sz < k; sz *= 2) {
         const int64_t pairs = ceil_div64(k, 2 * sz);
         const int64_t tiles = ceil_div64(sz, FB);
         dim3 grid((unsigned)tiles, (unsigned)tiles, (unsigned)pairs);
-        if (sz % PGT == 0 && k % 8 == 0) {
-            const int64_t t2 = sz / PGT;
-            dim3 g2((unsigned)t2, (unsigned)t2, (unsigned)pairs);
+        if (sz % 64 == 0 && k % 8 == 0) {
+            // 128 tiles when they fill every SM, else 64 tiles
+            const int64_t t128 = sz / 128;
+            const bool big = sz % 128 == 0 && t128 * t128 * pairs >= ctx->sm_count;
+            const int64_t tt = big ? t128 : sz / 64;
+            dim3 g2((unsigned)tt, (unsigned)tt, (unsigned)pairs);
+            auto kern = big ? k_pair_sgemm<128> : k_pair_sgemm<64>;
             // tmp21 = L21 X11 (X11 lower), X21 = -X22 tmp21 (X22 lower)
-            k_pair_sgemm<<<g2, 256, 0, s>>>(X, F->L, 1, F->l_df, k, sz, 2 * sz, sz, 0, 0, 0, X, tmp, sz, 0, 1.0f, 1);
+            kern<<<g2, 256, 0, s>>>(X, F->L, 1, F->l_df, k, sz, 2 * sz, sz, 0, 0, 0, X, tmp, sz, 0, 1.0f, 1);
             IHS_LAUNCH_CHECK();
-            k_pair_sgemm<<<g2, 256, 0, s>>>(X, nullptr, 0, 0, k, sz, 2 * sz, sz, sz, sz, 0, tmp, X, sz, 0, -1.0f, 2);
+            kern<<<g2, 256, 0, s>>>(X, nullptr, 0, 0, k, sz, 2 * sz, sz, sz, sz, 0, tmp, X, sz, 0, -1.0f, 2);
             IHS_LAUNCH_CHECK();
             continue;
         }

@@ -322,27 +322,6 @@ __global__ void k_col_scales(const unsigned* __restrict__ amax, int d, float* __
     recip[col] = __frcp_rn(sc);
 }
 
-// out[e] = colscale[e % d] * scale * sum_k part[k][e]  (fixed order, FP64)
-__global__ void k_reduce_parts_colscale(const float* __restrict__ part, int K, int64_t count, int d, double scale,
-                                        const float* __restrict__ colscale, float* __restrict__ out) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) s += (double)part[(size_t)k * count + e];
-        out[e] = (float)(s * scale * (double)colscale[e % d]);
-    }
-}
-
-__global__ void k_reduce_parts_tc(const float* __restrict__ part, int K, int64_t count, double scale,
-                                  float* __restrict__ out) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) s += (double)part[(size_t)k * count + e];
-        out[e] = (float)(s * scale);
-    }
-}
-
 }  // namespace
 
 int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed, int32_t level,
@@ -396,14 +375,6 @@ int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int
     if (fp8) IHS_TRY(tma ? launch(k_gauss_tc<1, true>, 1, crecip) : launch(k_gauss_tc<1, false>, 1, crecip));
     else IHS_TRY(tma ? launch(k_gauss_tc<0, true>, 0, nullptr) : launch(k_gauss_tc<0, false>, 0, nullptr));
     IHS_LAUNCH_CHECK();
-    const int64_t count = m * d;
-    const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
-    if (fp8) {
-        k_reduce_parts_colscale<<<rgrid, 256, 0, ctx->stream>>>(part, (int)KS, count, (int)d,
-                                                               1.0 / sqrt((double)m_scale), cscale, SA);
-    } else {
-        k_reduce_parts_tc<<<rgrid, 256, 0, ctx->stream>>>(part, (int)KS, count, 1.0 / sqrt((double)m_scale), SA);
-    }
-    IHS_LAUNCH_CHECK();
-    return IHS_OK;
+    return ihs_reduce_parts_enqueue(ctx, part, false, (int)KS, m * d, d, 1.0 / sqrt((double)m_scale),
+                                    fp8 ? cscale : nullptr, SA);
 }

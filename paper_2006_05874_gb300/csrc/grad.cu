@@ -671,31 +671,55 @@ k_grad_v3(const float* __restrict__ A, const float* __restrict__ b, const float*
     (void)ok;
 }
 
-// g[c] = fl32( sum_g (hi + lo)  + nu^2 x[c] ) over G partials in fixed order.
-__global__ void k_grad_reduce(const float2* __restrict__ part, const double* __restrict__ part_ax2, int G,
-                              int d, double nu2, const float* __restrict__ x, float* __restrict__ g,
-                              double* __restrict__ axnorm2) {
-    __shared__ double sm[8][33];
-    const int cx = threadIdx.x & 31, sy = threadIdx.x >> 5;
-    const int col = blockIdx.x * 32 + cx;
-    double s = 0.0;
-    if (col < d) {
-        for (int gi = sy; gi < G; gi += 8) {
-            const float2 v = part[(size_t)gi * d + col];
-            s += (double)v.x + (double)v.y;
+// Row group sy's share of column col of the G partials (rows sy, sy + 8, ...),
+// summed in order as a compensated pair; the loads go in batches of eight
+// ahead of the dependent additions.
+__device__ __forceinline__ Acc2 grad_column_sum(const float2* __restrict__ part, int G, int d, int col, int sy) {
+    Acc2 a{0.f, 0.f};
+    if (col >= d) return a;
+    for (int g0 = sy; g0 < G; g0 += 64) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (g0 + 8 * u < G) v[u] = part[(size_t)(g0 + 8 * u) * d + col];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (g0 + 8 * u >= G) break;
+            a.add_pair(v[u].x, v[u].y);
         }
     }
-    sm[sy][cx] = s;
+    return a;
+}
+
+// g[c] = fl32(sum_g (hi + lo) + nu^2 x[c]) over G partials in a fixed order,
+// as a compensated binary32 pair (TwoSum): FP64 runs at a small fraction of
+// the FP32 rate on this GPU.  ||A x||^2: the G FP64 partials summed by one
+// warp in a fixed order (lane strides, then a butterfly).  A non-zero *status
+// (status may be NULL) marks a gradient pass whose bounded wait gave up: the
+// results are then NaN.
+__global__ void __launch_bounds__(256) k_grad_reduce(const float2* __restrict__ part,
+                                                     const double* __restrict__ part_ax2, int G, int d, float nu2h,
+                                                     float nu2l, const float* __restrict__ x, float* __restrict__ g,
+                                                     double* __restrict__ axnorm2, const unsigned* __restrict__ status) {
+    __shared__ float2 sm[8][33];
+    const bool failed = status != nullptr && *status != 0u;
+    const int cx = threadIdx.x & 31, sy = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + cx;
+    Acc2 a = grad_column_sum(part, G, d, col, sy);
+    sm[sy][cx] = make_float2(a.hi, a.lo);
     __syncthreads();
     if (sy == 0 && col < d) {
-        double t = sm[0][cx];
-        for (int k = 1; k < 8; ++k) t += sm[k][cx];
-        g[col] = (float)(t + nu2 * (double)x[col]);
+        for (int k = 1; k < 8; ++k) a.add_pair(sm[k][cx].x, sm[k][cx].y);
+        const float2 q = df_mul(x[col], 0.f, nu2h, nu2l);
+        a.add_pair(q.x, q.y);
+        g[col] = failed ? __int_as_float(0x7fc00000) : __fadd_rn(a.hi, a.lo);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && axnorm2 != nullptr) {
+    if (blockIdx.x == 0 && sy == 1 && axnorm2 != nullptr) {
         double t = 0.0;
-        for (int gi = 0; gi < G; ++gi) t += part_ax2[gi];
-        *axnorm2 = t;
+        for (int gi = cx; gi < G; gi += 32) t += part_ax2[gi];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (cx == 0) *axnorm2 = failed ? __longlong_as_double(0x7ff8000000000000ll) : t;
     }
 }
 
@@ -913,8 +937,9 @@ int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, in
     double* part_ax2 = nullptr;
     int G = 0;
     IHS_TRY(grad_partials(ctx, A, b, n, d, x, &part, &part_ax2, &G));
-    k_grad_reduce<<<(unsigned)ceil_div64(d, 32), 256, 0, ctx->stream>>>(part, part_ax2, G, (int)d, nu * nu, x, g,
-                                                                        d_axnorm2);
+    const DfConst nu2 = df_const(nu * nu);
+    k_grad_reduce<<<(unsigned)ceil_div64(d, 32), 256, 0, ctx->stream>>>(part, part_ax2, G, (int)d, nu2.hi, nu2.lo, x,
+                                                                        g, d_axnorm2, nullptr);
     IHS_LAUNCH_CHECK();
     return IHS_OK;
 }
@@ -922,31 +947,28 @@ int ihs_grad_enqueue(ihs_ctx* ctx, const float* A, const float* b, int64_t n, in
 namespace {
 
 // gp[c] = sum of the partials of column c, gp[d] = sum of the ||A x||^2
-// partials: the same fixed-order FP64 sums as k_grad_reduce, left unrounded
-// and without nu^2 x, for a row shard whose sums other shards add to.
-__global__ void k_grad_reduce_f64(const float2* __restrict__ part, const double* __restrict__ part_ax2, int G, int d,
-                                  double* __restrict__ gp) {
-    __shared__ double sm[8][33];
+// partials: the fixed-order sums of k_grad_reduce, left unrounded (the
+// compensated pair widened to FP64) and without nu^2 x, for a row shard whose
+// sums other shards add to.
+__global__ void __launch_bounds__(256) k_grad_reduce_f64(const float2* __restrict__ part,
+                                                         const double* __restrict__ part_ax2, int G, int d,
+                                                         double* __restrict__ gp) {
+    __shared__ float2 sm[8][33];
     const int cx = threadIdx.x & 31, sy = threadIdx.x >> 5;
     const int col = blockIdx.x * 32 + cx;
-    double s = 0.0;
-    if (col < d) {
-        for (int gi = sy; gi < G; gi += 8) {
-            const float2 v = part[(size_t)gi * d + col];
-            s += (double)v.x + (double)v.y;
-        }
-    }
-    sm[sy][cx] = s;
+    Acc2 a = grad_column_sum(part, G, d, col, sy);
+    sm[sy][cx] = make_float2(a.hi, a.lo);
     __syncthreads();
     if (sy == 0 && col < d) {
-        double t = sm[0][cx];
-        for (int k = 1; k < 8; ++k) t += sm[k][cx];
-        gp[col] = t;
+        for (int k = 1; k < 8; ++k) a.add_pair(sm[k][cx].x, sm[k][cx].y);
+        gp[col] = (double)a.hi + (double)a.lo;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && sy == 1) {
         double t = 0.0;
-        for (int gi = 0; gi < G; ++gi) t += part_ax2[gi];
-        gp[d] = t;
+        for (int gi = cx; gi < G; gi += 32) t += part_ax2[gi];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (cx == 0) gp[d] = t;
     }
 }
 
@@ -1077,36 +1099,6 @@ int noalloc_setup(cudaStream_t stream, NoallocDevice** out) {
     return IHS_OK;
 }
 
-// Fixed-order FP64 reduction of the partials, as k_grad_reduce, except that a
-// gradient pass whose bounded wait gave up (status word non-zero) yields NaN.
-__global__ void k_grad_reduce_noalloc(const float2* __restrict__ part, const double* __restrict__ part_ax2, int G,
-                                      int d, double nu2, const float* __restrict__ x, float* __restrict__ g,
-                                      double* __restrict__ axnorm2, const unsigned* __restrict__ status) {
-    __shared__ double sm[8][33];
-    const bool failed = *status != 0u;
-    const int cx = threadIdx.x & 31, sy = threadIdx.x >> 5;
-    const int col = blockIdx.x * 32 + cx;
-    double s = 0.0;
-    if (col < d) {
-        for (int gi = sy; gi < G; gi += 8) {
-            const float2 v = part[(size_t)gi * d + col];
-            s += (double)v.x + (double)v.y;
-        }
-    }
-    sm[sy][cx] = s;
-    __syncthreads();
-    if (sy == 0 && col < d) {
-        double t = sm[0][cx];
-        for (int k = 1; k < 8; ++k) t += sm[k][cx];
-        g[col] = failed ? __int_as_float(0x7fc00000) : (float)(t + nu2 * (double)x[col]);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && axnorm2 != nullptr) {
-        double t = 0.0;
-        for (int gi = 0; gi < G; ++gi) t += part_ax2[gi];
-        *axnorm2 = failed ? __longlong_as_double(0x7ff8000000000000ll) : t;
-    }
-}
-
 }  // namespace
 
 extern "C" int ihs_grad_noalloc(void* stream_v, const float* A, const float* b, int64_t n, int64_t d, double nu,
@@ -1126,8 +1118,10 @@ extern "C" int ihs_grad_noalloc(void* stream_v, const float* A, const float* b, 
     const GradTarget tg{stream, std::min(nd->sm_count, IHS_NOALLOC_MAX_SMS), status};
     int G = 0;
     IHS_TRY(grad_pass_fast(tg, A, b, x, n, d, part, part_ax2, &G));
-    k_grad_reduce_noalloc<<<(unsigned)ceil_div64(d, 32), 256, 0, stream>>>(part, part_ax2, G, (int)d, nu * nu, x, g,
-                                                                          axnorm2, status);
+    // the reduction of the regular entry point, NaN where the pass gave up
+    const DfConst nu2 = df_const(nu * nu);
+    k_grad_reduce<<<(unsigned)ceil_div64(d, 32), 256, 0, stream>>>(part, part_ax2, G, (int)d, nu2.hi, nu2.lo, x, g,
+                                                                   axnorm2, status);
     IHS_LAUNCH_CHECK();
     return IHS_OK;
 }

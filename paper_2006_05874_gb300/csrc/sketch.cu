@@ -467,27 +467,75 @@ int launch_r32(ihs_ctx* ctx, const CUtensorMap& amap, int d, int64_t mc, int64_t
     return IHS_OK;
 }
 
-// out[e] = scale * sum_k part[k][e] in a fixed order (FP64).
-__global__ void k_reduce_parts(const float* __restrict__ part, int K, int64_t count, double scale,
-                               float* __restrict__ out) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) s += (double)part[(size_t)k * count + e];
-        out[e] = (float)(s * scale);
-    }
-}
-
-__global__ void k_reduce_parts2(const float2* __restrict__ part, int K, int64_t count, double scale,
-                                float* __restrict__ out) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) {
-            const float2 v = part[(size_t)k * count + e];
-            s += (double)v.x + (double)v.y;
+// out[e] = fl32(scale * colscale[e % d] * sum_k part_k[e]).  The K partials
+// are summed in a fixed order into a compensated binary32 pair (TwoSum), then
+// scaled in double-float arithmetic and rounded once: FP64 runs at a small
+// fraction of the FP32 rate on this GPU, and a double accumulator made the
+// reduction FP64-bound (about 1 TB/s) instead of HBM-bound.  PAIRS: each
+// element is a (hi, lo) float2.  16-byte streaming loads when every partial
+// starts on a 16-byte boundary (count a multiple of the elements per load).
+template <bool PAIRS>
+__global__ void __launch_bounds__(256)
+k_reduce_parts(const float* __restrict__ part, int K, int64_t count, int d, float sh, float sl,
+               const float* __restrict__ colscale, float* __restrict__ out) {
+    constexpr int EV = PAIRS ? 2 : 4;   // elements per float4
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    auto finish = [&](const Acc2& a, int64_t e) {
+        float2 v = df_mul(a.hi, a.lo, sh, sl);
+        if (colscale != nullptr) v = df_mul(v.x, v.y, colscale[e % d], 0.f);
+        out[e] = v.x;
+    };
+    // the partials in batches of eight independent loads ahead of the
+    // dependent compensated additions
+    constexpr int BK = 8;
+    if (count % EV == 0) {
+        const int64_t nv = count / EV;   // float4 per partial
+        const float4* src = reinterpret_cast<const float4*>(part);
+        for (int64_t v = t0; v < nv; v += stride) {
+            Acc2 a[EV] = {};
+            for (int k0 = 0; k0 < K; k0 += BK) {
+                float4 q[BK];
+#pragma unroll
+                for (int u = 0; u < BK; ++u)
+                    if (k0 + u < K) q[u] = __ldcs(src + (size_t)(k0 + u) * nv + v);
+#pragma unroll
+                for (int u = 0; u < BK; ++u) {
+                    if (k0 + u >= K) break;
+                    if constexpr (PAIRS) {
+                        a[0].add_pair(q[u].x, q[u].y);
+                        a[1].add_pair(q[u].z, q[u].w);
+                    } else {
+                        a[0].add(q[u].x);
+                        a[1].add(q[u].y);
+                        a[2].add(q[u].z);
+                        a[3].add(q[u].w);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < EV; ++i) finish(a[i], v * EV + i);
         }
-        out[e] = (float)(s * scale);
+    } else {
+        for (int64_t e = t0; e < count; e += stride) {
+            Acc2 a{0.f, 0.f};
+            for (int k0 = 0; k0 < K; k0 += BK) {
+                float2 q[BK];
+#pragma unroll
+                for (int u = 0; u < BK; ++u) {
+                    if (k0 + u >= K) continue;
+                    if constexpr (PAIRS) q[u] = reinterpret_cast<const float2*>(part)[(size_t)(k0 + u) * count + e];
+                    else q[u] = make_float2(part[(size_t)(k0 + u) * count + e], 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < BK; ++u) {
+                    if (k0 + u >= K) break;
+                    if constexpr (PAIRS) a.add_pair(q[u].x, q[u].y);
+                    else a.add(q[u].x);
+                }
+            }
+            finish(a, e);
+        }
     }
 }
 
@@ -640,11 +688,7 @@ int srht_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, 
                                                               (uint32_t)(seed >> 32), acc_in_smem, grow0, part);
         IHS_LAUNCH_CHECK();
     }
-    const int64_t count = m * d;
-    const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
-    k_reduce_parts<<<rgrid, 256, 0, ctx->stream>>>(part, (int)PG, count, 1.0 / sqrt((double)m), SA);
-    IHS_LAUNCH_CHECK();
-    return IHS_OK;
+    return ihs_reduce_parts_enqueue(ctx, part, false, (int)PG, m * d, d, 1.0 / sqrt((double)m), nullptr, SA);
 }
 
 // Rows [zrow0, zrow0 + m) of the Gaussian sketch of size m_scale (zrow0 % 4 == 0).
@@ -665,14 +709,27 @@ int gauss_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m,
                                                      (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)(zrow0 >> 2),
                                                      (uint32_t)grow0, part);
     IHS_LAUNCH_CHECK();
-    const int64_t count = m * d;
-    const unsigned rgrid = (unsigned)std::min<int64_t>(ceil_div64(count, 256), 8 * (int64_t)ctx->sm_count);
-    k_reduce_parts2<<<rgrid, 256, 0, ctx->stream>>>(part, (int)KS, count, 1.0 / sqrt((double)m_scale), SA);
-    IHS_LAUNCH_CHECK();
-    return IHS_OK;
+    return ihs_reduce_parts_enqueue(ctx, reinterpret_cast<const float*>(part), true, (int)KS, m * d, d,
+                                    1.0 / sqrt((double)m_scale), nullptr, SA);
 }
 
 }  // namespace
+
+int ihs_reduce_parts_enqueue(ihs_ctx* ctx, const float* part, bool pairs, int K, int64_t count, int64_t d,
+                             double scale, const float* colscale, float* out) {
+    if (K < 1 || count < 1 || d < 1) return IHS_EINVAL;
+    const int ev = pairs ? 2 : 4;
+    const int64_t work = count % ev == 0 ? count / ev : count;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div64(work, 256), 8 * (int64_t)ctx->sm_count);
+    const DfConst s = df_const(scale);
+    if (pairs) {
+        k_reduce_parts<true><<<grid, 256, 0, ctx->stream>>>(part, K, count, (int)d, s.hi, s.lo, colscale, out);
+    } else {
+        k_reduce_parts<false><<<grid, 256, 0, ctx->stream>>>(part, K, count, (int)d, s.hi, s.lo, colscale, out);
+    }
+    IHS_LAUNCH_CHECK();
+    return IHS_OK;
+}
 
 int ihs_gauss_fp32_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t m, uint64_t seed,
                            int32_t level, float* SA) {

@@ -51,45 +51,54 @@ Params make_params(int kind, double rho, double eta) {
     return p;
 }
 
-// xc = x - mu gt + beta (x - xp); block partials of ||xc||^2 (FP64).
-__global__ void k_candidate(const float* __restrict__ x, const float* __restrict__ gt,
-                            const float* __restrict__ xp, int64_t d, float mu, float beta, float* __restrict__ xc,
-                            double* __restrict__ part) {
-    __shared__ double sm[256];
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// One block of kSolveThreads threads walks a d-vector (d is small next to the
+// n x d passes) and sums one double per thread in a fixed order: a butterfly
+// in each warp, then the warp sums by warp 0; the result is valid in warp 0.
+// (A block of partials folded by one serial thread, and a second launch to
+// fold the blocks, cost more than the vector work.)
+constexpr int kSolveThreads = 1024;
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double ws[kSolveThreads / 32];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = ws[lane];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    }
+    return t;
+}
+
+// xc = x - mu gt + beta (x - xp); *xx = ||xc||^2 (FP64).
+__global__ void __launch_bounds__(kSolveThreads) k_candidate(const float* __restrict__ x, const float* __restrict__ gt,
+                                                             const float* __restrict__ xp, int64_t d, float mu,
+                                                             float beta, float* __restrict__ xc,
+                                                             double* __restrict__ xx) {
     double sq = 0.0;
-    if (i < d) {
+    for (int64_t i = threadIdx.x; i < d; i += kSolveThreads) {
         float v = __fmaf_rn(-mu, gt[i], x[i]);
         if (beta != 0.f) v = __fmaf_rn(beta, __fsub_rn(x[i], xp[i]), v);
         xc[i] = v;
-        sq = (double)v * (double)v;
+        sq += (double)v * (double)v;
     }
-    sm[threadIdx.x] = sq;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < 256; ++k) s += sm[k];
-        part[blockIdx.x] = s;
-    }
+    sq = block_sum(sq);
+    if (threadIdx.x == 0) *xx = sq;
 }
 
-__global__ void k_sumsq(const float* __restrict__ x, int64_t d, double* __restrict__ part) {
-    __shared__ double sm[256];
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const double v = i < d ? (double)x[i] : 0.0;
-    sm[threadIdx.x] = v * v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < 256; ++k) s += sm[k];
-        part[blockIdx.x] = s;
+// *xx = ||x||^2 (FP64).
+__global__ void __launch_bounds__(kSolveThreads) k_sumsq(const float* __restrict__ x, int64_t d,
+                                                         double* __restrict__ xx) {
+    double sq = 0.0;
+    for (int64_t i = threadIdx.x; i < d; i += kSolveThreads) {
+        const double v = (double)x[i];
+        sq += v * v;
     }
-}
-
-__global__ void k_fold(const double* __restrict__ part, int count, double* __restrict__ out) {
-    double s = 0.0;
-    for (int k = 0; k < count; ++k) s += part[k];
-    *out = s;
+    sq = block_sum(sq);
+    if (threadIdx.x == 0) *xx = sq;
 }
 
 // AT = A^T for row-major A (rows x cols), 32 x 32 tiles through shared memory.
@@ -202,15 +211,13 @@ __global__ void k_dual_reduce(const float2* __restrict__ part, int G, int cols, 
 }
 
 // xc = (x + xlo) - mu gt + beta ((x + xlo) - (xp + xplo)) as a double-float pair;
-// block partials of ||xc||^2 (FP64).
-__global__ void k_candidate_df(const float* __restrict__ x, const float* __restrict__ xlo,
-                               const float* __restrict__ gt, const float* __restrict__ xp,
-                               const float* __restrict__ xplo, int64_t d, float mu, float beta,
-                               float* __restrict__ xc, float* __restrict__ xclo, double* __restrict__ part) {
-    __shared__ double sm[256];
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// *xx = ||xc||^2 (FP64).
+__global__ void __launch_bounds__(kSolveThreads)
+k_candidate_df(const float* __restrict__ x, const float* __restrict__ xlo, const float* __restrict__ gt,
+               const float* __restrict__ xp, const float* __restrict__ xplo, int64_t d, float mu, float beta,
+               float* __restrict__ xc, float* __restrict__ xclo, double* __restrict__ xx) {
     double sq = 0.0;
-    if (i < d) {
+    for (int64_t i = threadIdx.x; i < d; i += kSolveThreads) {
         float p, e, s, es;
         two_prod(-mu, gt[i], p, e);                 // -mu gt exactly
         two_sum(x[i], p, s, es);
@@ -228,15 +235,11 @@ __global__ void k_candidate_df(const float* __restrict__ x, const float* __restr
         const float2 v = df_two_sum_norm(s, lo);
         xc[i] = v.x;
         xclo[i] = v.y;
-        sq = ((double)v.x + (double)v.y) * ((double)v.x + (double)v.y);
+        const double w = (double)v.x + (double)v.y;
+        sq += w * w;
     }
-    sm[threadIdx.x] = sq;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < 256; ++k) t += sm[k];
-        part[blockIdx.x] = t;
-    }
+    sq = block_sum(sq);
+    if (threadIdx.x == 0) *xx = sq;
 }
 
 // x = M (z + zlo) for row-major M (rows x cols): one warp per row, Dot2 on z,
@@ -403,10 +406,7 @@ int evaluate(Solver& S, int ix, int ig, int igt, double* r, double* ax2, double*
     IHS_CUDA_TRY(cudaEventRecord(ctx->ev[0], ctx->stream));
     IHS_TRY(ihs_apply_enqueue(ctx, S.F, S.vec[ig], S.vec[igt], S.dsc + 0));
     if (need_xx) {
-        const unsigned blocks = (unsigned)ceil_div64(S.d, 256);
-        k_sumsq<<<blocks, 256, 0, ctx->stream>>>(S.vec[ix], S.d, S.dsc + 8);
-        IHS_LAUNCH_CHECK();
-        k_fold<<<1, 1, 0, ctx->stream>>>(S.dsc + 8, (int)blocks, S.dsc + 2);
+        k_sumsq<<<1, kSolveThreads, 0, ctx->stream>>>(S.vec[ix], S.d, S.dsc + 2);
         IHS_LAUNCH_CHECK();
     }
     IHS_CUDA_TRY(cudaEventRecord(ctx->ev[3], ctx->stream));
@@ -439,16 +439,14 @@ int reapply(Solver& S, int ig, int igt, double* r) {
 
 int make_candidate(Solver& S, int ix, int igt, int ixp, double mu, double beta, int ixc, double* xx) {
     ihs_ctx* ctx = S.ctx;
-    const unsigned blocks = (unsigned)ceil_div64(S.d, 256);
     if (S.bsub) {
-        k_candidate_df<<<blocks, 256, 0, ctx->stream>>>(S.vec[ix], S.vlo[ix], S.vec[igt], S.vec[ixp], S.vlo[ixp], S.d,
-                                                       (float)mu, (float)beta, S.vec[ixc], S.vlo[ixc], S.dsc + 8);
+        k_candidate_df<<<1, kSolveThreads, 0, ctx->stream>>>(S.vec[ix], S.vlo[ix], S.vec[igt], S.vec[ixp], S.vlo[ixp],
+                                                            S.d, (float)mu, (float)beta, S.vec[ixc], S.vlo[ixc],
+                                                            S.dsc + 2);
     } else {
-        k_candidate<<<blocks, 256, 0, ctx->stream>>>(S.vec[ix], S.vec[igt], S.vec[ixp], S.d, (float)mu, (float)beta,
-                                                    S.vec[ixc], S.dsc + 8);
+        k_candidate<<<1, kSolveThreads, 0, ctx->stream>>>(S.vec[ix], S.vec[igt], S.vec[ixp], S.d, (float)mu,
+                                                         (float)beta, S.vec[ixc], S.dsc + 2);
     }
-    IHS_LAUNCH_CHECK();
-    k_fold<<<1, 1, 0, ctx->stream>>>(S.dsc + 8, (int)blocks, S.dsc + 2);
     IHS_LAUNCH_CHECK();
     (void)xx;
     return IHS_OK;
