@@ -371,19 +371,31 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_resolve(int64_t n_pad, int6
             if (match) atomicAdd(&S.hist[(k >> shift) & 255u], 1u);
         }
         __syncthreads();
-        if (tid == 0) {
-            unsigned long long acc = 0;
-            int b = 255;
-            for (int h = 0; h < 256; ++h) {
-                if (acc + S.hist[h] >= need) {
-                    b = h;
-                    break;
-                }
-                acc += S.hist[h];
+        // the first digit b whose inclusive prefix count reaches `need`
+        // (digit 255 with the whole count when none does): a shuffle scan in
+        // each of eight warps over the 256 bins, then one test per bin
+        unsigned hv = 0, incl = 0;
+        if (tid < 256) {
+            hv = S.hist[tid];
+            incl = hv;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
+                if ((tid & 31) >= off) incl += y;
             }
-            S.bcast[1] = (P << 8) | (unsigned long long)b;
-            S.bcast[2] = need - acc;
-            S.bcast[3] = (unsigned long long)S.hist[b];
+            if ((tid & 31) == 31) S.wsum[tid >> 5] = incl;
+        }
+        __syncthreads();
+        if (tid < 256) {
+            unsigned long long inc = incl;
+            for (int w = 0; w < (tid >> 5); ++w) inc += S.wsum[w];
+            const unsigned long long exc = inc - hv;
+            if ((exc < need && inc >= need) || (tid == 255 && inc < need)) {
+                const unsigned long long acc = inc >= need ? exc : inc;
+                S.bcast[1] = (P << 8) | (unsigned long long)tid;
+                S.bcast[2] = need - acc;
+                S.bcast[3] = (unsigned long long)hv;
+            }
         }
         __syncthreads();
         P = S.bcast[1];
