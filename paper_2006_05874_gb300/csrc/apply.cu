@@ -34,6 +34,7 @@ constexpr int kApplyWarps = kApplyThreads / 32;
 constexpr int kSlots = 8;                      // 16-byte loads per lane per item
 constexpr int kSegFloats = 32 * 4 * kSlots;    // 1024 floats per segment
 constexpr int kPrefetch = 2;                   // items loaded before a barrier
+constexpr int kLocalK = 128;                   // Woodbury k up to which each CTA forms X^T X v itself
 
 __device__ __forceinline__ float2 df_norm(float hi, float lo) {   // |hi| >= |lo|
     const float s = __fadd_rn(hi, lo);
@@ -222,6 +223,18 @@ __device__ __forceinline__ void run_stage(const Mat& M, int64_t gw, int64_t W, c
     }
 }
 
+// y = M v for a matrix of at most kSegFloats columns, every row in this CTA
+// (warp w takes rows w, w + 16, ...): the same per-row arithmetic as a stage's
+// item, so y[i] equals the item's single segment sum bit for bit.  v and y
+// may be shared-memory vectors.
+__device__ __forceinline__ void local_matvec(const Mat& M, const float2* v, float2* y) {
+    float4 buf[kSlots];
+    for (int64_t i = threadIdx.x >> 5; i < M.rows; i += kApplyWarps) {
+        load_item(M, i, buf);
+        dot_item(M, i, buf, nullptr, v, y);
+    }
+}
+
 // Entry i of a product whose segment sums are in Y (rows entries per
 // segment): the sum over segments [s0, s1) in increasing order.
 __device__ __forceinline__ float2 sum_parts(const float2* Y, int64_t rows, int64_t i, int64_t s0, int64_t s1) {
@@ -317,7 +330,59 @@ __global__ void __launch_bounds__(kApplyThreads, 1) k_apply_fused(const ApplyArg
     const int64_t PSAT = (m + kSegFloats - 1) / kSegFloats;         // of SA^T rows
     Pref P;
     int nb = 0;
-    if (a.woodbury) {
+    if (a.woodbury && k <= kLocalK) {
+        // Small k: every CTA forms u0 = X^T X t and the refinement X^T X res
+        // itself (the vectors are identical to the distributed stages'), four
+        // grid barriers instead of eight.
+        __shared__ float2 loc_u0[kLocalK], loc_a[kLocalK], loc_b[kLocalK];
+        // 1: t = SA g
+        prefetch(mSA, gw, W, P);
+        for (int64_t e = tid; e < d; e += kApplyThreads) vf[e] = __ldg(a.g + e);
+        __syncthreads();
+        run_stage(mSA, gw, W, P, vf, nullptr, a.Y0);
+        prefetch(mSAT, gw, W, P);
+        IHS_APPLY_SYNC();
+        // u0 = X^T (X t)
+        for (int64_t i = tid; i < m; i += kApplyThreads) vd[i] = sum_parts(a.Y0, m, i, 0, PSA);
+        __syncthreads();
+        local_matvec(mX, vd, loc_a);
+        __syncthreads();
+        local_matvec(mXT, loc_a, loc_u0);
+        __syncthreads();
+        // 4: w = SA^T u0
+        run_stage(mSAT, gw, W, P, nullptr, loc_u0, a.Y3);
+        prefetch(mSA, gw, W, P);
+        IHS_APPLY_SYNC();
+        // 5: w2 = SA w
+        for (int64_t c = tid; c < d; c += kApplyThreads) vd[c] = sum_parts(a.Y3, d, c, 0, PSAT);
+        __syncthreads();
+        run_stage(mSA, gw, W, P, nullptr, vd, a.Y1);
+        prefetch(mSAT, gw, W, P);
+        IHS_APPLY_SYNC();
+        // res = t - (nu^2 u0 + w2), u1 = u0 + X^T (X res)
+        for (int64_t i = tid; i < k; i += kApplyThreads)
+            loc_a[i] = df_residual(sum_parts(a.Y0, m, i, 0, PSA), loc_u0[i], a.nu2, sum_parts(a.Y1, m, i, 0, PSA));
+        __syncthreads();
+        local_matvec(mX, loc_a, loc_b);
+        __syncthreads();
+        local_matvec(mXT, loc_b, loc_a);
+        __syncthreads();
+        for (int64_t i = tid; i < k; i += kApplyThreads) loc_b[i] = df_add(loc_u0[i], loc_a[i]);
+        __syncthreads();
+        // 8: w = SA^T u1
+        run_stage(mSAT, gw, W, P, nullptr, loc_b, a.Y3);
+        IHS_APPLY_SYNC();
+        // gt = (g - w) / nu^2 and the decrement
+        double prod = 0.0;
+        for (int64_t c = (int64_t)blockIdx.x * kApplyThreads + tid; c < d; c += (int64_t)gridDim.x * kApplyThreads) {
+            const float2 w = sum_parts(a.Y3, d, c, 0, PSAT);
+            const double gc = (double)__ldg(a.g + c);
+            const double v = (gc - ((double)w.x + (double)w.y)) * a.inv_nu2;
+            a.gt[c] = (float)v;
+            prod += gc * v;
+        }
+        finish_decrement(a, prod);
+    } else if (a.woodbury) {
         // 1: t = SA g
         prefetch(mSA, gw, W, P);
         for (int64_t e = tid; e < d; e += kApplyThreads) vf[e] = __ldg(a.g + e);
@@ -431,6 +496,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) k_apply_fused(const ApplyArg
 }
 
 // Barriers per launch of k_apply_fused.
+constexpr int kBarriersWoodburyLocal = 4;
 constexpr int kBarriersWoodbury = 8;
 constexpr int kBarriersDirect = 6;
 
@@ -519,6 +585,7 @@ int ihs_apply_fused(ihs_ctx* ctx, const ihs_factor_t* F, const float* g, float* 
     IHS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_apply_fused, dim3((unsigned)G), dim3(kApplyThreads),
                                              args, smem, ctx->stream));
     ihs_count_launch();
-    ctx->apply_epoch += (uint64_t)(F->woodbury ? kBarriersWoodbury : kBarriersDirect) * (uint64_t)G;
+    const int nbar = F->woodbury ? (F->k <= kLocalK ? kBarriersWoodburyLocal : kBarriersWoodbury) : kBarriersDirect;
+    ctx->apply_epoch += (uint64_t)nbar * (uint64_t)G;
     return IHS_OK;
 }

@@ -39,85 +39,137 @@ constexpr int FB = 64;   // block size of the FP64 Cholesky and of the inverse
 // Split-K: blockIdx.y takes rows [y * kchunk, (y + 1) * kchunk) of the inner
 // dimension; with gridDim.y > 1 the (hi, lo) pairs go to `part` (one 64 x 64
 // tile of float2 per (split, tile)) for k_gram_reduce, else straight to G.
-__global__ void __launch_bounds__(256) k_gram_c32(const float* __restrict__ SA, int64_t d, int woodbury,
+// Thread (ty, tx) holds rows 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3 of the
+// tile as packed FP32x2 pairs of adjacent columns, so that every multiply,
+// FMA and TwoSum step does two entries' work in one instruction (the same
+// operations per entry as the scalar form, hence the same K bit for bit).
+// The inner dimension goes in chunks of 32 rows through two shared-memory
+// buffers, the next chunk loaded into registers while the current one is
+// used.
+__global__ void __launch_bounds__(256, 2) k_gram_c32(const float* __restrict__ SA, int64_t d, int woodbury,
                                                   int64_t kdim, int64_t K, int64_t kchunk, double nu2,
                                                   float2 nu2df, int out_df, double* __restrict__ G,
                                                   float2* __restrict__ part) {
-    __shared__ float xa[32][FB + 4];
-    __shared__ float xb[32][FB + 4];
+    __shared__ __align__(16) float xa[2][32][FB + 4];
+    __shared__ __align__(16) float xb[2][32][FB + 4];
     const int64_t t = blockIdx.x;
     int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
     while (I * (I + 1) / 2 > t) --I;
     while ((I + 1) * (I + 2) / 2 <= t) ++I;
     const int64_t J = t - I * (I + 1) / 2;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    float hi[4][4], lo[4][4];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
+    const int64_t kend = min(K, kbeg + kchunk);
+    // staging: 8 entries of each operand per thread and chunk
+    float la[8], lb[8];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int e = tid + 256 * i;
+            int rr, kk;
+            if (woodbury) {
+                rr = e / 32;
+                kk = e % 32;
+            } else {
+                kk = e / FB;
+                rr = e % FB;
+            }
+            const int64_t ra = I * FB + rr, rb = J * FB + rr, kq = k0 + kk;
+            const bool kin = kq < kend;
+            la[i] = (ra < kdim && kin) ? (woodbury ? SA[ra * d + kq] : SA[kq * d + ra]) : 0.f;
+            lb[i] = (rb < kdim && kin) ? (woodbury ? SA[rb * d + kq] : SA[kq * d + rb]) : 0.f;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int e = tid + 256 * i;
+            const int rr = woodbury ? e / 32 : e % FB, kk = woodbury ? e % 32 : e / FB;
+            xa[buf][kk][rr] = la[i];
+            xb[buf][kk][rr] = lb[i];
+        }
+    };
+    f2 hi[4][2], lo[4][2];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = 0.f;
-    const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
-    const int64_t kend = min(K, kbeg + kchunk);
+        for (int p = 0; p < 2; ++p) hi[a][p].v = lo[a][p].v = 0ull;
+    int buf = 0;
+    if (kbeg < kend) {
+        load(kbeg);
+        store(0);
+    }
+    __syncthreads();
     for (int64_t k0 = kbeg; k0 < kend; k0 += 32) {
-        __syncthreads();
-        if (woodbury) {
-            for (int e = threadIdx.x; e < 32 * FB; e += 256) {
-                const int rr = e / 32, kk = e % 32;
-                const int64_t ra = I * FB + rr, rb = J * FB + rr, k = k0 + kk;
-                xa[kk][rr] = (ra < kdim && k < kend) ? SA[ra * d + k] : 0.f;
-                xb[kk][rr] = (rb < kdim && k < kend) ? SA[rb * d + k] : 0.f;
-            }
-        } else {
-            for (int e = threadIdx.x; e < 32 * FB; e += 256) {
-                const int kk = e / FB, rr = e % FB;
-                const int64_t ra = I * FB + rr, rb = J * FB + rr, k = k0 + kk;
-                xa[kk][rr] = (ra < kdim && k < kend) ? SA[k * d + ra] : 0.f;
-                xb[kk][rr] = (rb < kdim && k < kend) ? SA[k * d + rb] : 0.f;
-            }
-        }
-        __syncthreads();
+        const bool more = k0 + 32 < kend;
+        if (more) load(k0 + 32);
 #pragma unroll
         for (int kc = 0; kc < 32; kc += 4) {
-            float av[4][4], bv[4][4];
+            f2 c4[4][2];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < 4; ++q) {
+                const float4 a4 = *reinterpret_cast<const float4*>(&xa[buf][kc + q][ty * 4]);
+                const float4 b4 = *reinterpret_cast<const float4*>(&xb[buf][kc + q][tx * 4]);
+                const f2 b01 = f2_pack(b4.x, b4.y), b23 = f2_pack(b4.z, b4.w);
+                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    av[q][a] = xa[kc + q][ty + 16 * a];
-                    bv[q][a] = xb[kc + q][tx + 16 * a];
+                    const f2 aa = f2_pack(av[a], av[a]);
+                    if (q == 0) {
+                        c4[a][0] = f2_mul(aa, b01);
+                        c4[a][1] = f2_mul(aa, b23);
+                    } else {
+                        c4[a][0] = f2_fma(aa, b01, c4[a][0]);
+                        c4[a][1] = f2_fma(aa, b23, c4[a][1]);
+                    }
                 }
+            }
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    float c4 = __fmul_rn(av[0][a], bv[0][b]);
-                    c4 = __fmaf_rn(av[1][a], bv[1][b], c4);
-                    c4 = __fmaf_rn(av[2][a], bv[2][b], c4);
-                    c4 = __fmaf_rn(av[3][a], bv[3][b], c4);
-                    float s, e;
-                    two_sum(hi[a][b], c4, s, e);
-                    hi[a][b] = s;
-                    lo[a][b] = __fadd_rn(lo[a][b], e);
+                for (int p = 0; p < 2; ++p) {
+                    Acc2x2 acc{hi[a][p], lo[a][p]};
+                    acc.add(c4[a][p]);
+                    hi[a][p] = acc.hi;
+                    lo[a][p] = acc.lo;
                 }
         }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
     }
+    // entry (a, b) of this thread: row 4 ty + a, column 4 tx + b
+    auto entry = [&](int a, int b, float& h, float& l) {
+        float h0, h1, l0, l1;
+        f2_unpack(hi[a][b >> 1], h0, h1);
+        f2_unpack(lo[a][b >> 1], l0, l1);
+        h = (b & 1) ? h1 : h0;
+        l = (b & 1) ? l1 : l0;
+    };
     if (gridDim.y > 1) {
         float2* pt = part + ((size_t)blockIdx.y * gridDim.x + t) * FB * FB;
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) pt[(ty + 16 * a) * FB + tx + 16 * b] = make_float2(hi[a][b], lo[a][b]);
+            for (int b = 0; b < 4; ++b) {
+                float h, l;
+                entry(a, b, h, l);
+                pt[(ty * 4 + a) * FB + tx * 4 + b] = make_float2(h, l);
+            }
         return;
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int64_t r = I * FB + ty + 16 * a, c = J * FB + tx + 16 * b;
+            const int64_t r = I * FB + ty * 4 + a, c = J * FB + tx * 4 + b;
             if (r < kdim && c < kdim && c <= r) {
+                float h, l;
+                entry(a, b, h, l);
                 if (out_df) {   // double-float pairs, the FP32 pipes only
                     float s, e;
-                    two_sum(hi[a][b], lo[a][b], s, e);
+                    two_sum(h, l, s, e);
                     float2 v = make_float2(s, e);
                     if (r == c) {
                         float s2, e2;
@@ -128,7 +180,7 @@ __global__ void __launch_bounds__(256) k_gram_c32(const float* __restrict__ SA, 
                     }
                     reinterpret_cast<float2*>(G)[r * kdim + c] = v;
                 } else {
-                    G[r * kdim + c] = (double)hi[a][b] + (double)lo[a][b] + (r == c ? nu2 : 0.0);
+                    G[r * kdim + c] = (double)h + (double)l + (r == c ? nu2 : 0.0);
                 }
             }
         }
@@ -757,6 +809,10 @@ __global__ void __launch_bounds__(256) k_chol_persistent(float2* __restrict__ Km
             bool loaded = false;
             for (int64_t it = cta; it < items; it += G) {
                 const int64_t r0 = j0 + nb + it * 16;
+                // the item's rows of K first, so that their loads overlap those of L_jj
+                const int64_t ra = r0 + wq, rb = r0 + 8 + wq;
+                float2 ka = (ra < k && lane < nb) ? __ldcg(Kmat + ra * k + j0 + lane) : make_float2(0.f, 0.f);
+                float2 kb = (rb < k && lane < nb) ? __ldcg(Kmat + rb * k + j0 + lane) : make_float2(0.f, 0.f);
                 if (!loaded) {
                     // L_jj and 1 / L_cc as double-float pairs, once per step
                     for (int e = tid; e < CB * CB; e += 256) {
@@ -768,9 +824,6 @@ __global__ void __launch_bounds__(256) k_chol_persistent(float2* __restrict__ Km
                     loaded = true;
                 }
                 // substitution in double-float (FP32 latencies on the dependent chains)
-                const int64_t ra = r0 + wq, rb = r0 + 8 + wq;
-                float2 ka = (ra < k && lane < nb) ? __ldcg(Kmat + ra * k + j0 + lane) : make_float2(0.f, 0.f);
-                float2 kb = (rb < k && lane < nb) ? __ldcg(Kmat + rb * k + j0 + lane) : make_float2(0.f, 0.f);
                 float2 xa = make_float2(0.f, 0.f), xb = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < CB; ++c) {
@@ -803,6 +856,13 @@ __global__ void __launch_bounds__(256) k_chol_persistent(float2* __restrict__ Km
             const int64_t items = ceil_div64(k - j1, 16);
             for (int64_t it = cta; it < items; it += G) {
                 const int64_t r0 = j1 + it * 16;
+                // the two K entries this thread updates, loaded ahead of the operands
+                const int tx = tid % CB, ty = tid / CB;
+                const int64_t c = j1 + tx;
+                const int64_t ra = r0 + ty, rb = r0 + 8 + ty;
+                const bool wa = ra < k && tx < ncol && c <= ra, wb = rb < k && tx < ncol && c <= rb;
+                const float2 ka = wa ? __ldcg(Kmat + ra * k + c) : make_float2(0.f, 0.f);
+                const float2 kb = wb ? __ldcg(Kmat + rb * k + c) : make_float2(0.f, 0.f);
                 __syncthreads();
                 for (int e = tid; e < CB * CB; e += 256) {
                     const int c = e / CB, q = e % CB;
@@ -813,7 +873,6 @@ __global__ void __launch_bounds__(256) k_chol_persistent(float2* __restrict__ Km
                     fa[r][q] = r0 + r < k ? __ldcg(Pdf + (r0 + r) * CB + q) : make_float2(0.f, 0.f);
                 }
                 __syncthreads();
-                const int tx = tid % CB, ty = tid / CB;
                 Acc2 a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f};
 #pragma unroll
                 for (int q = 0; q < CB; q += 2) {
@@ -823,14 +882,8 @@ __global__ void __launch_bounds__(256) k_chol_persistent(float2* __restrict__ Km
                     df_fma_acc(b0, fa[ty + 8][q], f0);
                     df_fma_acc(b1, fa[ty + 8][q + 1], f1);
                 }
-                const int64_t c = j1 + tx;
-                const int64_t ra = r0 + ty, rb = r0 + 8 + ty;
-                if (ra < k && tx < ncol && c <= ra)
-                    Kmat[ra * k + c] = pair_sub(__ldcg(Kmat + ra * k + c),
-                                                pair_add(pair_norm(a0.hi, a0.lo), pair_norm(a1.hi, a1.lo)));
-                if (rb < k && tx < ncol && c <= rb)
-                    Kmat[rb * k + c] = pair_sub(__ldcg(Kmat + rb * k + c),
-                                                pair_add(pair_norm(b0.hi, b0.lo), pair_norm(b1.hi, b1.lo)));
+                if (wa) Kmat[ra * k + c] = pair_sub(ka, pair_add(pair_norm(a0.hi, a0.lo), pair_norm(a1.hi, a1.lo)));
+                if (wb) Kmat[rb * k + c] = pair_sub(kb, pair_add(pair_norm(b0.hi, b0.lo), pair_norm(b1.hi, b1.lo)));
             }
         }
         if (!grid_sync_bounded(bar, nbar, status, nbar == 0 ? bar_extra : 0u, bar_limit_ns)) return;

@@ -308,73 +308,6 @@ k_grad_fast(const float* __restrict__ A, const float* __restrict__ b, const floa
 constexpr int kV3Consumers = 16;
 constexpr int kV3Threads = (kV3Consumers + 2) * 32;   // + finaliser + producer
 
-// packed FP32x2 (sm_100+): two independent IEEE binary32 operations per instruction
-struct f2 {
-    unsigned long long v;
-};
-__device__ __forceinline__ f2 f2_pack(float a, float b) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(f2 x, float& a, float& b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
-    f2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
-    return r;
-}
-
-// Two Acc2 accumulators in packed form.
-struct Acc2x2 {
-    f2 hi, lo;
-    // Dot2 step on both lanes: (hi, lo) += a * x exactly up to the final
-    // rounding of lo; xn = -x.  Same operations as Acc2::add_prod.
-    __device__ __forceinline__ void add_prod(f2 a, f2 x, f2 xn) {
-        const f2 np = f2_mul(a, xn);        // -p, p = fl(a x)
-        const f2 ep = f2_fma(a, x, np);     // a x - p
-        const f2 s = f2_sub(hi, np);        // hi + p
-        const f2 z = f2_sub(s, hi);
-        const f2 e1 = f2_sub(hi, f2_sub(s, z));
-        const f2 e2n = f2_add(np, z);       // -(p - z)
-        const f2 es = f2_sub(e1, e2n);
-        hi = s;
-        lo = f2_add(lo, f2_add(ep, es));
-    }
-    // Same operations as Acc2::add_pair.
-    __device__ __forceinline__ void add_pair(f2 h2, f2 l2) {
-        const f2 s = f2_add(hi, h2);
-        const f2 z = f2_sub(s, hi);
-        const f2 e = f2_add(f2_sub(hi, f2_sub(s, z)), f2_sub(h2, z));
-        hi = s;
-        lo = f2_add(lo, f2_add(e, l2));
-    }
-    // Same operations as Acc2::add.
-    __device__ __forceinline__ void add(f2 v) {
-        const f2 s = f2_add(hi, v);
-        const f2 z = f2_sub(s, hi);
-        const f2 e = f2_add(f2_sub(hi, f2_sub(s, z)), f2_sub(v, z));
-        hi = s;
-        lo = f2_add(lo, e);
-    }
-};
-
 struct V3Layout {
     size_t pdot, bsh, rsh, bars, total;
     // np: lane partials per tile (consumer lanes x rows per lane)
