@@ -85,6 +85,8 @@ extern "C" int ihs_ctx_create(ihs_ctx** out, void* stream, const ihs_params* p) 
         c->chol_per_sm = (cp && cp[0] == '1') ? 1 : 2;
         const char* ac = getenv("IHS_APPLY_CTAS");
         c->apply_ctas = ac ? (int)strtol(ac, nullptr, 10) : 0;
+        const char* gs = getenv("IHS_GRAM_SIMT");
+        c->gram_simt = (gs && gs[0] == '1') ? 1 : 0;
     }
     int st = IHS_OK;
     do {

@@ -89,6 +89,9 @@ struct ihs_ctx {
     int chol_per_sm;
     // CTAs of the fused apply (IHS_APPLY_CTAS, 1 .. SM count; 0: one per SM)
     int apply_ctas;
+    // 1: the Gram of a factorisation on the CUDA cores (compensated FP32 FMA
+    // chains) instead of the tensor cores (IHS_GRAM_SIMT=1)
+    int gram_simt;
 };
 
 // Decision log of the controller (api.cu): cleared at the start of a solve,
@@ -169,6 +172,11 @@ int ihs_gauss_tc_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int
 // fixed order; colscale may be NULL.
 int ihs_reduce_parts_enqueue(ihs_ctx* ctx, const float* part, bool pairs, int K, int64_t count, int64_t d,
                              double scale, const float* colscale, float* out);
+// K = X X^T + nu^2 I (X = SA, Woodbury, or (SA)^T, direct; kdim rows of X,
+// K inner entries) on the tensor cores into G (lower part; double-float pairs
+// when out_df, else FP64), on stream s (gram_tc.cu).
+int ihs_gram_tc_enqueue(ihs_ctx* ctx, const float* SA, int64_t d, int woodbury, int64_t kdim, int64_t K, double nu2,
+                        int out_df, double* G, cudaStream_t s);
 // A row shard's term of the sketch (rows [row0, row0 + n) of n_total) and of
 // the gradient (FP64 partial sums, d + 1 doubles: A^T (A x - b) and ||A x||^2).
 int ihs_sketch_shard_enqueue(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t row0, int64_t n_total,

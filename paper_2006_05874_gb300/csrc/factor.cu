@@ -1395,7 +1395,10 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
     const double nu2 = F->nu * F->nu;
     const float nu2_hi = (float)nu2;
     const float2 nu2df = make_float2(nu2_hi, (float)(nu2 - (double)nu2_hi));
-    {
+    if (!ctx->gram_simt) {
+        // tensor cores: exact three-piece BF16 split, slice sums added in double-float
+        IHS_TRY(ihs_gram_tc_enqueue(ctx, F->SA, F->d, F->woodbury, k, K, nu2, F->l_df, Kmat, s));
+    } else {
         // split the inner dimension so that at least two CTAs per SM work on
         // the Gram, with at least 64 inner rows per split
         const int64_t ntiles = T * (T + 1) / 2;
