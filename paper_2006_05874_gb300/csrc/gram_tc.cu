@@ -57,17 +57,26 @@ __device__ __forceinline__ uint32_t gkmaj(int r, int kb) {
 __device__ __forceinline__ void g_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void g_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// x = p1 + p2 + p3 exactly (BF16 pieces, round to nearest at each step)
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& p1, __nv_bfloat16& p2, __nv_bfloat16& p3) {
-    p1 = __float2bfloat16_rn(x);
-    const float r1 = __fsub_rn(x, __bfloat162float(p1));
-    p2 = __float2bfloat16_rn(r1);
-    const float r2 = __fsub_rn(r1, __bfloat162float(p2));
-    p3 = __float2bfloat16_rn(r2);
+// x = p1 + p2 + p3 exactly (BF16 pieces, round to nearest at each step), for
+// two entries at once as packed BF16 pairs (first entry in the low half): one
+// conversion instruction per piece for both entries, the widening back to
+// binary32 by shifts and masks, the residuals by f32x2 subtraction.
+__device__ __forceinline__ f2 bf2_widen(uint32_t u) {
+    return f2_pack(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
 }
-
-__device__ __forceinline__ uint32_t bf2(__nv_bfloat16 a, __nv_bfloat16 b) {
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+__device__ __forceinline__ uint32_t bf2_round(f2 x) {
+    float a, b;
+    f2_unpack(x, a, b);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ void split3x2(float a, float b, uint32_t& p1, uint32_t& p2, uint32_t& p3) {
+    const f2 x = f2_pack(a, b);
+    p1 = bf2_round(x);
+    const f2 r1 = f2_sub(x, bf2_widen(p1));
+    p2 = bf2_round(r1);
+    const f2 r2 = f2_sub(r1, bf2_widen(p2));
+    p3 = bf2_round(r2);
 }
 
 }  // namespace
@@ -134,15 +143,13 @@ k_gram_tc(const float* __restrict__ SA, int64_t d, int woodbury, int64_t kdim, i
                     v[j] = (row < kdim && kk < kend) ? (woodbury ? __ldg(SA + row * d + kk) : __ldg(SA + kk * d + row))
                                                      : 0.f;
                 }
-                __nv_bfloat16 p[3][8];
+                uint32_t p[3][4];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) split3(v[j], p[0][j], p[1][j], p[2][j]);
+                for (int j = 0; j < 4; ++j) split3x2(v[2 * j], v[2 * j + 1], p[0][j], p[1][j], p[2][j]);
                 const uint32_t off = gkmaj(r, kq * 2);
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
-                    *reinterpret_cast<uint4*>(pc + (size_t)q * GPIECE + off) =
-                        make_uint4(bf2(p[q][0], p[q][1]), bf2(p[q][2], p[q][3]), bf2(p[q][4], p[q][5]),
-                                   bf2(p[q][6], p[q][7]));
+                    *reinterpret_cast<uint4*>(pc + (size_t)q * GPIECE + off) = make_uint4(p[q][0], p[q][1], p[q][2], p[q][3]);
             }
         }
     };
@@ -175,9 +182,12 @@ k_gram_tc(const float* __restrict__ SA, int64_t d, int woodbury, int64_t kdim, i
     };
 
     const int quad = warp & 3, cpart = warp >> 2;   // TMEM lanes 32 quad .., columns 32 cpart ..
-    Acc2 acc[32];
+    // the 32 entries' (hi, lo) sums as packed pairs of adjacent columns: each
+    // TwoSum step is one f32x2 instruction for two entries (the same
+    // operations per entry as Acc2::add)
+    Acc2x2 acc[16];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = Acc2{0.f, 0.f};
+    for (int j = 0; j < 16; ++j) acc[j].hi.v = acc[j].lo.v = 0ull;
     bool ok = true;
     int64_t issued = -1;   // last chunk whose MMAs were issued
     if (nch > 0) split_chunk(0, 0);
@@ -198,20 +208,21 @@ k_gram_tc(const float* __restrict__ SA, int64_t d, int woodbury, int64_t kdim, i
                 break;
             }
             g_fence_after();
-            uint32_t v[32];
-            const uint32_t a = taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)(ks * GT + 32 * cpart);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(a));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j].add(__uint_as_float(v[j]));
+            for (int hh = 0; hh < 2; ++hh) {   // two loads of 16 columns each
+                uint32_t v[16];
+                const uint32_t a = taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)(ks * GT + 32 * cpart + 16 * hh);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(a));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    acc[8 * hh + j].add(f2_pack(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])));
+            }
         }
         // accumulators read and the next stage written: the next MMAs may start
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -232,7 +243,13 @@ k_gram_tc(const float* __restrict__ SA, int64_t d, int woodbury, int64_t kdim, i
         // that each store writes 32 consecutive entries of one row
         float2* tile = reinterpret_cast<float2*>(stage) + (size_t)warp * (32 * 33);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = make_float2(acc[j].hi, acc[j].lo);
+        for (int j = 0; j < 16; ++j) {
+            float h0, h1, l0, l1;
+            f2_unpack(acc[j].hi, h0, h1);
+            f2_unpack(acc[j].lo, l0, l1);
+            tile[lane * 33 + 2 * j] = make_float2(h0, l0);
+            tile[lane * 33 + 2 * j + 1] = make_float2(h1, l1);
+        }
         __syncwarp();
         const int64_t col = J * GT + 32 * cpart + lane;
         if (gridDim.y > 1) {

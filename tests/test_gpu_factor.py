@@ -104,3 +104,32 @@ def test_apply_parity_solver_sizes(ctx, torch_cuda, m, d, nu):
     assert err <= 1e-6, err
     r_ref = linalg.newton_decrement(g, gt_ref)
     assert abs(r - r_ref) <= 1e-9 * abs(r_ref)
+
+
+@pytest.mark.parametrize("m,d,nu", [(1024, 2048, 0.015313), (2048, 2048, 0.015313), (300, 200, 0.1), (37, 640, 0.2)])
+def test_gram_paths_match_oracle(torch_cuda, monkeypatch, m, d, nu):
+    """K = X X^T + nu^2 I (App. B.4) on the tensor cores (every entry of SA split
+    exactly into three BF16 pieces, slice sums added in double-float) and on the
+    CUDA cores (compensated FP32 chains, IHS_GRAM_SIMT=1): each factor's
+    application matches the FP64 oracle to the same bounds, and the two agree."""
+    from paper_2006_05874_gb300 import ihs
+
+    torch = torch_cuda
+    SA = _spectral_sketch(m, d, seed=m + 2 * d)
+    g = problems.random_vector(d, seed=d + 9)
+    gt_ref = linalg.WoodburyFactor(SA, nu).apply(g)
+    r_ref = linalg.newton_decrement(g, gt_ref)
+    outs = []
+    for simt in ("0", "1"):
+        monkeypatch.setenv("IHS_GRAM_SIMT", simt)
+        ctx = ihs.Context()
+        F = ctx.factor(torch.from_numpy(SA).cuda(), nu)
+        gt = torch.empty(d, device="cuda")
+        r = F.apply_hinv(torch.from_numpy(g).cuda(), gt)
+        F.destroy()
+        ctx.destroy()
+        gt = gt.cpu().numpy()
+        assert np.linalg.norm(gt - gt_ref) / np.linalg.norm(gt_ref) <= 1e-6
+        assert abs(r - r_ref) <= 1e-9 * abs(r_ref)
+        outs.append(gt)
+    assert np.linalg.norm(outs[0] - outs[1]) / np.linalg.norm(gt_ref) <= 2e-6
