@@ -455,7 +455,9 @@ __global__ void __launch_bounds__(256) k_syrk_rest(double* __restrict__ Kmat, in
 //            other CTAs apply panel j-1 to the trailing tiles of column
 //            blocks >= j+1 (the look-ahead overlap of the stream version);
 //   phase N: all CTAs form panel j (rows below block j) = K W_j^T;
-//   phase S: all CTAs update column block j+1 with panel j.
+//   phase S: all CTAs update column block j+1 with panel j, once the two CTAs
+//            that formed its first 32 rows (which every row's update reads)
+//            have published them on a counter: no grid barrier between N and S.
 // Matrix reads go through L2 (__ldcg): other SMs wrote them since the last
 // barrier.  Every barrier wait is bounded; a wait that gives up sets
 // IHS_DEV_TIMEOUT and the CTAs leave.
@@ -494,6 +496,29 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned* cnt, unsigned& nbar,
     }
     __syncthreads();
     return gs_ok != 0;
+}
+
+// Wait (bounded, like grid_sync_bounded) until the counter at `flag` reaches
+// `target`: the CTAs that published what this CTA reads next have arrived.
+__device__ __forceinline__ bool flag_wait_bounded(const unsigned* flag, unsigned target, unsigned* status,
+                                                  uint64_t limit_ns) {
+    __shared__ int fw_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fw_ok = 1;
+        if (ld_acquire_gpu(flag) < target) {
+            const uint64_t t0 = global_timer_ns();
+            while (ld_acquire_gpu(flag) < target) {
+                if (global_timer_ns() - t0 > limit_ns) {
+                    atomicOr(status, IHS_DEV_TIMEOUT);
+                    fw_ok = 0;
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return fw_ok != 0;
 }
 
 // acc += (a.x + a.y)(b.x + b.y) for double-float operands (pairs of binary32
@@ -685,6 +710,7 @@ __global__ void __launch_bounds__(256) k_chol_persistent(float2* __restrict__ Km
     // phase N, read by phase S and by the next step's trailing tiles)
     float2* Pdf = reinterpret_cast<float2*>(Wall + T * CB);
     unsigned nbar = 0;   // grid barriers passed
+    unsigned panel_target = 0;   // arrivals due so far on the panel counter (bar + 1)
     for (int64_t jb = 0; jb < T; ++jb) {
         const int64_t j0 = jb * CB;
         const int nb = (int)min((int64_t)CB, k - j0);
@@ -847,7 +873,22 @@ __global__ void __launch_bounds__(256) k_chol_persistent(float2* __restrict__ Km
                 if (rb < k) Pdf[rb * CB + lane] = xb;
             }
         }
-        if (!grid_sync_bounded(bar, nbar, status, nbar == 0 ? bar_extra : 0u, bar_limit_ns)) return;
+        // The column update reads panel rows j1 .. j1+31 (items 0 and 1, on
+        // CTAs 0 and 1 % G) and the CTA's own rows: the two producers publish
+        // their items on a counter instead of a grid barrier.
+        {
+            const int64_t items = ceil_div64(rest, 16);
+            const unsigned mine = (cta == 0 ? 1u : 0u) + ((items >= 2 && cta == 1 % G) ? 1u : 0u);
+            panel_target += items >= 2 ? 2u : 1u;
+            if (mine) {
+                __syncthreads();   // every warp's rows of the items are written
+                if (tid == 0) {
+                    __threadfence();
+                    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar + 1), "r"(mine) : "memory");
+                }
+            }
+            if (!flag_wait_bounded(bar + 1, panel_target, status, bar_limit_ns)) return;
+        }
         // ---- phase S: column block jb+1 updated by panel jb, 16 rows per work
         // item (thread (ty, tx) takes rows ty and ty + 8 of the item, column tx)
         {
@@ -1432,8 +1473,8 @@ int ihs_factor_enqueue(ihs_ctx* ctx, ihs_factor_t* F) {
     if (F->l_df) {
         const int G = Gcoop;
         {
-            unsigned* bar = ctx->d_status + 16;
-            IHS_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
+            unsigned* bar = ctx->d_status + 16;   // grid-barrier counter, then the panel counter
+            IHS_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
             int64_t kk = k;
             // test-only: the first launch of a context with the knob set gets an
             // unreachable first barrier (see ihs_ctx)
