@@ -7,22 +7,23 @@
 // residual keeps at most 8 significant bits fewer than the one before, so the
 // last piece is exact).  A product of two pieces is exact in FP32, and
 // x_a x_b = sum over the nine piece pairs.  The tensor core forms, for every
-// 16-wide slice of the inner dimension, the nine piece-pair products of a
-// 128 x 128 output tile in one FP32 accumulator in tensor memory; the CTA's
-// warps read each slice's accumulator back (tcgen05.ld) and add it into
-// double-float (hi, lo) accumulators in registers.  The only roundings are
-// the FP32 sum of one slice's 16 x 9 exact products and the compensated
-// additions, so K comes out about as accurate as with compensated FP32 FMA
-// chains on the CUDA cores.
+// 32-wide stretch of the inner dimension (two MMA slices of 16), the nine
+// piece-pair products of a 128 x 128 output tile in one FP32 accumulator in
+// tensor memory; the CTA's warps read each accumulator back (tcgen05.ld) and
+// add it into double-float (hi, lo) accumulators in registers.  The only
+// roundings are the FP32 sum of one stretch's 32 x 9 exact products and the
+// compensated additions, so K comes out about as accurate as with
+// compensated FP32 FMA chains on the CUDA cores.
 //
 // Layout: one CTA per output tile (and split of the inner dimension), 512
-// threads (16 warps) and all 512 tensor-memory columns: four accumulators of
-// 128 columns, one per slice of a 64-wide chunk.  The chunk's pieces (3 for
-// the tile's rows, 3 for its columns; 128 rows x 128 bytes each, K-major
-// without swizzle: core matrices of 8 rows x 16 bytes) sit in one of two
-// shared-memory stages, so that the warps split the next chunk while the
-// tensor core works on this one.  Warp w drains TMEM lanes 32 (w % 4) ...
-// and 32 columns starting at 32 (w / 4).
+// threads (16 warps) and all 512 tensor-memory columns: two pairs of 128-column
+// accumulators, a 64-wide chunk's two stretches in one pair, so that the MMAs
+// of the next chunk (in the other pair) run while the warps drain this one.
+// The chunk's pieces (3 for the tile's rows, 3 for its columns; 128 rows x
+// 128 bytes each, K-major without swizzle: core matrices of 8 rows x 16 bytes)
+// sit in one of two shared-memory stages, so that the warps split the next
+// chunk while the tensor core works on this one.  Warp w drains TMEM lanes
+// 32 (w % 4) ... and 32 columns starting at 32 (w / 4).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -33,7 +34,6 @@ namespace {
 
 constexpr int GT = 128;                        // output tile (M = N = 128)
 constexpr int GKE = 64;                        // inner entries per chunk
-constexpr int GSL = 16;                        // inner entries per MMA (BF16)
 constexpr int GTHREADS = 512;
 constexpr uint32_t GRB = GKE * 2;              // bytes of one row of a piece per chunk
 constexpr uint32_t GPIECE = GT * GRB;          // 16 KiB per piece
@@ -156,27 +156,31 @@ k_gram_tc(const float* __restrict__ SA, int64_t d, int woodbury, int64_t kdim, i
     // F32 accumulator, BF16 A and B, both K-major, N = M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GT >> 3) << 17) |
                            ((uint32_t)(GT >> 4) << 24);
-    // the nine piece-pair MMAs of each 16-wide slice into accumulator ks,
-    // one commit per accumulator
-    auto issue = [&](int s) {
+    // the nine piece-pair MMAs of the chunk's four 16-wide slices: slices 2h
+    // and 2h + 1 into accumulator 2 pr + h of pair pr (one commit each)
+    auto issue = [&](int s, int pr) {
         const uint32_t abase = smem_u32(stage + (size_t)s * GSTAGE);
         const uint32_t bbase = diag ? abase : abase + 3 * GPIECE;
 #pragma unroll
-        for (int ks = 0; ks < GKE / GSL; ++ks) {
-            const uint32_t tacc = taddr + (uint32_t)(ks * GT);
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t tacc = taddr + (uint32_t)((2 * pr + h) * GT);
 #pragma unroll
-            for (int pq = 0; pq < 9; ++pq) {
-                const int p = pq / 3, q = pq % 3;
-                const uint64_t ad = gdesc(abase + (uint32_t)p * GPIECE + ks * 256, 128, (GRB / 16) * 128);
-                const uint64_t bd = gdesc(bbase + (uint32_t)q * GPIECE + ks * 256, 128, (GRB / 16) * 128);
-                const uint32_t accum = pq > 0 ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tacc),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+            for (int sl = 0; sl < 2; ++sl) {
+                const int ks = 2 * h + sl;
+#pragma unroll
+                for (int pq = 0; pq < 9; ++pq) {
+                    const int p = pq / 3, q = pq % 3;
+                    const uint64_t ad = gdesc(abase + (uint32_t)p * GPIECE + ks * 256, 128, (GRB / 16) * 128);
+                    const uint64_t bd = gdesc(bbase + (uint32_t)q * GPIECE + ks * 256, 128, (GRB / 16) * 128);
+                    const uint32_t accum = (sl > 0 || pq > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tacc),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&bar[ks]))
+                             smem_u32(&bar[2 * pr + h]))
                          : "memory");
         }
     };
@@ -190,19 +194,32 @@ k_gram_tc(const float* __restrict__ SA, int64_t d, int woodbury, int64_t kdim, i
     for (int j = 0; j < 16; ++j) acc[j].hi.v = acc[j].lo.v = 0ull;
     bool ok = true;
     int64_t issued = -1;   // last chunk whose MMAs were issued
+    // pipeline: the MMAs of chunk c + 1 (accumulator pair (c + 1) & 1) run
+    // while the warps drain chunk c; the split of chunk c + 1 runs while the
+    // MMAs of chunk c do.  Barrier 2 pr + h completes once every two chunks.
     if (nch > 0) split_chunk(0, 0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     g_fence_before();
     __syncthreads();
     g_fence_after();
+    if (nch > 0 && tid == 0) issue(0, 0);
+    issued = nch > 0 ? 0 : -1;
     for (int64_t c = 0; c < nch && ok; ++c) {
-        const int s = (int)(c & 1);
-        if (tid == 0) issue(s);
-        issued = c;
-        if (c + 1 < nch) split_chunk(c + 1, s ^ 1);
-        // drain the chunk's four accumulators into the double-float sums
-        for (int ks = 0; ks < GKE / GSL; ++ks) {
-            const bool w = mbar_wait_bounded(&bar[ks], (uint32_t)(c & 1), status);
+        const int pr = (int)(c & 1);
+        if (c + 1 < nch) {
+            // stage (c + 1) & 1 was read by the MMAs of chunk c - 1, drained
+            // in the previous iteration; so was accumulator pair (c + 1) & 1
+            split_chunk(c + 1, (int)((c + 1) & 1));
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            g_fence_before();
+            __syncthreads();
+            g_fence_after();
+            if (tid == 0) issue((int)((c + 1) & 1), pr ^ 1);
+            issued = c + 1;
+        }
+        // drain chunk c's two accumulators into the double-float sums
+        for (int h = 0; h < 2; ++h) {
+            const bool w = mbar_wait_bounded(&bar[2 * pr + h], (uint32_t)((c >> 1) & 1), status);
             if (__syncthreads_or(!w)) {
                 ok = false;
                 break;
@@ -211,7 +228,8 @@ k_gram_tc(const float* __restrict__ SA, int64_t d, int woodbury, int64_t kdim, i
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {   // two loads of 16 columns each
                 uint32_t v[16];
-                const uint32_t a = taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)(ks * GT + 32 * cpart + 16 * hh);
+                const uint32_t a = taddr + ((uint32_t)(32 * quad) << 16) +
+                                   (uint32_t)((2 * pr + h) * GT + 32 * cpart + 16 * hh);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
@@ -224,8 +242,7 @@ k_gram_tc(const float* __restrict__ SA, int64_t d, int woodbury, int64_t kdim, i
                     acc[8 * hh + j].add(f2_pack(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])));
             }
         }
-        // accumulators read and the next stage written: the next MMAs may start
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // accumulator pair pr read: chunk c + 2 may be issued into it
         g_fence_before();
         __syncthreads();
         g_fence_after();
@@ -233,7 +250,7 @@ k_gram_tc(const float* __restrict__ SA, int64_t d, int woodbury, int64_t kdim, i
     if (!ok) {
         // a wait gave up: let the last issued MMAs finish before the TMEM is freed
         if (tid == 0 && issued >= 0)
-            mbar_wait_bounded(&bar[GKE / GSL - 1], (uint32_t)(issued & 1), status);
+            mbar_wait_bounded(&bar[2 * (int)(issued & 1) + 1], (uint32_t)((issued >> 1) & 1), status);
         g_fence_before();
         __syncthreads();
         g_fence_after();
