@@ -42,7 +42,7 @@ extern "C" {
 #define IHS_OK          0
 #define IHS_EINVAL     (-1)  /* bad argument (sizes, nu <= 0, n < d, m < 1, ...) */
 #define IHS_ENOMEM     (-2)  /* device or pinned-host allocation failed          */
-#define IHS_ENOTPD     (-3)  /* Cholesky met a non-positive pivot (FP64)          */
+#define IHS_ENOTPD     (-3)  /* Cholesky met a non-positive or non-finite pivot   */
 #define IHS_ENONFINITE (-4)  /* NaN/Inf in an input or in the decrement r_t       */
 #define IHS_EMCAP      (-5)  /* sketch size reached its cap (report flag only)    */
 #define IHS_EMAXITER   (-6)  /* iteration limit reached; x holds the last iterate */
@@ -166,8 +166,11 @@ int ihs_sketch_rows(ihs_ctx* ctx, const float* A, int64_t n, int64_t d, int64_t 
                     int32_t level, int64_t row0, int64_t mrows, float* SA_rows);
 
 /* Factor H_S = (SA)^T SA + nu^2 I (Eq. 3) for repeated applies: m < d caches
- * the FP64 Cholesky factor of nu^2 I_m + SA SA^T (Woodbury, App. B.4); m >= d
- * the FP64 Cholesky factor of H_S itself.  SA (m x d, device) must stay valid
+ * the Cholesky factor of nu^2 I_m + SA SA^T (Woodbury, App. B.4); m >= d
+ * the Cholesky factor of H_S itself.  The Gram is formed on the tensor cores
+ * from an exact three-piece BF16 split of SA's entries; the factor is held as
+ * double-float pairs of binary32 (about 2^-46 relative; FP64 in contexts that
+ * factor side by side).  SA (m x d, device) must stay valid
  * and unchanged while *F_h is in use.  nu > 0.  IHS_ENOTPD on breakdown. */
 int ihs_factor(ihs_ctx* ctx, const float* SA, int64_t m, int64_t d, double nu, ihs_factor_t** F_h);
 int ihs_factor_destroy(ihs_factor_t* F);
